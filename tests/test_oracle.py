@@ -285,3 +285,21 @@ def test_dense_gradient_matches_finite_difference():
         fd = (loss(H + step * E) - loss(H - step * E)) / (2 * step)
         an = g[a, c] + (g[c, a] if a != c else 0)
         assert abs(fd - an) < 1e-7 * max(1.0, abs(an))
+
+
+def test_iterates_after_switch_equal_plain_cocg(oracle_mod):
+    """After a seed switch the iterates of the remaining shifts are still those
+    of COCG run directly on each shift (Eq. inv_KS: one Krylov space serves all)."""
+    h = small_anderson(L=3, seed=23)
+    b = inputs.random_unit_complex(h.n, 13)
+    shifts = np.array([40.0 + 2.0j, -0.4 + 0.05j, 0.9 + 0.05j, 2.5 + 0.1j])
+    n = 30
+    a = oracle_mod.shifted_cocg(h.rowptr, h.col, h.val, shifts, b, proj_idx=[0], tol=1e-9,
+                                max_iter=n, seed=0, want_x=True)
+    assert a.n_switch >= 1 and a.n_iter == n and a.iters[0] < n
+    for k in range(1, 4):
+        if a.iters[k] < n:
+            continue
+        d = oracle_mod.shifted_cocg(h.rowptr, h.col, h.val, shifts[k:k + 1], b, proj_idx=[0],
+                                    tol=0.0, max_iter=n, seed=0, want_x=True)
+        assert np.linalg.norm(a.X[k] - d.X[0]) < 1e-9 * np.linalg.norm(d.X[0])
