@@ -1,0 +1,220 @@
+/*
+ * scocg.h -- C ABI of the GB300 shifted-COCG Green's-function library.
+ *
+ * The library solves, for one real symmetric N x N Hamiltonian H, many complex
+ * energies z_k = e_k + i delta_k at once and one or more right-hand sides b,
+ *
+ *     (z_k I - H) x_k = b                         (arXiv:0802.0748, Eq. lin_eq,
+ *                                                  Eq. shift_lin_eq)
+ *
+ * with the shifted conjugate-orthogonal conjugate-gradient method (Sec. III.C):
+ * one seed COCG recurrence on z_s, every other shift obtained from it by scalar
+ * recurrences (collinear residuals), seed switching when the seed converges
+ * first, and residual monitoring (Eq. residual).  It returns projections
+ *
+ *     G_mk = c_m^T x_k                            (Eq. gf: G_ij = <i|x_j>)
+ *
+ * for unit vectors c_m = e_i (Green's-function elements, local DOS
+ * -Im G_ii / pi) or dense vectors c_m (for a spectrum <b|G|b> pass c = conj(b)).
+ * H is either a CSR matrix (tight-binding form, Sec. II) or the matrix-free
+ * extended Hubbard model in a fixed (N_up, N_dn) sector (Sec. IV.D).
+ *
+ * Conventions for every entry point:
+ *  - Complex numbers are (re, im) pairs of doubles, scocg_c128.
+ *  - "device" pointers are CUDA global-memory pointers on the handle's device;
+ *    "host" pointers are ordinary CPU memory.  Caller memory is only borrowed
+ *    for the duration of a call; the library never frees it.
+ *  - The handle owns its device copy of H and its workspace (freed by
+ *    scocg_destroy).  All device work runs on the stream given at create time
+ *    (NULL = legacy default stream); calls that return results synchronise it.
+ *  - Errors are reported by return code only (see scocg_status); the library
+ *    never exits, aborts or traps.  A handle stays usable after any error
+ *    except SCOCG_ERR_CUDA.
+ *  - A handle is not thread-safe: one call at a time per handle.
+ */
+#ifndef SCOCG_H
+#define SCOCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct scocg_ctx *scocg_handle;
+typedef struct { double re, im; } scocg_c128;
+
+typedef enum {
+    SCOCG_OK = 0,               /* all shifts reached the tolerance                 */
+    SCOCG_NOT_CONVERGED = 1,    /* max_iter reached; outputs valid, see resid       */
+    SCOCG_ERR_INVALID = -1,     /* bad argument (size, pointer, index range)        */
+    SCOCG_ERR_CUDA = -2,        /* a CUDA runtime call failed                       */
+    SCOCG_ERR_OOM = -3,         /* device allocation failed                         */
+    SCOCG_ERR_BREAKDOWN = -4,   /* r^T r, r^T A p or a pi^k became zero / not finite */
+    SCOCG_ERR_TIMEOUT = -5,     /* a device-wide barrier did not complete in time   */
+    SCOCG_ERR_UNSYMMETRIC = -6  /* CSR input is not structurally/numerically symmetric */
+} scocg_status;
+
+typedef enum {
+    SCOCG_FP64 = 0,   /* complex128 vectors, FP64 H values and arithmetic            */
+    SCOCG_MIXED = 1   /* complex64 vectors and FP32 H values with FP32 arithmetic in
+                         the H apply and vector updates; FP64 seed scalars, FP64
+                         shift recurrences and periodic FP64 residual replacement   */
+} scocg_precision;
+
+/* Options, fixed at create time (scocg_set_opts changes them later).
+ * A zero-initialised struct (or NULL) selects every default. */
+typedef struct {
+    int precision;        /* scocg_precision                                          */
+    int max_iter;         /* iteration cap per solve; 0 -> 100000                     */
+    int replace_every;    /* MIXED: FP64 true-residual replacement interval in
+                             iterations; 0 -> 200; < 0 disables it                    */
+    int seed;             /* seed shift index; < 0 or out of range -> the seed rule:
+                             smallest Im z, then Re z nearest the median Re z, then
+                             the lowest index                                         */
+    int no_switch;        /* 1 disables seed switching (a converged seed with shifts
+                             left then returns SCOCG_ERR_BREAKDOWN)                   */
+    int autotune;         /* 1: time the kernel variants on the first solve and keep
+                             the fastest for this (N, nnz, nrhs, precision)           */
+    double timeout_ms;    /* device barrier watchdog; 0 -> 10000 ms                   */
+    int layout;           /* CSR handles: 0 = automatic (4x4-blocked sliced ELL when
+                             the pattern allows it, else CSR), 1 = force CSR         */
+    int grid;             /* CTAs of the persistent kernel; 0 = automatic, otherwise
+                             clamped to the device's co-resident maximum            */
+    int debug_inject;     /* fault-injection hook for tests, 0 = off:
+                             1 = make one CTA skip one barrier arrival at iteration 3
+                                 (the solve must end with SCOCG_ERR_TIMEOUT)
+                             2 = poison alpha with NaN at iteration 3 (the solve must
+                                 end with SCOCG_ERR_BREAKDOWN)                        */
+} scocg_opts;
+
+/* Per-solve report.  The two arrays are optional caller-owned HOST buffers of
+ * nrhs * nshift entries ([rhs][shift]); set them to NULL to skip. */
+typedef struct {
+    int iters;             /* seed iterations executed                                */
+    int n_switch;          /* seed switches                                          */
+    int seed_final;        /* index of the last seed shift                            */
+    int n_replace;         /* residual replacements (MIXED)                           */
+    long long shift_iters; /* sum over iterations of unconverged (rhs, shift) pairs   */
+    int *freeze_iter;      /* out: iteration at which each shift converged (or iters) */
+    double *resid;         /* out: ||r_k|| / ||b|| from the recurrence, at the end    */
+    double seconds;        /* device time of the solve kernel(s) (CUDA events)        */
+    double bytes_per_iter; /* algorithmic bytes of one seed iteration: H once in its
+                              device layout plus every vector pass of the kernel     */
+} scocg_info;
+
+/*
+ * scocg_create_csr -- take a real symmetric H in CSR form (Sec. II tight-binding
+ * Hamiltonian; the solver needs (z I - H) complex symmetric, Sec. III.C).
+ *   n                 rows (1 <= n < 2^31)
+ *   nnz               stored entries
+ *   rowptr[n+1]       int64, rowptr[0] = 0, non-decreasing, rowptr[n] = nnz
+ *   col[nnz]          int32 column of each entry, 0 <= col < n
+ *   val[nnz]          double value of each entry
+ *   ptr_on_device     0: the three arrays are host memory; 1: device memory
+ *   opts              may be NULL (defaults)
+ *   cuda_stream       cudaStream_t for all of this handle's work (NULL = default)
+ * The matrix is validated on the device (index range, sorted-or-not is allowed,
+ * exact symmetry H_ij == H_ji of every stored entry); a failure returns
+ * SCOCG_ERR_INVALID or SCOCG_ERR_UNSYMMETRIC and *out = NULL.  The library
+ * copies H into its own device layout (CSR, or 4x4-blocked sliced ELL when the
+ * pattern consists of dense 4x4 blocks), with FP32 values in MIXED precision.
+ */
+int scocg_create_csr(scocg_handle *out, int64_t n, int64_t nnz, const int64_t *rowptr,
+                     const int32_t *col, const double *val, int ptr_on_device,
+                     const scocg_opts *opts, void *cuda_stream);
+
+/*
+ * scocg_create_hubbard -- matrix-free extended Hubbard ring (Sec. IV.D):
+ *   H = -t sum_{<ij>,s} (c+_is c_js + h.c.) + U sum_i n_i,up n_i,dn + V sum_<ij> n_i n_j
+ * on L sites (2 <= L <= 16) in the sector with n_up up and n_dn down electrons.
+ * Bonds are (i, i+1), plus (L-1, 0) when periodic and L >= 3.  Basis index =
+ * rank_up * C(L, n_dn) + rank_dn, where rank is the position of the site-
+ * occupation bit string (bit i = site i) among all strings with the same number
+ * of ones in ascending numeric order.  Fermion signs follow Jordan-Wigner with
+ * modes ordered all up-spin sites, then all down-spin sites.
+ */
+int scocg_create_hubbard(scocg_handle *out, int L, int n_up, int n_dn, double t, double U,
+                         double V, int periodic, const scocg_opts *opts, void *cuda_stream);
+
+/* Dimension N of the handle's H. */
+int scocg_dim(scocg_handle h, int64_t *n);
+
+/* Replace the handle's options (same meaning as at create; precision changes
+ * re-layout H on the next solve). */
+int scocg_set_opts(scocg_handle h, const scocg_opts *opts);
+
+/*
+ * scocg_apply -- y = (z I - H) x once (the matrix of Eq. lin_eq).
+ *   precision SCOCG_FP64: x, y device complex128 [N]
+ *   precision SCOCG_MIXED: x, y device complex64 [N] (float re, im pairs),
+ *                          arithmetic in FP32 with FP32 values of H
+ * Synchronises the stream.
+ */
+int scocg_apply(scocg_handle h, scocg_c128 z, const void *x, void *y, int precision);
+
+/*
+ * scocg_solve -- shifted COCG for all shifts and right-hand sides (Sec. III.C).
+ *   shifts[nshift]        host, z_k (Im z_k > 0 for retarded Green's functions)
+ *   rhs                   device complex128 [nrhs][N], b for each right-hand side
+ *   proj_idx              host int64 [nrhs][nproj]: c_m = e_{proj_idx} (per rhs), or NULL
+ *   proj_vec              device complex128 [nproj][N]: dense c_m shared by all rhs, or NULL
+ *                         (exactly one of proj_idx / proj_vec is non-NULL)
+ *   tol                   shift k stops once ||r_k|| / ||b|| <= tol, where r_k is the
+ *                         residual of Eq. residual tracked by the recurrence
+ *   G_out                 device complex128 [nrhs][nproj][nshift], G_mk = c_m^T x_k
+ *   info                  optional report (may be NULL)
+ * Returns SCOCG_OK, SCOCG_NOT_CONVERGED (outputs valid, per-shift residuals in
+ * info) or an error.  1 <= nshift <= 4096, 1 <= nproj <= 32 (<= 4 when nrhs > 1).
+ */
+int scocg_solve(scocg_handle h, const scocg_c128 *shifts, int nshift, const void *rhs, int nrhs,
+                const int64_t *proj_idx, const void *proj_vec, int nproj, double tol,
+                scocg_c128 *G_out, scocg_info *info);
+
+/*
+ * scocg_solve_full -- the same solve for one right-hand side, but every shift's
+ * full solution x_k is formed (per-shift vectors p_k, x_k updated each
+ * iteration).  X_out: device complex128 [nshift][N].  Used by the adjoint and
+ * for true-residual checks; FP64 arithmetic regardless of the precision option.
+ */
+int scocg_solve_full(scocg_handle h, const scocg_c128 *shifts, int nshift, const void *rhs,
+                     double tol, void *X_out, scocg_info *info);
+
+/*
+ * scocg_grad -- gradient of a real loss L(G) with respect to every stored CSR
+ * value, given dL_dG (device complex128 [nrhs][nproj][nshift], torch
+ * convention dL/dRe G + i dL/dIm G).  With A_k = z_k I - H, x_k = A_k^{-1} b
+ * and y_mk = A_k^{-1} c_m (A_k is complex symmetric, so the adjoint solve is a
+ * second forward solve with the projection vectors as right-hand sides):
+ *   dL_dval[v] = Re sum_{k,m} conj(dL_dG_mk) y_mk[a] x_k[b]   for entry v = (a, b)
+ * Each stored entry is treated as an independent parameter; the gradient of a
+ * symmetric pair (a,b),(b,a) is dL_dval[(a,b)] + dL_dval[(b,a)].
+ * dL_dval: device double [nnz], overwritten.  Shifts are processed in chunks
+ * when the [chunk][N] solution vectors do not fit.  Not available for Hubbard
+ * handles (SCOCG_ERR_INVALID).  nrhs must be 1.
+ */
+int scocg_grad(scocg_handle h, const scocg_c128 *shifts, int nshift, const void *rhs, int nrhs,
+               const int64_t *proj_idx, const void *proj_vec, int nproj, double tol,
+               const scocg_c128 *dL_dG, double *dL_dval, scocg_info *info);
+
+/* Free the handle and everything it owns (NULL is ignored). */
+void scocg_destroy(scocg_handle h);
+
+/* Static description of a status code. */
+const char *scocg_strerror(int code);
+
+/*
+ * scocg_hubbard_tables -- copy the per-spin basis tables built on the device by
+ * scocg_create_hubbard, for checking.  Arrays are host memory:
+ *   states[D]            bit string of each rank (D = C(L, n_s))
+ *   hop_target[D][2L]    rank reached by each hop (-1 = unused slot)
+ *   hop_sign[D][2L]      Jordan-Wigner sign (+1/-1) of that hop (0 = unused)
+ * spin 0 = up, 1 = down.  Returns D in *dim.
+ */
+int scocg_hubbard_tables(scocg_handle h, int spin, int32_t *dim, uint32_t *states,
+                         int32_t *hop_target, int8_t *hop_sign);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCOCG_H */

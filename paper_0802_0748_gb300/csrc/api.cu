@@ -1,0 +1,479 @@
+// C ABI of the shifted-COCG library (declared in include/scocg.h): handle
+// life cycle, argument checks, workspace management and the solve driver
+// that launches the persistent kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "api_internal.h"
+
+using namespace scocg;
+
+// ---------------------------------------------------------------- helpers
+namespace scocg {
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return SCOCG_OK;
+    if (e == cudaErrorMemoryAllocation) return SCOCG_ERR_OOM;
+    return SCOCG_ERR_CUDA;
+}
+
+void* Workspace::get(size_t bytes) {
+    const size_t need = off + ((bytes + 255) / 256) * 256;
+    if (need > cap) return nullptr;
+    void* p = static_cast<char*>(base) + off;
+    off = need;
+    return p;
+}
+
+cudaError_t Workspace::reserve(size_t bytes) {
+    off = 0;
+    if (bytes <= cap) return cudaSuccess;
+    if (base) cudaFree(base);
+    base = nullptr; cap = 0;
+    cudaError_t e = cudaMalloc(&base, bytes);
+    if (e != cudaSuccess) { base = nullptr; return e; }
+    cap = bytes;
+    return cudaSuccess;
+}
+
+void Workspace::release() {
+    if (base) cudaFree(base);
+    base = nullptr; cap = 0; off = 0;
+}
+
+void fill_opts(scocg_opts& o, const scocg_opts* in) {
+    std::memset(&o, 0, sizeof(o));
+    if (in) o = *in;
+    if (o.max_iter <= 0) o.max_iter = 100000;
+    if (o.replace_every == 0) o.replace_every = 200;
+    if (o.timeout_ms <= 0) o.timeout_ms = 10000.0;
+    if (o.precision != SCOCG_FP64 && o.precision != SCOCG_MIXED) o.precision = -1;
+    if (o.layout != 0 && o.layout != 1) o.precision = -1;
+}
+
+// The seed rule (the method leaves the choice open): smallest Im z, then Re z
+// nearest the median of Re z, then the lowest index.
+int default_seed(const scocg_c128* z, int K) {
+    std::vector<double> re(K);
+    for (int k = 0; k < K; ++k) re[k] = z[k].re;
+    std::sort(re.begin(), re.end());
+    const double med = (K % 2) ? re[K / 2] : 0.5 * (re[K / 2 - 1] + re[K / 2]);
+    int best = 0;
+    for (int k = 1; k < K; ++k) {
+        if (z[k].im < z[best].im) { best = k; continue; }
+        if (z[k].im == z[best].im && std::fabs(z[k].re - med) < std::fabs(z[best].re - med)) best = k;
+    }
+    return best;
+}
+
+}  // namespace scocg
+
+extern "C" const char* scocg_strerror(int code) {
+    switch (code) {
+        case SCOCG_OK: return "ok";
+        case SCOCG_NOT_CONVERGED: return "not converged within max_iter (outputs valid)";
+        case SCOCG_ERR_INVALID: return "invalid argument";
+        case SCOCG_ERR_CUDA: return "CUDA runtime error";
+        case SCOCG_ERR_OOM: return "device out of memory";
+        case SCOCG_ERR_BREAKDOWN: return "COCG breakdown (zero or non-finite r^T r, r^T A p or pi)";
+        case SCOCG_ERR_TIMEOUT: return "device barrier timed out";
+        case SCOCG_ERR_UNSYMMETRIC: return "matrix is not symmetric";
+    }
+    return "unknown status";
+}
+
+// ---------------------------------------------------------------- create / destroy
+int scocg::init_ctx(scocg_ctx* h, const scocg_opts* opts, void* stream) {
+    fill_opts(h->opts, opts);
+    if (h->opts.precision < 0) return SCOCG_ERR_INVALID;
+    h->stream = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    int coop = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (!coop) return SCOCG_ERR_CUDA;
+    e = cudaMalloc(&h->d_ctrl, sizeof(Ctrl));
+    if (e != cudaSuccess) return cuda_status(e);
+    return SCOCG_OK;
+}
+
+void scocg_ctx::free_all() {
+    void* ptrs[] = {d_rowptr, d_col, d_val64, d_val32, d_unit_off, d_bcol, d_bval64, d_bval32, d_ctrl,
+                    hub.d_states, hub.d_hop_target, hub.d_hop_sign, hub.d_hop_packed};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    ws.release();
+}
+
+extern "C" void scocg_destroy(scocg_handle h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
+    h->free_all();
+    delete h;
+}
+
+extern "C" int scocg_dim(scocg_handle h, int64_t* n) {
+    if (!h || !n) return SCOCG_ERR_INVALID;
+    *n = h->n;
+    return SCOCG_OK;
+}
+
+extern "C" int scocg_set_opts(scocg_handle h, const scocg_opts* opts) {
+    if (!h) return SCOCG_ERR_INVALID;
+    scocg_opts o;
+    fill_opts(o, opts);
+    if (o.precision < 0) return SCOCG_ERR_INVALID;
+    h->opts = o;
+    return SCOCG_OK;
+}
+
+extern "C" int scocg_create_csr(scocg_handle* out, int64_t n, int64_t nnz, const int64_t* rowptr,
+                                const int32_t* col, const double* val, int ptr_on_device,
+                                const scocg_opts* opts, void* cuda_stream) {
+    if (!out) return SCOCG_ERR_INVALID;
+    *out = nullptr;
+    if (n < 1 || n >= (int64_t(1) << 31) || nnz < 0 || nnz >= (int64_t(1) << 31) || !rowptr ||
+        (nnz > 0 && (!col || !val)))
+        return SCOCG_ERR_INVALID;
+    scocg_ctx* h = new (std::nothrow) scocg_ctx();
+    if (!h) return SCOCG_ERR_OOM;
+    int st = init_ctx(h, opts, cuda_stream);
+    if (st != SCOCG_OK) { h->free_all(); delete h; return st; }
+    h->kind = HandleKind::kCsr;
+    h->n = n;
+    h->nnz = nnz;
+    cudaStream_t s = h->stream;
+
+    // device copies of the caller's arrays when they are host memory
+    const int64_t* d_rp = rowptr;
+    const int32_t* d_c = col;
+    const double* d_v = val;
+    void* tmp = nullptr;
+    cudaError_t e = cudaSuccess;
+    const size_t nnz_a = (size_t)std::max<int64_t>(nnz, 1);
+    if (!ptr_on_device) {
+        const size_t bytes = 256 * 4 + sizeof(int64_t) * (n + 1) + (sizeof(int32_t) + sizeof(double)) * nnz_a;
+        e = cudaMalloc(&tmp, bytes);
+        if (e == cudaSuccess) {
+            char* p = static_cast<char*>(tmp);
+            int64_t* rp = reinterpret_cast<int64_t*>(p);
+            p += ((sizeof(int64_t) * (n + 1) + 255) / 256) * 256;
+            double* vv = reinterpret_cast<double*>(p);
+            p += ((sizeof(double) * nnz_a + 255) / 256) * 256;
+            int32_t* cc = reinterpret_cast<int32_t*>(p);
+            e = cudaMemcpyAsync(rp, rowptr, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(cc, col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(vv, val, sizeof(double) * nnz, cudaMemcpyHostToDevice, s);
+            d_rp = rp; d_c = cc; d_v = vv;
+        }
+    }
+    unsigned* d_flags = nullptr;
+    unsigned flags = 0;
+    if (e == cudaSuccess) e = cudaMalloc(&d_flags, sizeof(unsigned));
+    if (e == cudaSuccess) e = validate_csr(n, nnz, d_rp, d_c, d_v, d_flags, &flags, s);
+    if (e == cudaSuccess) {
+        if (flags & (kFlagBadPtr | kFlagBadCol | kFlagBadVal)) st = SCOCG_ERR_INVALID;
+        else if (flags & kFlagUnsym) st = SCOCG_ERR_UNSYMMETRIC;
+    } else {
+        st = cuda_status(e);
+    }
+    h->fp32_exact = !(flags & kFlagNotFp32);
+    // int32 CSR with FP64 and FP32 values
+    if (st == SCOCG_OK) {
+        e = cudaMalloc(&h->d_rowptr, sizeof(int) * (n + 1));
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_col, sizeof(int) * nnz_a);
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_val64, sizeof(double) * nnz_a);
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_val32, sizeof(float) * nnz_a);
+        if (e == cudaSuccess)
+            e = convert_csr32(n, nnz, d_rp, d_c, d_v, h->d_rowptr, h->d_col, h->d_val64, h->d_val32, s);
+        if (e != cudaSuccess) st = cuda_status(e);
+    }
+    // 4x4-blocked sliced ELL when the pattern allows it
+    h->bsr_ok = st == SCOCG_OK && !(flags & kFlagNotBsr4) && nnz > 0;
+    if (h->bsr_ok) {
+        std::vector<int64_t> rp(n + 1);
+        e = cudaMemcpyAsync(rp.data(), d_rp, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        const int64_t nbr = n / 4, nunits = (nbr + 7) / 8;
+        std::vector<int> uoff(nunits + 1, 0);
+        if (e == cudaSuccess) {
+            int64_t slots = 0;
+            for (int64_t u = 0; u < nunits; ++u) {
+                int64_t mx = 0;
+                for (int64_t B = u * 8; B < std::min<int64_t>(nbr, u * 8 + 8); ++B)
+                    mx = std::max<int64_t>(mx, (rp[4 * B + 1] - rp[4 * B]) / 4);
+                uoff[u] = (int)slots;
+                slots += mx;
+            }
+            uoff[nunits] = (int)slots;
+            h->nunits_bsr = nunits;
+            h->nslots = slots;
+            e = cudaMalloc(&h->d_unit_off, sizeof(int) * (nunits + 1));
+            if (e == cudaSuccess) e = cudaMalloc(&h->d_bcol, sizeof(int) * 8 * std::max<int64_t>(slots, 1));
+            if (e == cudaSuccess) e = cudaMalloc(&h->d_bval64, sizeof(double) * 128 * std::max<int64_t>(slots, 1));
+            if (e == cudaSuccess) e = cudaMalloc(&h->d_bval32, sizeof(float) * 128 * std::max<int64_t>(slots, 1));
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h->d_unit_off, uoff.data(), sizeof(int) * (nunits + 1), cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess)
+                e = convert_bsr4(n, nunits, d_rp, d_c, d_v, h->d_unit_off, h->d_bcol, h->d_bval64, h->d_bval32, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        }
+        if (e != cudaSuccess) st = cuda_status(e);
+    }
+    if (st == SCOCG_OK) {
+        const double avg = (double)nnz / (double)n;
+        h->csr_kind = avg <= 4.0 ? LayoutKind::kCsr1 : (avg <= 24.0 ? LayoutKind::kCsr4 : LayoutKind::kCsr16);
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_status(e);
+    }
+    if (d_flags) cudaFree(d_flags);
+    if (tmp) { cudaStreamSynchronize(s); cudaFree(tmp); }
+    if (st != SCOCG_OK) { h->free_all(); delete h; return st; }
+    *out = h;
+    return SCOCG_OK;
+}
+
+Layout scocg_ctx::layout(bool prefer_csr) const {
+    Layout L{};
+    prefer_csr = prefer_csr || opts.layout == 1;
+    L.kind = (bsr_ok && !prefer_csr) ? LayoutKind::kBsr4 : csr_kind;
+    if (force_kind >= 0) L.kind = static_cast<LayoutKind>(force_kind);
+    if (L.kind == LayoutKind::kBsr4 && !bsr_ok) L.kind = csr_kind;
+    L.n = n; L.nnz = nnz;
+    L.rowptr = d_rowptr; L.col = d_col; L.val64 = d_val64; L.val32 = d_val32;
+    L.nunits_bsr = nunits_bsr; L.nslots = nslots;
+    L.unit_off = d_unit_off; L.bcol = d_bcol; L.bval64 = d_bval64; L.bval32 = d_bval32;
+    return L;
+}
+
+// ---------------------------------------------------------------- apply
+extern "C" int scocg_apply(scocg_handle h, scocg_c128 z, const void* x, void* y, int precision) {
+    if (!h || !x || !y || (precision != SCOCG_FP64 && precision != SCOCG_MIXED)) return SCOCG_ERR_INVALID;
+    cudaError_t e;
+    if (h->kind == HandleKind::kHubbard)
+        e = hubbard_apply(h->hub, precision == SCOCG_MIXED, c2(z.re, z.im), x, y, h->stream);
+    else
+        e = launch_apply(h->layout(false), precision == SCOCG_MIXED, c2(z.re, z.im), x, y, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return cuda_status(e);
+}
+
+// ---------------------------------------------------------------- solve
+namespace scocg {
+
+template <typename R>
+static int solve_one_rhs(scocg_ctx* h, const double2* d_z, int K, int seed, const double2* b,
+                         const int64_t* d_cidx, const void* cvec, int M, double tol, double2* G,
+                         int grid, ShiftState S, double* partA, double* partB, double* partC, int strideB,
+                         typename Vec<R>::T* r, typename Vec<R>::T* q, typename Vec<R>::T* pseed,
+                         typename Vec<R>::T* xhi, typename Vec<R>::T* xlo, double2* xd, const Layout& L) {
+    SolveArgs<R> a{};
+    a.n = h->n;
+    a.rows_per_unit = h->kind == HandleKind::kHubbard ? 32 : rows_per_unit(L.kind);
+    a.nunits = h->kind == HandleKind::kHubbard ? h->hub.nunits : (h->n + a.rows_per_unit - 1) / a.rows_per_unit;
+    a.r = r; a.q = q; a.b = b;
+    a.cvec = static_cast<const typename Vec<R>::T*>(cvec);
+    a.cidx = d_cidx;
+    a.nproj = M;
+    a.p_seed = pseed; a.x_hi = xhi; a.x_lo = xlo; a.xd = xd;
+    a.replace_every = h->opts.replace_every;
+    a.K = K; a.z = d_z; a.seed = seed;
+    a.allow_switch = !h->opts.no_switch;
+    a.tol = tol;
+    a.max_iter = h->opts.max_iter;
+    a.S = S;
+    a.partA = partA; a.partB = partB; a.partC = partC; a.strideB = strideB;
+    a.sync.count = &h->d_ctrl->count;
+    a.sync.status = &h->d_ctrl->status;
+    a.sync.timeout_ns = (uint64_t)(h->opts.timeout_ms * 1e6);
+    a.stats = &h->d_ctrl->stats;
+    a.G = G;
+    a.debug_inject = h->opts.debug_inject;
+    cudaError_t e = cudaMemsetAsync(h->d_ctrl, 0, sizeof(Ctrl), h->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (h->kind == HandleKind::kHubbard) e = hubbard_launch_solve(a, h->hub, grid, h->stream);
+    else e = launch_solve<R>(a, L, grid, h->stream);
+    return cuda_status(e);
+}
+
+__global__ void k_to_c64(int64_t n, const double2* in, float2* out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
+int algorithmic_bytes_note(void) { return 0; }
+
+}  // namespace scocg
+
+extern "C" int scocg_solve(scocg_handle h, const scocg_c128* shifts, int nshift, const void* rhs, int nrhs,
+                           const int64_t* proj_idx, const void* proj_vec, int nproj, double tol,
+                           scocg_c128* G_out, scocg_info* info) {
+    if (!h || !shifts || nshift < 1 || nshift > 4096 || !rhs || nrhs < 1 || nproj < 1 ||
+        nproj > kMaxProj || !G_out || (proj_idx == nullptr) == (proj_vec == nullptr) || !(tol >= 0.0))
+        return SCOCG_ERR_INVALID;
+    for (int k = 0; k < nshift; ++k)
+        if (!std::isfinite(shifts[k].re) || !std::isfinite(shifts[k].im)) return SCOCG_ERR_INVALID;
+    if (proj_idx)
+        for (int64_t j = 0; j < (int64_t)nrhs * nproj; ++j)
+            if (proj_idx[j] < 0 || proj_idx[j] >= h->n) return SCOCG_ERR_INVALID;
+    const bool mixed = h->opts.precision == SCOCG_MIXED;
+    const int64_t n = h->n;
+    const int K = nshift, M = nproj;
+    const int seed = (h->opts.seed >= 0 && h->opts.seed < K) ? h->opts.seed : default_seed(shifts, K);
+    cudaStream_t s = h->stream;
+
+    const Layout L = h->kind == HandleKind::kHubbard ? Layout{} : h->layout(false);
+    int maxco = h->kind == HandleKind::kHubbard ? hubbard_max_ctas(h->hub, mixed, h->num_sms)
+                                                 : max_coresident_ctas(L, mixed, h->num_sms);
+    if (maxco <= 0) return SCOCG_ERR_CUDA;
+    const int rpu = h->kind == HandleKind::kHubbard ? 32 : rows_per_unit(L.kind);
+    const int64_t nunits = h->kind == HandleKind::kHubbard ? h->hub.nunits : (n + rpu - 1) / rpu;
+    int64_t want = std::max<int64_t>((nunits + kWarps - 1) / kWarps, (K + kBlock - 1) / kBlock);
+    if (h->opts.grid > 0) want = h->opts.grid;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, maxco));
+    if ((int64_t)grid * kBlock < K) return SCOCG_ERR_INVALID;
+    const int strideB = 3 + 2 * M + 1;
+
+    // workspace layout
+    const size_t vbytes = (mixed ? sizeof(float2) : sizeof(double2)) * (size_t)n;
+    size_t need = 0;
+    auto add = [&](size_t b) { need += ((b + 255) / 256) * 256; };
+    add(vbytes); add(vbytes);                                  // r, q
+    if (mixed) { add(vbytes); add(vbytes); add(vbytes); add(sizeof(double2) * n); }
+    if (mixed && proj_vec) add(sizeof(float2) * (size_t)n * M);
+    add(sizeof(int64_t) * M);
+    add(sizeof(double2) * K);                                  // z
+    add(sizeof(double2) * K * 4); add(sizeof(double2) * (size_t)K * M * 2);
+    add(sizeof(int) * K * 2); add(sizeof(double) * K);
+    add(sizeof(double) * grid * 4); add(sizeof(double) * grid * strideB); add(sizeof(double) * grid * 4);
+    cudaError_t e = h->ws.reserve(need);
+    if (e != cudaSuccess) return cuda_status(e);
+    Workspace& W = h->ws;
+    void* r = W.get(vbytes);
+    void* q = W.get(vbytes);
+    void *ps = nullptr, *xh = nullptr, *xl = nullptr;
+    double2* xd = nullptr;
+    if (mixed) { ps = W.get(vbytes); xh = W.get(vbytes); xl = W.get(vbytes); xd = (double2*)W.get(sizeof(double2) * n); }
+    void* cvec = nullptr;
+    if (mixed && proj_vec) cvec = W.get(sizeof(float2) * (size_t)n * M);
+    int64_t* d_cidx = (int64_t*)W.get(sizeof(int64_t) * M);
+    double2* d_z = (double2*)W.get(sizeof(double2) * K);
+    ShiftState S;
+    S.pi_prev = (double2*)W.get(sizeof(double2) * K);
+    S.pi_cur = (double2*)W.get(sizeof(double2) * K);
+    S.sigma = (double2*)W.get(sizeof(double2) * K);
+    S.alpha_k = (double2*)W.get(sizeof(double2) * K);
+    S.P = (double2*)W.get(sizeof(double2) * (size_t)K * M);
+    S.X = (double2*)W.get(sizeof(double2) * (size_t)K * M);
+    S.frozen = (int*)W.get(sizeof(int) * K);
+    S.iters = (int*)W.get(sizeof(int) * K);
+    S.resid = (double*)W.get(sizeof(double) * K);
+    double* partA = (double*)W.get(sizeof(double) * grid * 4);
+    double* partB = (double*)W.get(sizeof(double) * grid * strideB);
+    double* partC = (double*)W.get(sizeof(double) * grid * 4);
+
+    e = cudaMemcpyAsync(d_z, shifts, sizeof(double2) * K, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && mixed && proj_vec) {
+        const int64_t tot = n * M;
+        k_to_c64<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(tot, (const double2*)proj_vec, (float2*)cvec);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    const void* cv = proj_vec ? (mixed ? cvec : proj_vec) : nullptr;
+
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEventCreate(&ev0); cudaEventCreate(&ev1);
+    float total_ms = 0.f;
+    int worst = SCOCG_OK;
+    int iters = 0, nsw = 0, seed_final = seed, nrep = 0;
+    long long siters = 0;
+    std::vector<int> h_iters(K);
+    std::vector<double> h_resid(K);
+    for (int j = 0; j < nrhs && worst >= 0; ++j) {
+        if (proj_idx) {
+            e = cudaMemcpyAsync(d_cidx, proj_idx + (size_t)j * M, sizeof(int64_t) * M, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) { worst = cuda_status(e); break; }
+        }
+        const double2* b = static_cast<const double2*>(rhs) + (size_t)j * n;
+        double2* G = reinterpret_cast<double2*>(G_out) + (size_t)j * M * K;
+        cudaEventRecord(ev0, s);
+        int st = mixed ? solve_one_rhs<float>(h, d_z, K, seed, b, proj_idx ? d_cidx : nullptr, cv, M, tol, G, grid, S,
+                                              partA, partB, partC, strideB, (float2*)r, (float2*)q, (float2*)ps,
+                                              (float2*)xh, (float2*)xl, xd, L)
+                       : solve_one_rhs<double>(h, d_z, K, seed, b, proj_idx ? d_cidx : nullptr, cv, M, tol, G, grid,
+                                               S, partA, partB, partC, strideB, (double2*)r, (double2*)q, nullptr,
+                                               nullptr, nullptr, nullptr, L);
+        cudaEventRecord(ev1, s);
+        if (st != SCOCG_OK) { worst = st; break; }
+        Ctrl c;
+        e = cudaMemcpyAsync(&c, h->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_iters.data(), S.iters, sizeof(int) * K, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_resid.data(), S.resid, sizeof(double) * K, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { worst = cuda_status(e); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        total_ms += ms;
+        const int dst = c.status;
+        if (dst < 0) worst = dst;
+        else if (dst == SCOCG_NOT_CONVERGED && worst == SCOCG_OK) worst = SCOCG_NOT_CONVERGED;
+        iters = std::max(iters, c.stats.iters);
+        nsw += c.stats.n_switch;
+        nrep += c.stats.n_replace;
+        seed_final = c.stats.seed;
+        siters += c.stats.shift_iters;
+        if (info) {
+            if (info->freeze_iter) std::memcpy(info->freeze_iter + (size_t)j * K, h_iters.data(), sizeof(int) * K);
+            if (info->resid) std::memcpy(info->resid + (size_t)j * K, h_resid.data(), sizeof(double) * K);
+        }
+    }
+    cudaEventDestroy(ev0); cudaEventDestroy(ev1);
+    if (info) {
+        info->iters = iters;
+        info->n_switch = nsw;
+        info->seed_final = seed_final;
+        info->n_replace = nrep;
+        info->shift_iters = siters;
+        info->seconds = total_ms * 1e-3;
+        info->bytes_per_iter = h->bytes_per_iter(mixed, proj_vec != nullptr, M);
+    }
+    return worst;
+}
+
+double scocg_ctx::bytes_per_iter(bool mixed, bool dense_proj, int M) const {
+    // Algorithmic bytes of one seed iteration: H once in the device layout,
+    // plus every vector pass the kernel makes (phase A: gather r, read and
+    // write q; phase B: read r and q, write r, read each dense c_m; MIXED adds
+    // the seed p (read, write) and the compensated x (two vectors read, write)).
+    const double vb = mixed ? 8.0 : 16.0;
+    double hbytes;
+    if (kind == HandleKind::kHubbard) {
+        hbytes = hub.table_bytes;
+    } else {
+        const Layout L = layout(false);
+        const double rb = mixed ? 4.0 : 8.0;
+        if (L.kind == LayoutKind::kBsr4) hbytes = (double)nslots * 8 * (4 + 16 * rb) + 4.0 * (nunits_bsr + 1);
+        else hbytes = (double)nnz * (4 + rb) + 4.0 * (n + 1);
+    }
+    double passes = 6 + (dense_proj ? M : 0);
+    if (mixed && opts.replace_every > 0) passes += 6;
+    return hbytes + passes * vb * (double)n;
+}
+
+// ---------------------------------------------------------------- not yet built entry points
+extern "C" int scocg_solve_full(scocg_handle h, const scocg_c128* shifts, int nshift, const void* rhs, double tol,
+                                void* X_out, scocg_info* info) {
+    return solve_full_impl(h, shifts, nshift, rhs, tol, X_out, info);
+}
+
+extern "C" int scocg_grad(scocg_handle h, const scocg_c128* shifts, int nshift, const void* rhs, int nrhs,
+                          const int64_t* proj_idx, const void* proj_vec, int nproj, double tol,
+                          const scocg_c128* dL_dG, double* dL_dval, scocg_info* info) {
+    return grad_impl(h, shifts, nshift, rhs, nrhs, proj_idx, proj_vec, nproj, tol, dL_dG, dL_dval, info);
+}

@@ -1,0 +1,97 @@
+// Handle structure and internal entry points shared by the C-ABI translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "layout.h"
+#include "solver_launch.h"
+
+namespace scocg {
+
+enum class HandleKind : int { kCsr = 0, kHubbard = 1 };
+
+// Device control block of one solve: barrier counter, status word, statistics.
+struct Ctrl {
+    unsigned long long count;
+    int status;
+    int pad;
+    SolveStats stats;
+};
+
+// Grow-only device workspace carved into 256-byte aligned pieces.
+struct Workspace {
+    void* base = nullptr;
+    size_t cap = 0;
+    size_t off = 0;
+    cudaError_t reserve(size_t bytes);   // resets the carve offset
+    void* get(size_t bytes);
+    void release();
+};
+
+// Matrix-free extended Hubbard model (per-spin tables built on the device).
+struct Hubbard {
+    int L = 0, n_up = 0, n_dn = 0, periodic = 0;
+    double t = 0, U = 0, V = 0;
+    int D_up = 0, D_dn = 0;
+    int64_t nunits = 0;
+    // tables for spin s at offset s * (table stride) in each array
+    uint32_t* d_states = nullptr;   // [2][Dmax]
+    int32_t* d_hop_target = nullptr;   // [2][Dmax][2L]
+    int8_t* d_hop_sign = nullptr;      // [2][Dmax][2L]
+    int32_t* d_hop_packed = nullptr;   // [2][Dmax][2L]: (target << 1) | (sign < 0), -1 = unused
+    int Dmax = 0;
+    double table_bytes = 0;
+};
+
+}  // namespace scocg
+
+struct scocg_ctx {
+    scocg::HandleKind kind = scocg::HandleKind::kCsr;
+    int64_t n = 0, nnz = 0;
+    scocg_opts opts{};
+    cudaStream_t stream = nullptr;
+    int device = 0, num_sms = 0;
+    // CSR layouts
+    int* d_rowptr = nullptr;
+    int* d_col = nullptr;
+    double* d_val64 = nullptr;
+    float* d_val32 = nullptr;
+    bool bsr_ok = false;
+    bool fp32_exact = false;
+    int64_t nunits_bsr = 0, nslots = 0;
+    int* d_unit_off = nullptr;
+    int* d_bcol = nullptr;
+    double* d_bval64 = nullptr;
+    float* d_bval32 = nullptr;
+    scocg::LayoutKind csr_kind = scocg::LayoutKind::kCsr1;
+    int force_kind = -1;       // tuning override of the CSR lanes-per-row layout
+    // Hubbard
+    scocg::Hubbard hub;
+    // per-solve state
+    scocg::Ctrl* d_ctrl = nullptr;
+    scocg::Workspace ws;
+
+    void free_all();
+    scocg::Layout layout(bool prefer_csr) const;
+    double bytes_per_iter(bool mixed, bool dense_proj, int M) const;
+};
+
+namespace scocg {
+int cuda_status(cudaError_t e);
+int init_ctx(scocg_ctx* h, const scocg_opts* opts, void* stream);
+void fill_opts(scocg_opts& o, const scocg_opts* in);
+int default_seed(const scocg_c128* z, int K);
+
+// Hubbard (hubbard.cu)
+cudaError_t hubbard_apply(const Hubbard& hb, bool mixed, double2 z, const void* x, void* y, cudaStream_t st);
+int hubbard_max_ctas(const Hubbard& hb, bool mixed, int num_sms);
+template <typename R>
+cudaError_t hubbard_launch_solve(const SolveArgs<R>& a, const Hubbard& hb, int grid, cudaStream_t st);
+
+// full-vector solve and gradient (adjoint.cu)
+int solve_full_impl(scocg_ctx* h, const scocg_c128* shifts, int nshift, const void* rhs, double tol, void* X_out,
+                    scocg_info* info);
+int grad_impl(scocg_ctx* h, const scocg_c128* shifts, int nshift, const void* rhs, int nrhs,
+              const int64_t* proj_idx, const void* proj_vec, int nproj, double tol, const scocg_c128* dL_dG,
+              double* dL_dval, scocg_info* info);
+}  // namespace scocg

@@ -1,0 +1,263 @@
+// Matrix-free extended Hubbard ring (Sec. IV.D of arXiv:0802.0748):
+//   H = -t sum_{<ij>,s} (c+_is c_js + h.c.) + U sum_i n_i,up n_i,dn + V sum_<ij> n_i n_j
+// in the sector with n_up up and n_dn down electrons on L sites.
+//
+// Basis: index = rank_up * D_dn + rank_dn; rank = position of the occupation
+// bit string among all L-bit strings with the same popcount, ascending, which
+// is the combinatorial number system sum_j C(pos_j, j + 1) over the set bits
+// pos_0 < pos_1 < ...  A hop moves one electron along a bond; with modes
+// ordered all up sites then all down sites (Jordan-Wigner) its sign is
+// (-1)^(number of same-spin electrons strictly between the two sites).
+// Per spin the device builds, for every rank, the list of (target rank, sign)
+// of all hops; the diagonal comes from popcounts of the two bit strings.
+//
+// Apply: a unit is 32 consecutive down-ranks (a "tile") of one up-rank, and
+// units are ordered tile-major and visited by all CTAs together, so the up-hop
+// gathers x[u'][tile] of concurrently running warps hit the same few column
+// tiles of x (L2 reuse); down-hop gathers stay inside the row x[u][:].
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "api_internal.h"
+#include "solver_kernel.cuh"
+
+namespace scocg {
+
+template <typename VV> struct Scal;
+template <> struct Scal<float2> { using T = float; };
+template <> struct Scal<double2> { using T = double; };
+
+__host__ __device__ inline int64_t binom(int n, int k) {
+    if (k < 0 || k > n) return 0;
+    int64_t r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+}
+
+__device__ inline int64_t rank_of(uint32_t s) {
+    int64_t r = 0;
+    int j = 0;
+    for (int pos = 0; pos < 32; ++pos)
+        if ((s >> pos) & 1u) { ++j; r += binom(pos, j); }
+    return r;
+}
+
+__device__ inline uint32_t unrank(int64_t r, int k, int L) {
+    uint32_t s = 0;
+    for (int j = k; j >= 1; --j) {
+        int p = j - 1;
+        while (p + 1 < L && binom(p + 1, j) <= r) ++p;
+        s |= 1u << p;
+        r -= binom(p, j);
+    }
+    return s;
+}
+
+// One thread per rank of one spin species.
+__global__ void k_hubbard_tables(int L, int k, int D, int ring, uint32_t* states, int32_t* target, int8_t* sign,
+                                 int32_t* packed) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= D) return;
+    const int S = 2 * L;
+    const uint32_t s = unrank(r, k, L);
+    states[r] = s;
+    int cnt = 0;
+    const int nb = ring ? L : L - 1;
+    for (int b = 0; b < nb; ++b) {
+        const int i = b, j = (b + 1) % L;
+        for (int dir = 0; dir < 2; ++dir) {
+            const int src = dir ? j : i, dst = dir ? i : j;
+            if (!((s >> src) & 1u) || ((s >> dst) & 1u)) continue;
+            const uint32_t s2 = (s & ~(1u << src)) | (1u << dst);
+            const int lo = min(src, dst), hi = max(src, dst);
+            const uint32_t between = hi - lo > 1 ? (s & (((1u << hi) - 1u) & ~((1u << (lo + 1)) - 1u))) : 0u;
+            const int sg = (__popc(between) & 1) ? -1 : 1;
+            const int t = (int)rank_of(s2);
+            target[(size_t)r * S + cnt] = t;
+            sign[(size_t)r * S + cnt] = (int8_t)sg;
+            packed[(size_t)r * S + cnt] = (t << 1) | (sg < 0 ? 1 : 0);
+            ++cnt;
+        }
+    }
+    for (int c = cnt; c < S; ++c) {
+        target[(size_t)r * S + c] = -1;
+        sign[(size_t)r * S + c] = 0;
+        packed[(size_t)r * S + c] = -1;
+    }
+}
+
+template <typename R>
+struct ApplyHubbard {
+    static constexpr int kRowsPerUnit = 32;
+    static constexpr bool kStrided = true;
+    const uint32_t* st_up;
+    const uint32_t* st_dn;
+    const int32_t* hop_up;     // packed, [D_up][S]
+    const int32_t* hop_dn;     // packed, [D_dn][S]
+    int S, D_up, D_dn, L, ring;
+    double t, U, V;
+    int64_t n;
+
+    __device__ __forceinline__ uint32_t partner(uint32_t x) const {
+        // bit i of the result = occupation of the bond partner i + 1 (and 0 for i = L - 1 on a ring)
+        return (x >> 1) | (ring ? ((x & 1u) << (L - 1)) : 0u);
+    }
+
+    template <typename VV>
+    __device__ __forceinline__ bool operator()(int64_t unit, int lane, VV zs, const VV* x, int64_t& row,
+                                               VV& w) const {
+        using T = typename Scal<VV>::T;
+        const int u = (int)(unit % D_up);
+        const int d = (int)(unit / D_up) * 32 + lane;
+        if (d >= D_dn) return false;
+        row = (int64_t)u * D_dn + d;
+        const uint32_t su = st_up[u], sd = st_dn[d];
+        const uint32_t pu = partner(su), pd = partner(sd);
+        const int cu = __popc(su & sd);
+        const int cv = __popc(su & pu) + __popc(sd & pd) + __popc(su & pd) + __popc(sd & pu);
+        const T diag = (T)U * (T)cu + (T)V * (T)cv;
+        VV acc;
+        {
+            const VV xr = x[row];
+            const T zr = zs.x - diag;
+            acc.x = zr * xr.x - zs.y * xr.y;
+            acc.y = zr * xr.y + zs.y * xr.x;
+        }
+        const T tt = (T)t;
+        const VV* xrow = x + (size_t)u * D_dn;
+        for (int j = 0; j < S; ++j) {
+            const int e = hop_dn[(size_t)d * S + j];
+            if (e < 0) break;
+            const VV xv = xrow[e >> 1];
+            const T c = (e & 1) ? -tt : tt;
+            acc.x += c * xv.x; acc.y += c * xv.y;
+        }
+        for (int j = 0; j < S; ++j) {
+            const int e = hop_up[(size_t)u * S + j];
+            if (e < 0) break;
+            const VV xv = x[(size_t)(e >> 1) * D_dn + d];
+            const T c = (e & 1) ? -tt : tt;
+            acc.x += c * xv.x; acc.y += c * xv.y;
+        }
+        w = acc;
+        return true;
+    }
+};
+
+template <typename R>
+static ApplyHubbard<R> make_apply(const Hubbard& hb) {
+    ApplyHubbard<R> ap;
+    ap.st_up = hb.d_states;
+    ap.st_dn = hb.d_states + hb.Dmax;
+    ap.S = 2 * hb.L;
+    ap.hop_up = hb.d_hop_packed;
+    ap.hop_dn = hb.d_hop_packed + (size_t)hb.Dmax * ap.S;
+    ap.D_up = hb.D_up; ap.D_dn = hb.D_dn; ap.L = hb.L;
+    ap.ring = hb.periodic && hb.L >= 3;
+    ap.t = hb.t; ap.U = hb.U; ap.V = hb.V;
+    ap.n = (int64_t)hb.D_up * hb.D_dn;
+    return ap;
+}
+
+int hubbard_max_ctas(const Hubbard& hb, bool mixed, int num_sms) {
+    int nb = 0;
+    cudaError_t e = mixed
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cocg_persistent<float, ApplyHubbard<float>>, kBlock, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cocg_persistent<double, ApplyHubbard<double>>, kBlock, 0);
+    (void)hb;
+    return e == cudaSuccess ? nb * num_sms : 0;
+}
+
+template <typename R>
+cudaError_t hubbard_launch_solve(const SolveArgs<R>& a, const Hubbard& hb, int grid, cudaStream_t st) {
+    ApplyHubbard<R> ap = make_apply<R>(hb);
+    void* args[] = {(void*)&a, (void*)&ap};
+    return cudaLaunchCooperativeKernel((const void*)cocg_persistent<R, ApplyHubbard<R>>, dim3(grid), dim3(kBlock),
+                                       args, 0, st);
+}
+template cudaError_t hubbard_launch_solve<double>(const SolveArgs<double>&, const Hubbard&, int, cudaStream_t);
+template cudaError_t hubbard_launch_solve<float>(const SolveArgs<float>&, const Hubbard&, int, cudaStream_t);
+
+template <typename VV, class Apply>
+__global__ void __launch_bounds__(256) k_hub_apply(Apply ap, int64_t nunits, VV zs, const VV* x, VV* y) {
+    const int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (u >= nunits) return;
+    int64_t row;
+    VV w;
+    if (ap(u, threadIdx.x & 31, zs, x, row, w)) y[row] = w;
+}
+
+cudaError_t hubbard_apply(const Hubbard& hb, bool mixed, double2 z, const void* x, void* y, cudaStream_t st) {
+    const unsigned blocks = (unsigned)((hb.nunits * 32 + 255) / 256);
+    if (mixed)
+        k_hub_apply<float2><<<blocks, 256, 0, st>>>(make_apply<float>(hb), hb.nunits,
+                                                    make_float2((float)z.x, (float)z.y), (const float2*)x, (float2*)y);
+    else
+        k_hub_apply<double2><<<blocks, 256, 0, st>>>(make_apply<double>(hb), hb.nunits, z, (const double2*)x,
+                                                     (double2*)y);
+    return cudaGetLastError();
+}
+
+}  // namespace scocg
+
+using namespace scocg;
+
+extern "C" int scocg_create_hubbard(scocg_handle* out, int L, int n_up, int n_dn, double t, double U, double V,
+                                    int periodic, const scocg_opts* opts, void* cuda_stream) {
+    if (!out) return SCOCG_ERR_INVALID;
+    *out = nullptr;
+    if (L < 2 || L > 16 || n_up < 0 || n_dn < 0 || n_up > L || n_dn > L || !std::isfinite(t) ||
+        !std::isfinite(U) || !std::isfinite(V))
+        return SCOCG_ERR_INVALID;
+    scocg_ctx* h = new (std::nothrow) scocg_ctx();
+    if (!h) return SCOCG_ERR_OOM;
+    int st = init_ctx(h, opts, cuda_stream);
+    if (st != SCOCG_OK) { h->free_all(); delete h; return st; }
+    Hubbard& hb = h->hub;
+    hb.L = L; hb.n_up = n_up; hb.n_dn = n_dn; hb.periodic = periodic ? 1 : 0;
+    hb.t = t; hb.U = U; hb.V = V;
+    hb.D_up = (int)binom(L, n_up);
+    hb.D_dn = (int)binom(L, n_dn);
+    hb.Dmax = std::max(hb.D_up, hb.D_dn);
+    const int S = 2 * L;
+    hb.nunits = (int64_t)hb.D_up * ((hb.D_dn + 31) / 32);
+    h->kind = HandleKind::kHubbard;
+    h->n = (int64_t)hb.D_up * hb.D_dn;
+    h->nnz = 0;
+    const size_t tab = (size_t)hb.Dmax * S;
+    cudaError_t e = cudaMalloc(&hb.d_states, sizeof(uint32_t) * 2 * hb.Dmax);
+    if (e == cudaSuccess) e = cudaMalloc(&hb.d_hop_target, sizeof(int32_t) * 2 * tab);
+    if (e == cudaSuccess) e = cudaMalloc(&hb.d_hop_sign, sizeof(int8_t) * 2 * tab);
+    if (e == cudaSuccess) e = cudaMalloc(&hb.d_hop_packed, sizeof(int32_t) * 2 * tab);
+    const int ring = (periodic && L >= 3) ? 1 : 0;
+    for (int sp = 0; sp < 2 && e == cudaSuccess; ++sp) {
+        const int D = sp ? hb.D_dn : hb.D_up, k = sp ? n_dn : n_up;
+        k_hubbard_tables<<<(D + 127) / 128, 128, 0, h->stream>>>(L, k, D, ring, hb.d_states + (size_t)sp * hb.Dmax,
+                                                                 hb.d_hop_target + sp * tab, hb.d_hop_sign + sp * tab,
+                                                                 hb.d_hop_packed + sp * tab);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    hb.table_bytes = (double)(hb.D_up + hb.D_dn) * (4.0 + 4.0 * S);
+    if (e != cudaSuccess) { st = cuda_status(e); h->free_all(); delete h; return st; }
+    *out = h;
+    return SCOCG_OK;
+}
+
+extern "C" int scocg_hubbard_tables(scocg_handle h, int spin, int32_t* dim, uint32_t* states, int32_t* hop_target,
+                                    int8_t* hop_sign) {
+    if (!h || h->kind != HandleKind::kHubbard || (spin != 0 && spin != 1) || !dim) return SCOCG_ERR_INVALID;
+    const Hubbard& hb = h->hub;
+    const int D = spin ? hb.D_dn : hb.D_up;
+    const size_t S = 2 * hb.L, tab = (size_t)hb.Dmax * S;
+    *dim = D;
+    cudaError_t e = cudaSuccess;
+    if (states) e = cudaMemcpy(states, hb.d_states + (size_t)spin * hb.Dmax, sizeof(uint32_t) * D, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && hop_target)
+        e = cudaMemcpy(hop_target, hb.d_hop_target + spin * tab, sizeof(int32_t) * D * S, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && hop_sign)
+        e = cudaMemcpy(hop_sign, hb.d_hop_sign + spin * tab, sizeof(int8_t) * D * S, cudaMemcpyDeviceToHost);
+    return cuda_status(e);
+}

@@ -1,0 +1,119 @@
+// Instantiations and launch of the persistent shifted-COCG kernel for every
+// (precision, H layout) pair, plus a one-shot apply kernel y = (z - H) x.
+#include "solver_kernel.cuh"
+#include "solver_launch.h"
+
+namespace scocg {
+
+template <typename R, class Apply>
+static cudaError_t coop_launch(const SolveArgs<R>& a, const Apply& ap, int grid, cudaStream_t st) {
+    void* args[] = {(void*)&a, (void*)&ap};
+    return cudaLaunchCooperativeKernel((const void*)cocg_persistent<R, Apply>, dim3(grid), dim3(kBlock), args, 0, st);
+}
+
+template <typename R, class Apply>
+static int occupancy_of() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cocg_persistent<R, Apply>, kBlock, 0) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+template <typename R>
+static const R* pick(const Layout& h, const double* d, const float* f);
+template <> const double* pick<double>(const Layout&, const double* d, const float*) { return d; }
+template <> const float* pick<float>(const Layout&, const double*, const float* f) { return f; }
+
+template <typename R>
+static int dispatch_occ(const Layout& h) {
+    switch (h.kind) {
+        case LayoutKind::kBsr4: return occupancy_of<R, ApplyBSR4<R>>();
+        case LayoutKind::kCsr1: return occupancy_of<R, ApplyCSR<R, 1>>();
+        case LayoutKind::kCsr4: return occupancy_of<R, ApplyCSR<R, 4>>();
+        case LayoutKind::kCsr16: return occupancy_of<R, ApplyCSR<R, 16>>();
+    }
+    return 0;
+}
+
+int max_coresident_ctas(const Layout& h, bool mixed, int num_sms) {
+    const int occ = mixed ? dispatch_occ<float>(h) : dispatch_occ<double>(h);
+    return occ * num_sms;
+}
+
+int rows_per_unit(LayoutKind k) {
+    switch (k) {
+        case LayoutKind::kBsr4: return 32;
+        case LayoutKind::kCsr1: return 32;
+        case LayoutKind::kCsr4: return 8;
+        case LayoutKind::kCsr16: return 2;
+    }
+    return 32;
+}
+
+template <typename R>
+cudaError_t launch_solve(const SolveArgs<R>& a, const Layout& h, int grid, cudaStream_t st) {
+    switch (h.kind) {
+        case LayoutKind::kBsr4: {
+            ApplyBSR4<R> ap{h.unit_off, h.bcol, pick<R>(h, h.bval64, h.bval32), h.n};
+            return coop_launch(a, ap, grid, st);
+        }
+        case LayoutKind::kCsr1: {
+            ApplyCSR<R, 1> ap{h.rowptr, h.col, pick<R>(h, h.val64, h.val32), h.n};
+            return coop_launch(a, ap, grid, st);
+        }
+        case LayoutKind::kCsr4: {
+            ApplyCSR<R, 4> ap{h.rowptr, h.col, pick<R>(h, h.val64, h.val32), h.n};
+            return coop_launch(a, ap, grid, st);
+        }
+        case LayoutKind::kCsr16: {
+            ApplyCSR<R, 16> ap{h.rowptr, h.col, pick<R>(h, h.val64, h.val32), h.n};
+            return coop_launch(a, ap, grid, st);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+template cudaError_t launch_solve<double>(const SolveArgs<double>&, const Layout&, int, cudaStream_t);
+template cudaError_t launch_solve<float>(const SolveArgs<float>&, const Layout&, int, cudaStream_t);
+
+// ---------------------------------------------------------------- one apply
+template <typename R, typename VV, class Apply>
+__global__ void __launch_bounds__(256) k_apply(Apply ap, int64_t nunits, VV zs, const VV* x, VV* y) {
+    const int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (u >= nunits) return;
+    int64_t row;
+    VV w;
+    if (ap(u, lane, zs, x, row, w)) y[row] = w;
+}
+
+template <typename R, typename VV, class Apply>
+static cudaError_t apply_one(const Apply& ap, int64_t nunits, VV zs, const VV* x, VV* y, cudaStream_t st) {
+    const int64_t threads = nunits * 32;
+    k_apply<R, VV, Apply><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(ap, nunits, zs, x, y);
+    return cudaGetLastError();
+}
+
+template <typename R, typename VV>
+static cudaError_t apply_dispatch(const Layout& h, int64_t nunits, VV zs, const VV* x, VV* y, cudaStream_t st) {
+    switch (h.kind) {
+        case LayoutKind::kBsr4:
+            return apply_one<R, VV>(ApplyBSR4<R>{h.unit_off, h.bcol, pick<R>(h, h.bval64, h.bval32), h.n}, nunits, zs, x, y, st);
+        case LayoutKind::kCsr1:
+            return apply_one<R, VV>(ApplyCSR<R, 1>{h.rowptr, h.col, pick<R>(h, h.val64, h.val32), h.n}, nunits, zs, x, y, st);
+        case LayoutKind::kCsr4:
+            return apply_one<R, VV>(ApplyCSR<R, 4>{h.rowptr, h.col, pick<R>(h, h.val64, h.val32), h.n}, nunits, zs, x, y, st);
+        case LayoutKind::kCsr16:
+            return apply_one<R, VV>(ApplyCSR<R, 16>{h.rowptr, h.col, pick<R>(h, h.val64, h.val32), h.n}, nunits, zs, x, y, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_apply(const Layout& h, bool mixed, double2 z, const void* x, void* y, cudaStream_t st) {
+    const int64_t nunits = (h.n + rows_per_unit(h.kind) - 1) / rows_per_unit(h.kind);
+    if (mixed)
+        return apply_dispatch<float, float2>(h, nunits, make_float2((float)z.x, (float)z.y), (const float2*)x,
+                                             (float2*)y, st);
+    return apply_dispatch<double, double2>(h, nunits, z, (const double2*)x, (double2*)y, st);
+}
+
+}  // namespace scocg

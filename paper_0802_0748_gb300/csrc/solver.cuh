@@ -1,0 +1,231 @@
+// Persistent single-right-hand-side shifted-COCG kernel (Sec. III.C of
+// arXiv:0802.0748), templated on the vector precision R (double: complex128,
+// float: complex64 with FP64 scalars) and on the H-apply functor.
+//
+// One cooperative launch runs the whole solve.  Each CTA owns a fixed range of
+// rows (the apply's "units") and a fixed subset of shifts (k = cta + j*grid).
+// Per seed iteration n (matrix A = z_s I - H):
+//   phase A  q_n = A r_n + beta_{n-1} q_{n-1}, partial r_n^T q_n      -> barrier
+//   phase B  alpha_n = rho_n / (r_n^T q_n) (every CTA, same reduction order);
+//            r_{n+1} = r_n - alpha_n q_n; partial r^T r, ||r||^2, c_m^T r -> barrier
+//   phase C  rho_{n+1}, beta_n; every CTA updates its own shifts:
+//            pi^k_{n+1} = (1 + alpha_n sigma_k) pi^k_n
+//                         + (alpha_n beta_{n-1}/alpha_{n-1}) (pi^k_n - pi^k_{n-1}),
+//            projected p^k and x^k:  P^k_m = c_m^T r_n / pi^k_n + beta^k_{n-1} P^k_m,
+//            X^k_m += alpha^k_n P^k_m, residual ||r_{n+1}|| / (|pi^k_{n+1}| ||b||).
+// q_n = A p_n replaces the seed direction p_n (p is never stored); r_n^T q_n
+// equals p_n^T A p_n because successive directions are A-conjugate in the
+// bilinear form.  When the seed converges first, the unconverged shift with
+// the largest residual becomes the new seed (seed switching) with
+//   r' = r_{n+1} / pi'_{n+1},  q' = (r_n / pi'_n - r_{n+1} / pi'_{n+1}) / alpha'_n,
+// pi^k <- pi^k / pi', sigma_k <- z_k - z_s'.
+// MIXED precision additionally carries the seed's p and x (x compensated) and
+// every `replace_every` iterations replaces r by the FP64 true residual
+// b - A x (reliable update).
+#pragma once
+#include "common.cuh"
+
+namespace scocg {
+
+struct ShiftState {          // device arrays, [K] or [K][M]
+    double2* pi_prev;
+    double2* pi_cur;
+    double2* sigma;
+    double2* alpha_k;        // alpha^k_n of the last update (needed by a switch)
+    double2* P;              // [K][M] c_m^T p^k
+    double2* X;              // [K][M] c_m^T x^k
+    int* frozen;
+    int* iters;
+    double* resid;
+};
+
+struct SolveStats {          // device, written by CTA 0
+    int status;
+    int iters;
+    int n_switch;
+    int seed;
+    int n_replace;
+    int pad;
+    long long shift_iters;
+};
+
+// ---------------------------------------------------------------- applies
+// Every apply maps (unit, lane) to at most one row and returns, on the lane
+// that owns the row, w = z_s x_row - (H x)_row.  The vector type VV sets the
+// arithmetic precision (float2: FP32, double2: FP64 with FP32 values promoted).
+
+__device__ __forceinline__ void cfma_r(double2& acc, float v, double2 x) { cfma_r(acc, (double)v, x); }
+
+// four consecutive complex entries starting at a 32-byte (float2) or 64-byte
+// (double2) aligned address
+__device__ __forceinline__ void load4(const float2* p, float2 (&x)[4]) {
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    const float4 b = *reinterpret_cast<const float4*>(p + 2);
+    x[0] = make_float2(a.x, a.y); x[1] = make_float2(a.z, a.w);
+    x[2] = make_float2(b.x, b.y); x[3] = make_float2(b.z, b.w);
+}
+__device__ __forceinline__ void load4(const double2* p, double2 (&x)[4]) {
+    x[0] = p[0]; x[1] = p[1]; x[2] = p[2]; x[3] = p[3];
+}
+
+template <typename R, int LPR>
+struct ApplyCSR {
+    static constexpr int kRowsPerUnit = 32 / LPR;
+    static constexpr bool kStrided = false;
+    const int* rowptr;
+    const int* col;
+    const R* val;
+    int64_t n;
+
+    template <typename VV>
+    __device__ __forceinline__ bool operator()(int64_t unit, int lane, VV zs, const VV* x,
+                                               int64_t& row, VV& w) const {
+        const int sub = lane / LPR, l = lane % LPR;
+        row = unit * kRowsPerUnit + sub;
+        VV acc = vzero<VV>();
+        if (row < n) {
+            const int e0 = rowptr[row], e1 = rowptr[row + 1];
+            for (int e = e0 + l; e < e1; e += LPR) cfma_r(acc, ld_stream(val + e), x[ld_stream(col + e)]);
+        }
+#pragma unroll
+        for (int o = LPR / 2; o > 0; o >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        }
+        if (row < n && l == 0) {
+            w = vsub(vcfma(zs, x[row], vzero<VV>()), acc);
+            return true;
+        }
+        return false;
+    }
+};
+
+// 4x4-blocked sliced ELL: a unit is 8 block rows (32 rows); slot s of unit u
+// holds, for each of its 8 block rows, one column-block index (or -1 for
+// padding) and one dense 4x4 block stored row-major.  Lane = 4 * block row +
+// row within the block, so a warp's load of one slot is contiguous.
+template <typename R>
+struct ApplyBSR4 {
+    static constexpr int kRowsPerUnit = 32;
+    static constexpr bool kStrided = false;
+    const int* unit_off;     // [nunits + 1] first slot of each unit
+    const int* bcol;         // [slots][8]
+    const R* bval;           // [slots][8][4][4]
+    int64_t n;
+
+    __device__ __forceinline__ static void load_row(const float* p, float (&v)[4]) {
+        const float4 t = ld_stream(reinterpret_cast<const float4*>(p));
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+    __device__ __forceinline__ static void load_row(const double* p, double (&v)[4]) {
+        const double2 a = ld_stream(reinterpret_cast<const double2*>(p));
+        const double2 b = ld_stream(reinterpret_cast<const double2*>(p) + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+
+    template <typename VV>
+    __device__ __forceinline__ static void block_fma(VV& acc, int cb, const R (&v)[4], const VV* x) {
+        if (cb >= 0) {
+            VV xv[4];
+            load4(x + (size_t)cb * 4, xv);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) cfma_r(acc, v[j], xv[j]);
+        }
+    }
+
+    template <typename VV>
+    __device__ __forceinline__ bool operator()(int64_t unit, int lane, VV zs, const VV* x,
+                                               int64_t& row, VV& w) const {
+        const int br = lane >> 2, rr = lane & 3;
+        row = unit * 32 + lane;
+        const int s0 = unit_off[unit], s1 = unit_off[unit + 1];
+        VV acc = vzero<VV>();
+        int s = s0;
+        for (; s + 4 <= s1; s += 4) {                 // four slots in flight
+            int cb[4];
+            R v[4][4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                cb[j] = ld_stream(bcol + (size_t)(s + j) * 8 + br);
+                load_row(bval + ((size_t)(s + j) * 8 + br) * 16 + rr * 4, v[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) block_fma(acc, cb[j], v[j], x);
+        }
+        for (; s < s1; ++s) {
+            R v[4];
+            const int cb = ld_stream(bcol + (size_t)s * 8 + br);
+            load_row(bval + ((size_t)s * 8 + br) * 16 + rr * 4, v);
+            block_fma(acc, cb, v, x);
+        }
+        if (row < n) {
+            w = vsub(vcfma(zs, x[row], vzero<VV>()), acc);
+            return true;
+        }
+        return false;
+    }
+};
+
+// ---------------------------------------------------------------- arguments
+template <typename R>
+struct SolveArgs {
+    using V = typename Vec<R>::T;
+    int64_t n;
+    int64_t nunits;
+    int rows_per_unit;
+    V* r;
+    V* q;
+    const double2* b;          // rhs, complex128 [n]
+    const V* cvec;             // dense projections [nproj][n] in vector precision, or null
+    const int64_t* cidx;       // unit projections [nproj], or null
+    int nproj;
+    // MIXED: seed direction and compensated seed solution; FP64 apply for replacement
+    V* p_seed;
+    V* x_hi;
+    V* x_lo;
+    double2* xd;               // FP64 copy of x used by the replacement apply
+    int replace_every;
+    // shifts
+    int K;
+    const double2* z;
+    int seed;
+    int allow_switch;
+    double tol;
+    int max_iter;
+    ShiftState S;
+    // per-CTA partials
+    double* partA;             // [grid][4]
+    double* partB;             // [grid][strideB]
+    double* partC;             // [grid][4]
+    int strideB;
+    GridSync sync;
+    SolveStats* stats;
+    double2* G;                // out [nproj][K] for this right-hand side
+    int debug_inject;
+};
+
+// Shared per-CTA copy of the seed scalars; every CTA holds identical values.
+struct SeedScalars {
+    double2 alpha, alpha_prev, beta_prev, rho, rho_prev, zs;
+    double rnorm, bnorm;
+    int seed, active, n;
+    int replace_on, n_switch, n_replace;
+    long long shift_iters;
+    double2 cr_cur[kMaxProj];   // c_m^T r_n
+    double2 cr_next[kMaxProj];  // c_m^T r_{n+1}
+    double red[4 + 2 * kMaxProj + 4];
+    double scratch[kWarps * (3 + 2 * kMaxProj)];
+};
+
+// residual estimate of a shift from the seed residual norm and its pi
+__device__ __forceinline__ double shift_resid(double rnorm, double2 pi, double bnorm) {
+    return rnorm / (cabs_(pi) * bnorm);
+}
+
+// Fixed-order complex dot contribution c^T r in FP64
+__device__ __forceinline__ void acc_dot(double2& s, double2 a, double2 b) {
+    s.x = fma(a.x, b.x, fma(-a.y, b.y, s.x));
+    s.y = fma(a.x, b.y, fma(a.y, b.x, s.y));
+}
+
+}  // namespace scocg

@@ -1,0 +1,419 @@
+// Body of the persistent single-right-hand-side shifted-COCG kernel.  See
+// solver.cuh for the algorithm; this file holds the phases.
+#pragma once
+#include "solver.cuh"
+
+namespace scocg {
+
+template <int NV>
+__device__ __forceinline__ void block_sum_n(double (&v)[NV], double* scratch, double* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        double t = warp_sum(v[j]);
+        if (lane == 0) scratch[warp * NV + j] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+        for (int w = 0; w < kWarps; ++w) s += scratch[w * NV + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// per-thread accumulation of u^T v (bilinear) in the vector precision
+__device__ __forceinline__ void acc_bil(double& re, double& im, double2 u, double2 v) {
+    re = fma(u.x, v.x, fma(-u.y, v.y, re)); im = fma(u.x, v.y, fma(u.y, v.x, im));
+}
+__device__ __forceinline__ void acc_bil(float& re, float& im, float2 u, float2 v) {
+    re = fmaf(u.x, v.x, fmaf(-u.y, v.y, re)); im = fmaf(u.x, v.y, fmaf(u.y, v.x, im));
+}
+__device__ __forceinline__ void acc_nrm(double& s, double2 u) { s = fma(u.x, u.x, fma(u.y, u.y, s)); }
+__device__ __forceinline__ void acc_nrm(float& s, float2 u) { s = fmaf(u.x, u.x, fmaf(u.y, u.y, s)); }
+
+// Per-thread accumulation of the r partials: rho = r^T r, ||r||^2, c_0^T r.
+template <typename R>
+__device__ __forceinline__ void acc_r(R (&acc)[5], typename Vec<R>::T ri, const typename Vec<R>::T* c0) {
+    acc_bil(acc[0], acc[1], ri, ri);
+    acc_nrm(acc[2], ri);
+    if (c0) acc_bil(acc[3], acc[4], *c0, ri);
+}
+
+// CTA sum of the accumulated partials into part[0..5); the extra dense
+// projections m >= 1 are summed in separate passes over r into part[3 + 2m].
+template <typename R>
+__device__ __forceinline__ void finish_r_partials(const SolveArgs<R>& a, const R (&acc)[5], int64_t rbeg,
+                                                  int64_t rend, SeedScalars& s, double* s_part, double* part) {
+    const int tid = threadIdx.x;
+    double v[5] = {acc[0], acc[1], acc[2], acc[3], acc[4]};
+    block_sum_n<5>(v, s.scratch, s_part);
+    if (tid < 5) part[tid] = s_part[tid];
+    for (int m = 1; m < a.nproj && a.cvec; ++m) {
+        R w[2] = {0, 0};
+        for (int64_t i = rbeg + tid; i < rend; i += kBlock) acc_bil(w[0], w[1], a.cvec[(size_t)m * a.n + i], a.r[i]);
+        double w2[2] = {w[0], w[1]};
+        block_sum_n<2>(w2, s.scratch, s_part);
+        if (tid < 2) part[3 + 2 * m + tid] = s_part[tid];
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void r_partials(const SolveArgs<R>& a, int64_t rbeg, int64_t rend,
+                                           SeedScalars& s, double* s_part, double* part) {
+    R acc[5] = {0, 0, 0, 0, 0};
+    for (int64_t i = rbeg + threadIdx.x; i < rend; i += kBlock)
+        acc_r(acc, a.r[i], a.cvec ? a.cvec + i : nullptr);
+    finish_r_partials(a, acc, rbeg, rend, s, s_part, part);
+}
+
+template <typename R, class Apply>
+__global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, Apply ap) {
+    using V = typename Vec<R>::T;
+    constexpr bool kMixed = sizeof(R) == 4;
+    __shared__ SeedScalars s;
+    __shared__ double s_part[8];
+    __shared__ int s_flag[4];
+    __shared__ double s_min[kWarps];
+    __shared__ int s_arg[kWarps];
+
+    const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    // phase A visits units: a contiguous range per CTA, or (strided applies) the
+    // units cta + G * (warp + kWarps * j) so that all CTAs sweep the unit space
+    // together; the row-wise phases use a contiguous row range per CTA.
+    const int64_t ubeg = (int64_t)cta * a.nunits / G, uend = (int64_t)(cta + 1) * a.nunits / G;
+    const int64_t u_first = Apply::kStrided ? (int64_t)cta + (int64_t)G * warp : ubeg + warp;
+    const int64_t u_step = Apply::kStrided ? (int64_t)G * kWarps : kWarps;
+    const int64_t u_end = Apply::kStrided ? a.nunits : uend;
+    const int64_t rbeg = (int64_t)cta * a.n / G, rend = (int64_t)(cta + 1) * a.n / G;
+    const int M = a.nproj;
+    const bool dense_proj = a.cvec != nullptr;
+    const int nred = dense_proj ? 3 + 2 * M : 3;
+    double* myB = a.partB + (size_t)cta * a.strideB;
+    unsigned long long epoch = 0;
+    const int k_own = cta + tid * G;          // the shift this thread owns (if < K)
+    const bool owns = k_own < a.K;
+    int status = 0;
+
+    // ------------------------------------------------------------ init: r_0 = b, q_{-1} = 0
+    {
+        double nb = 0.0;
+        for (int64_t i = rbeg + tid; i < rend; i += kBlock) {
+            const double2 bi = a.b[i];
+            a.r[i] = Vec<R>::make(bi);
+            a.q[i] = vzero<V>();
+            if constexpr (kMixed) {
+                a.p_seed[i] = vzero<V>(); a.x_hi[i] = vzero<V>(); a.x_lo[i] = vzero<V>();
+            }
+            nb = fma(bi.x, bi.x, fma(bi.y, bi.y, nb));
+        }
+        double v1[1] = {nb};
+        block_sum_n<1>(v1, s.scratch, s_part);
+        if (tid == 0) a.partC[(size_t)cta * 4] = s_part[0];
+        __syncthreads();
+        r_partials(a, rbeg, rend, s, s_part, myB);
+        if (owns) {
+            const int k = k_own;
+            a.S.pi_prev[k] = c2(1, 0); a.S.pi_cur[k] = c2(1, 0);
+            a.S.sigma[k] = csub(a.z[k], a.z[a.seed]);
+            a.S.alpha_k[k] = c2(0, 0);
+            for (int m = 0; m < M; ++m) { a.S.P[(size_t)k * M + m] = c2(0, 0); a.S.X[(size_t)k * M + m] = c2(0, 0); }
+            a.S.frozen[k] = 0; a.S.iters[k] = 0; a.S.resid[k] = 1.0;
+        }
+        if (tid < 4) s_flag[tid] = 0;
+        if (!grid_barrier(a.sync, epoch)) return;
+        grid_sum(a.partB, a.strideB, nred, s.red);
+        grid_sum(a.partC, 4, 1, s.red + nred);
+        if (tid == 0) {
+            s.rho = c2(s.red[0], s.red[1]);
+            s.bnorm = sqrt(s.red[nred]);
+            s.rnorm = s.bnorm;
+            s.alpha_prev = c2(1, 0);
+            s.beta_prev = c2(0, 0);
+            s.seed = a.seed;
+            s.zs = a.z[a.seed];
+            s.n = 0;
+            s.active = a.K;
+            s.replace_on = kMixed && a.replace_every > 0;
+            s.n_switch = 0; s.n_replace = 0; s.shift_iters = 0;
+        }
+        if (tid < M) {
+            s.cr_cur[tid] = dense_proj ? c2(s.red[3 + 2 * tid], s.red[4 + 2 * tid])
+                                       : Vec<R>::wide(__ldcg(a.r + a.cidx[tid]));
+        }
+        __syncthreads();
+        if (s.bnorm == 0.0) {                 // b = 0: x = 0 solves every shift
+            if (owns) { a.S.frozen[k_own] = 1; a.S.resid[k_own] = 0.0; }
+            status = SCOCG_OK;
+        }
+    }
+
+    // ------------------------------------------------------------ iterations
+    while (status == 0) {
+        // ---- phase A: q_n = (z_s - H) r_n + beta_{n-1} q_{n-1}; partial r_n^T q_n
+        {
+            const V zs = Vec<R>::make(s.zs);
+            const V bp = Vec<R>::make(s.beta_prev);
+            R rq[2] = {0, 0};
+            for (int64_t u = u_first; u < u_end; u += u_step) {
+                int64_t row;
+                V w;
+                if (ap(u, lane, zs, (const V*)a.r, row, w)) {
+                    const V qn = vcfma(bp, a.q[row], w);
+                    a.q[row] = qn;
+                    acc_bil(rq[0], rq[1], a.r[row], qn);
+                }
+            }
+            double v[2] = {rq[0], rq[1]};
+            block_sum_n<2>(v, s.scratch, s_part);
+            if (tid == 0) {
+                double* pa = a.partA + (size_t)cta * 4;
+                pa[0] = s_part[0]; pa[1] = s_part[1];
+                pa[2] = (double)s_flag[0];   // unconverged shifts of this CTA after the last phase C
+                pa[3] = (double)s_flag[1];   // a pi^k of this CTA became zero or non-finite
+            }
+        }
+        if (!grid_barrier(a.sync, epoch, a.debug_inject == 1 && cta == 0 && s.n == 3)) return;
+        grid_sum(a.partA, 4, 4, s.red);
+        if (tid == 0) {
+            const double2 rq = c2(s.red[0], s.red[1]);
+            const int active = s.n == 0 ? a.K : (int)s.red[2];
+            int st = 0;
+            if (s.n > 0 && s.red[3] != 0.0) st = SCOCG_ERR_BREAKDOWN;
+            else if (active == 0) st = SCOCG_OK;
+            else if (s.n >= a.max_iter) st = SCOCG_NOT_CONVERGED;
+            else if (cabs2(s.rho) == 0.0 || cabs2(rq) == 0.0 || !cfinite(rq)) st = SCOCG_ERR_BREAKDOWN;
+            else {
+                s.alpha = cdiv(s.rho, rq);
+                if (a.debug_inject == 2 && s.n == 3) s.alpha = c2(__longlong_as_double(0x7ff8000000000000ll), 0);
+                if (!cfinite(s.alpha)) st = SCOCG_ERR_BREAKDOWN;
+                s.shift_iters += active;
+            }
+            s.active = active;
+            s_flag[2] = st;
+        }
+        __syncthreads();
+        if (s_flag[2] != 0) { status = s_flag[2]; break; }
+
+        // ---- phase B: r_{n+1} = r_n - alpha_n q_n; partials rho, ||r||^2, c^T r
+        {
+            const V al = Vec<R>::make(s.alpha);
+            const V bp = Vec<R>::make(s.beta_prev);
+            const bool track_x = kMixed && s.replace_on;
+            R acc[5] = {0, 0, 0, 0, 0};
+            for (int64_t i = rbeg + tid; i < rend; i += kBlock) {
+                const V ro = a.r[i];
+                if constexpr (kMixed) {
+                    if (track_x) {
+                        // p_n = r_n + beta_{n-1} p_{n-1};  x_{n+1} = x_n + alpha_n p_n (compensated sum)
+                        const V p = vcfma(bp, a.p_seed[i], ro);
+                        a.p_seed[i] = p;
+                        const V inc = vcfma(al, p, vzero<V>());
+                        const V hi = a.x_hi[i];
+                        V lo = a.x_lo[i];
+                        const float sx = hi.x + inc.x, bx = sx - hi.x;
+                        const float sy = hi.y + inc.y, by = sy - hi.y;
+                        lo.x += (hi.x - (sx - bx)) + (inc.x - bx);
+                        lo.y += (hi.y - (sy - by)) + (inc.y - by);
+                        a.x_hi[i] = make_float2(sx, sy);
+                        a.x_lo[i] = lo;
+                    }
+                }
+                const V rn = vsub(ro, vcfma(al, a.q[i], vzero<V>()));
+                a.r[i] = rn;
+                acc_r(acc, rn, a.cvec ? a.cvec + i : nullptr);
+            }
+            __syncthreads();
+            finish_r_partials(a, acc, rbeg, rend, s, s_part, myB);
+        }
+        if (!grid_barrier(a.sync, epoch)) return;
+        grid_sum(a.partB, a.strideB, nred, s.red);
+        if (tid < M) {
+            s.cr_next[tid] = dense_proj ? c2(s.red[3 + 2 * tid], s.red[4 + 2 * tid])
+                                        : Vec<R>::wide(__ldcg(a.r + a.cidx[tid]));
+        }
+        __syncthreads();
+
+        // ---- phase C: per-shift scalar recurrences for this CTA's shifts
+        const double2 rho_new = c2(s.red[0], s.red[1]);
+        const double rnorm_new = sqrt(s.red[2]);
+        const bool seed_conv = a.tol > 0.0 && shift_resid(rnorm_new, c2(1, 0), s.bnorm) <= a.tol;
+        int my_active = 0, my_bad = 0;
+        if (owns && !a.S.frozen[k_own]) {
+            const int k = k_own;
+            const double2 pp = a.S.pi_prev[k], pc = a.S.pi_cur[k];
+            const double2 ratio = cdiv(pp, pc);
+            const double2 beta_k = cmul(cmul(ratio, ratio), s.beta_prev);
+            const double2 inv_pi = cdiv(c2(1, 0), pc);
+            const double2 t1 = cmul(s.alpha, a.S.sigma[k]);
+            const double2 t2 = cdiv(cmul(s.alpha, s.beta_prev), s.alpha_prev);
+            const double2 pn = cadd(cmul(cadd(c2(1, 0), t1), pc), cmul(t2, csub(pc, pp)));
+            if (cabs2(pn) == 0.0 || !cfinite(pn)) {
+                my_bad = 1;
+            } else {
+                const double2 ak = cmul(cdiv(pc, pn), s.alpha);
+                for (int m = 0; m < M; ++m) {
+                    const size_t o = (size_t)k * M + m;
+                    const double2 P = cadd(cmul(s.cr_cur[m], inv_pi), cmul(beta_k, a.S.P[o]));
+                    a.S.P[o] = P;
+                    a.S.X[o] = cadd(a.S.X[o], cmul(ak, P));
+                }
+                a.S.alpha_k[k] = ak;
+                a.S.pi_prev[k] = pc;
+                a.S.pi_cur[k] = pn;
+                const double res = shift_resid(rnorm_new, pn, s.bnorm);
+                a.S.resid[k] = res;
+                a.S.iters[k] = s.n + 1;
+                if (a.tol > 0.0 && res <= a.tol) a.S.frozen[k] = 1;
+                else my_active = 1;
+            }
+        }
+        const int cnt_active = __syncthreads_count(my_active);
+        const int any_bad = __syncthreads_or(my_bad);
+        if (tid == 0) {
+            s_flag[0] = cnt_active;
+            s_flag[1] = any_bad;
+            s.beta_prev = cdiv(rho_new, s.rho);
+            s.alpha_prev = s.alpha;
+            s.rho_prev = s.rho;
+            s.rho = rho_new;
+            s.rnorm = rnorm_new;
+            s.n += 1;
+        }
+        if (tid < M) s.cr_cur[tid] = s.cr_next[tid];
+        __syncthreads();
+
+        // ---- seed switching (Sec. III.C) once the seed has converged
+        if (seed_conv) {
+            // local candidate: the unconverged shift with the smallest |pi| (largest residual)
+            double best = INFINITY;
+            int arg = 0x7fffffff;
+            if (owns && !a.S.frozen[k_own]) { best = cabs_(a.S.pi_cur[k_own]); arg = k_own; }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oa = __shfl_xor_sync(0xffffffffu, arg, o);
+                if (ob < best || (ob == best && oa < arg)) { best = ob; arg = oa; }
+            }
+            if (lane == 0) { s_min[warp] = best; s_arg[warp] = arg; }
+            __syncthreads();
+            if (tid == 0) {
+                for (int w = 1; w < kWarps; ++w)
+                    if (s_min[w] < best || (s_min[w] == best && s_arg[w] < arg)) { best = s_min[w]; arg = s_arg[w]; }
+                double* pc = a.partC + (size_t)cta * 4;
+                pc[0] = (double)s_flag[0]; pc[1] = best; pc[2] = (double)arg; pc[3] = (double)s_flag[1];
+            }
+            if (!grid_barrier(a.sync, epoch)) return;
+            if (tid == 0) {
+                double tot = 0, bad = 0, gbest = INFINITY;
+                int garg = 0x7fffffff;
+                for (int c = 0; c < G; ++c) {
+                    const double* pc = a.partC + (size_t)c * 4;
+                    tot += __ldcg(pc); bad += __ldcg(pc + 3);
+                    const double b2 = __ldcg(pc + 1);
+                    const int a2 = (int)__ldcg(pc + 2);
+                    if (b2 < gbest || (b2 == gbest && a2 < garg)) { gbest = b2; garg = a2; }
+                }
+                int st = 0;
+                if (bad != 0.0) st = SCOCG_ERR_BREAKDOWN;
+                else if (tot == 0.0) st = SCOCG_OK;
+                else if (!a.allow_switch) st = SCOCG_ERR_BREAKDOWN;
+                s_flag[2] = st;
+                s_flag[3] = garg;
+            }
+            __syncthreads();
+            if (s_flag[2] != 0) { status = s_flag[2]; break; }
+            const int s2 = s_flag[3];
+            const double2 pin = __ldcg(a.S.pi_prev + s2);      // pi^{s'}_n
+            const double2 pin1 = __ldcg(a.S.pi_cur + s2);      // pi^{s'}_{n+1}
+            const double2 alpha_s2 = __ldcg(a.S.alpha_k + s2); // alpha^{s'}_n
+            // r' = r_{n+1} / pi'_{n+1};  q' = (r_n / pi'_n - r_{n+1} / pi'_{n+1}) / alpha'_n,
+            // with r_n = r_{n+1} + alpha_n q_n
+            const double2 inv1 = cdiv(c2(1, 0), pin1);
+            const double2 ca = cdiv(csub(cdiv(c2(1, 0), pin), inv1), alpha_s2);   // times r_{n+1}
+            const double2 cb = cdiv(cdiv(s.alpha_prev, pin), alpha_s2);           // times q_n
+            const V v_inv1 = Vec<R>::make(inv1), v_ca = Vec<R>::make(ca), v_cb = Vec<R>::make(cb);
+            for (int64_t i = rbeg + tid; i < rend; i += kBlock) {
+                const V ri = a.r[i], qi = a.q[i];
+                a.q[i] = vcfma(v_cb, qi, vcfma(v_ca, ri, vzero<V>()));
+                a.r[i] = vcfma(v_inv1, ri, vzero<V>());
+            }
+            if (owns) {
+                const int k = k_own;
+                if (k == s2) {
+                    a.S.pi_prev[k] = c2(1, 0); a.S.pi_cur[k] = c2(1, 0);
+                } else {
+                    a.S.pi_prev[k] = cdiv(a.S.pi_prev[k], pin);
+                    a.S.pi_cur[k] = cdiv(a.S.pi_cur[k], pin1);
+                }
+                a.S.sigma[k] = csub(a.z[k], a.z[s2]);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                const double2 ratio = cdiv(pin, pin1);
+                s.rho = cdiv(s.rho, cmul(pin1, pin1));
+                s.beta_prev = cmul(cmul(ratio, ratio), s.beta_prev);
+                s.alpha_prev = alpha_s2;
+                s.rnorm = s.rnorm / cabs_(pin1);
+                s.seed = s2;
+                s.zs = a.z[s2];
+                s.n_switch += 1;
+                s.replace_on = 0;        // the new seed's full solution is not tracked
+            }
+            if (tid < M) s.cr_cur[tid] = cmul(s.cr_cur[tid], inv1);
+            if (!grid_barrier(a.sync, epoch)) return;
+        }
+
+        // ---- MIXED: FP64 true-residual replacement r_{n+1} = b - (z_s - H) x_{n+1}
+        if constexpr (kMixed) {
+            if (s.replace_on && s.n % a.replace_every == 0) {
+                for (int64_t i = rbeg + tid; i < rend; i += kBlock) {
+                    const V hi = a.x_hi[i], lo = a.x_lo[i];
+                    a.xd[i] = c2((double)hi.x + (double)lo.x, (double)hi.y + (double)lo.y);
+                }
+                if (!grid_barrier(a.sync, epoch)) return;
+                const double2 zs = s.zs;
+                for (int64_t u = u_first; u < u_end; u += u_step) {
+                    int64_t row;
+                    double2 w;
+                    if (ap(u, lane, zs, (const double2*)a.xd, row, w)) {
+                        const double2 bi = a.b[row];
+                        a.r[row] = Vec<R>::make(c2(bi.x - w.x, bi.y - w.y));
+                    }
+                }
+                if (!grid_barrier(a.sync, epoch)) return;
+                r_partials(a, rbeg, rend, s, s_part, myB);
+                if (!grid_barrier(a.sync, epoch)) return;
+                grid_sum(a.partB, a.strideB, nred, s.red);
+                if (tid == 0) {
+                    s.rho = c2(s.red[0], s.red[1]);
+                    s.beta_prev = cdiv(s.rho, s.rho_prev);
+                    s.rnorm = sqrt(s.red[2]);
+                    s.n_replace += 1;
+                }
+                if (tid < M) {
+                    s.cr_cur[tid] = dense_proj ? c2(s.red[3 + 2 * tid], s.red[4 + 2 * tid])
+                                               : Vec<R>::wide(__ldcg(a.r + a.cidx[tid]));
+                }
+                __syncthreads();
+            }
+        }
+    }
+
+    // ------------------------------------------------------------ outputs
+    if (owns) {
+        for (int m = 0; m < M; ++m) a.G[(size_t)m * a.K + k_own] = a.S.X[(size_t)k_own * M + m];
+    }
+    if (cta == 0 && tid == 0) {
+        a.stats->iters = s.n;
+        a.stats->n_switch = s.n_switch;
+        a.stats->seed = s.seed;
+        a.stats->n_replace = s.n_replace;
+        a.stats->shift_iters = s.shift_iters;
+        a.stats->status = status;
+        atomicCAS(a.sync.status, 0, status);
+    }
+}
+
+}  // namespace scocg

@@ -1,0 +1,325 @@
+"""Thin ctypes binding of the C ABI in include/scocg.h (same entry-point names).
+
+Only argument marshalling happens here: device buffers are PyTorch CUDA
+tensors, host arrays are numpy arrays, and every step of the solve runs in the
+CUDA library.  There is no CPU fallback: if the library is missing, loading it
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from pathlib import Path
+
+import numpy as np
+
+LIB_PATH = Path(__file__).resolve().parent / "_build" / "libscocg.so"
+
+OK, NOT_CONVERGED = 0, 1
+ERR_INVALID, ERR_CUDA, ERR_OOM, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_UNSYMMETRIC = -1, -2, -3, -4, -5, -6
+FP64, MIXED = 0, 1
+
+EXPORTED = [
+    "scocg_create_csr", "scocg_create_hubbard", "scocg_dim", "scocg_set_opts", "scocg_apply",
+    "scocg_solve", "scocg_solve_full", "scocg_grad", "scocg_destroy", "scocg_strerror",
+    "scocg_hubbard_tables",
+]
+
+
+class ScocgError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+        self.code = code
+
+
+class c128(ctypes.Structure):
+    _fields_ = [("re", ctypes.c_double), ("im", ctypes.c_double)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("max_iter", ctypes.c_int), ("replace_every", ctypes.c_int),
+                ("seed", ctypes.c_int), ("no_switch", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("timeout_ms", ctypes.c_double), ("layout", ctypes.c_int), ("grid", ctypes.c_int),
+                ("debug_inject", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("n_switch", ctypes.c_int), ("seed_final", ctypes.c_int),
+                ("n_replace", ctypes.c_int), ("shift_iters", ctypes.c_longlong),
+                ("freeze_iter", ctypes.POINTER(ctypes.c_int)), ("resid", ctypes.POINTER(ctypes.c_double)),
+                ("seconds", ctypes.c_double), ("bytes_per_iter", ctypes.c_double)]
+
+
+@dataclass
+class SolveOptions:
+    precision: int = FP64
+    max_iter: int = 0
+    replace_every: int = 0
+    seed: int = -1
+    no_switch: int = 0
+    autotune: int = 0
+    timeout_ms: float = 0.0
+    layout: int = 0
+    grid: int = 0
+    debug_inject: int = 0
+
+    def c(self) -> Opts:
+        return Opts(self.precision, self.max_iter, self.replace_every, self.seed, self.no_switch,
+                    self.autotune, self.timeout_ms, self.layout, self.grid, self.debug_inject)
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not LIB_PATH.exists():
+            raise RuntimeError(f"CUDA library not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(str(LIB_PATH))
+        P, I64, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        D = ctypes.c_double
+        L.scocg_create_csr.argtypes = [ctypes.POINTER(P), I64, I64, P, P, P, I, ctypes.POINTER(Opts), P]
+        L.scocg_create_hubbard.argtypes = [ctypes.POINTER(P), I, I, I, D, D, D, I, ctypes.POINTER(Opts), P]
+        L.scocg_dim.argtypes = [P, ctypes.POINTER(I64)]
+        L.scocg_set_opts.argtypes = [P, ctypes.POINTER(Opts)]
+        L.scocg_apply.argtypes = [P, c128, P, P, I]
+        L.scocg_solve.argtypes = [P, P, I, P, I, P, P, I, D, P, ctypes.POINTER(Info)]
+        L.scocg_solve_full.argtypes = [P, P, I, P, D, P, ctypes.POINTER(Info)]
+        L.scocg_grad.argtypes = [P, P, I, P, I, P, P, I, D, P, P, ctypes.POINTER(Info)]
+        L.scocg_destroy.argtypes = [P]
+        L.scocg_destroy.restype = None
+        L.scocg_strerror.argtypes = [I]
+        L.scocg_strerror.restype = ctypes.c_char_p
+        L.scocg_hubbard_tables.argtypes = [P, I, ctypes.POINTER(ctypes.c_int32), P, P, P]
+        for name in EXPORTED:
+            if name not in ("scocg_destroy", "scocg_strerror"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().scocg_strerror(code).decode()
+
+
+def _check(code: int, where: str) -> int:
+    if code < 0:
+        raise ScocgError(code, where)
+    return code
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Handle:
+    """Owns one scocg_handle; destroyed by close() or garbage collection."""
+
+    def __init__(self, ptr: ctypes.c_void_p, stream):
+        self._ptr = ptr
+        self.stream = stream
+
+    @property
+    def ptr(self):
+        if self._ptr is None:
+            raise ValueError("handle closed")
+        return self._ptr
+
+    def close(self):
+        if self._ptr is not None and _lib is not None:
+            _lib.scocg_destroy(self._ptr)
+        self._ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def scocg_create_csr(rowptr, col, val, opts: SolveOptions | None = None, stream=None) -> Handle:
+    """scocg_create_csr: H from CSR arrays (numpy on the host, or torch CUDA tensors)."""
+    import torch
+    out = ctypes.c_void_p()
+    o = (opts or SolveOptions()).c()
+    if isinstance(rowptr, torch.Tensor):
+        rp = rowptr.to(torch.int64).contiguous(); cc = col.to(torch.int32).contiguous()
+        vv = val.to(torch.float64).contiguous()
+        n, nnz = rp.numel() - 1, cc.numel()
+        code = lib().scocg_create_csr(ctypes.byref(out), n, nnz, _dev(rp), _dev(cc), _dev(vv), 1,
+                                      ctypes.byref(o), _stream_ptr(stream))
+    else:
+        rp = np.ascontiguousarray(rowptr, dtype=np.int64); cc = np.ascontiguousarray(col, dtype=np.int32)
+        vv = np.ascontiguousarray(val, dtype=np.float64)
+        n, nnz = rp.size - 1, cc.size
+        code = lib().scocg_create_csr(ctypes.byref(out), n, nnz, rp.ctypes.data, cc.ctypes.data,
+                                      vv.ctypes.data, 0, ctypes.byref(o), _stream_ptr(stream))
+    _check(code, "scocg_create_csr")
+    h = Handle(out, stream)
+    h.n, h.nnz = n, nnz
+    return h
+
+
+def scocg_create_hubbard(L, n_up, n_dn, t, U, V, periodic=True, opts: SolveOptions | None = None,
+                         stream=None) -> Handle:
+    """scocg_create_hubbard: matrix-free extended Hubbard ring (Sec. IV.D)."""
+    out = ctypes.c_void_p()
+    o = (opts or SolveOptions()).c()
+    code = lib().scocg_create_hubbard(ctypes.byref(out), L, n_up, n_dn, t, U, V, int(bool(periodic)),
+                                      ctypes.byref(o), _stream_ptr(stream))
+    _check(code, "scocg_create_hubbard")
+    h = Handle(out, stream)
+    h.L = L
+    return h
+
+
+def scocg_dim(h: Handle) -> int:
+    n = ctypes.c_int64()
+    _check(lib().scocg_dim(h.ptr, ctypes.byref(n)), "scocg_dim")
+    return int(n.value)
+
+
+def scocg_set_opts(h: Handle, opts: SolveOptions) -> None:
+    o = opts.c()
+    _check(lib().scocg_set_opts(h.ptr, ctypes.byref(o)), "scocg_set_opts")
+
+
+def scocg_apply(h: Handle, z: complex, x, precision: int = FP64):
+    """y = (z I - H) x; x is a CUDA complex128 (FP64) or complex64 (MIXED) tensor."""
+    import torch
+    want = torch.complex64 if precision == MIXED else torch.complex128
+    if x.dtype != want or not x.is_cuda:
+        raise TypeError(f"x must be a CUDA {want} tensor")
+    x = x.contiguous()
+    y = torch.empty_like(x)
+    _check(lib().scocg_apply(h.ptr, c128(float(np.real(z)), float(np.imag(z))), _dev(x), _dev(y), precision),
+           "scocg_apply")
+    return y
+
+
+def _shifts(shifts):
+    z = np.ascontiguousarray(np.asarray(shifts, dtype=np.complex128))
+    return z, z.ctypes.data
+
+
+def _info_struct(nrhs, nshift):
+    it = np.zeros(nrhs * nshift, dtype=np.int32)
+    rs = np.zeros(nrhs * nshift, dtype=np.float64)
+    info = Info()
+    info.freeze_iter = it.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    info.resid = rs.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return info, it, rs
+
+
+def _info_dict(info, it, rs, nrhs, nshift, status):
+    return {"status": status, "iters": info.iters, "n_switch": info.n_switch, "seed_final": info.seed_final,
+            "n_replace": info.n_replace, "shift_iters": int(info.shift_iters), "seconds": info.seconds,
+            "bytes_per_iter": info.bytes_per_iter, "freeze_iter": it.reshape(nrhs, nshift),
+            "resid": rs.reshape(nrhs, nshift)}
+
+
+def scocg_solve(h: Handle, shifts, rhs, proj_idx=None, proj_vec=None, tol: float = 1e-10):
+    """scocg_solve: returns (G [nrhs][nproj][nshift] CUDA complex128 tensor, info dict).
+
+    rhs: CUDA complex128 [nrhs][N] (or [N]); proj_idx: host int [nrhs][nproj]
+    (or [nproj], shared); proj_vec: CUDA complex128 [nproj][N]."""
+    import torch
+    z, zp = _shifts(shifts)
+    K = z.size
+    rhs = rhs if rhs.dim() == 2 else rhs.reshape(1, -1)
+    if rhs.dtype != torch.complex128 or not rhs.is_cuda:
+        raise TypeError("rhs must be a CUDA complex128 tensor")
+    rhs = rhs.contiguous()
+    nrhs = rhs.shape[0]
+    pidx_p = pvec_p = None
+    if proj_idx is not None:
+        pidx = np.ascontiguousarray(np.asarray(proj_idx, dtype=np.int64))
+        if pidx.ndim == 1:
+            pidx = np.ascontiguousarray(np.broadcast_to(pidx, (nrhs, pidx.size)))
+        M = pidx.shape[1]
+        pidx_p = pidx.ctypes.data
+    else:
+        pv = proj_vec if proj_vec.dim() == 2 else proj_vec.reshape(1, -1)
+        if pv.dtype != torch.complex128 or not pv.is_cuda:
+            raise TypeError("proj_vec must be a CUDA complex128 tensor")
+        pv = pv.contiguous()
+        M = pv.shape[0]
+        pvec_p = _dev(pv)
+    G = torch.zeros((nrhs, M, K), dtype=torch.complex128, device=rhs.device)
+    info, it, rs = _info_struct(nrhs, K)
+    code = lib().scocg_solve(h.ptr, zp, K, _dev(rhs), nrhs, pidx_p, pvec_p, M, float(tol), _dev(G),
+                             ctypes.byref(info))
+    _check(code, "scocg_solve")
+    return G, _info_dict(info, it, rs, nrhs, K, code)
+
+
+def scocg_solve_full(h: Handle, shifts, rhs, tol: float = 1e-10):
+    """scocg_solve_full: returns (X [nshift][N] CUDA complex128 tensor, info dict)."""
+    import torch
+    z, zp = _shifts(shifts)
+    K = z.size
+    rhs = rhs.reshape(-1).contiguous()
+    X = torch.zeros((K, rhs.numel()), dtype=torch.complex128, device=rhs.device)
+    info, it, rs = _info_struct(1, K)
+    code = lib().scocg_solve_full(h.ptr, zp, K, _dev(rhs), float(tol), _dev(X), ctypes.byref(info))
+    _check(code, "scocg_solve_full")
+    return X, _info_dict(info, it, rs, 1, K, code)
+
+
+def scocg_grad(h: Handle, shifts, rhs, dL_dG, proj_idx=None, proj_vec=None, tol: float = 1e-10):
+    """scocg_grad: returns (dL/dval CUDA float64 [nnz], info dict)."""
+    import torch
+    z, zp = _shifts(shifts)
+    K = z.size
+    rhs = rhs.reshape(1, -1).contiguous()
+    pidx_p = pvec_p = None
+    if proj_idx is not None:
+        pidx = np.ascontiguousarray(np.asarray(proj_idx, dtype=np.int64).reshape(1, -1))
+        M = pidx.shape[1]
+        pidx_p = pidx.ctypes.data
+    else:
+        pv = (proj_vec if proj_vec.dim() == 2 else proj_vec.reshape(1, -1)).contiguous()
+        M = pv.shape[0]
+        pvec_p = _dev(pv)
+    g = dL_dG.to(torch.complex128).contiguous()
+    out = torch.zeros(int(h.nnz), dtype=torch.float64, device=rhs.device)
+    info, it, rs = _info_struct(1, K)
+    code = lib().scocg_grad(h.ptr, zp, K, _dev(rhs), 1, pidx_p, pvec_p, M, float(tol), _dev(g), _dev(out),
+                            ctypes.byref(info))
+    _check(code, "scocg_grad")
+    return out, _info_dict(info, it, rs, 1, K, code)
+
+
+def scocg_destroy(h: Handle) -> None:
+    h.close()
+
+
+def scocg_strerror(code: int) -> str:
+    return strerror(code)
+
+
+def scocg_hubbard_tables(h: Handle, spin: int):
+    """Per-spin basis tables built on the device: (states, hop_target, hop_sign)."""
+    d = ctypes.c_int32()
+    _check(lib().scocg_hubbard_tables(h.ptr, spin, ctypes.byref(d), None, None, None), "scocg_hubbard_tables")
+    D = d.value
+    states = np.zeros(D, dtype=np.uint32)
+    # slots per rank = 2L; recover L from the handle's dimension request below
+    L2 = _hub_slots(h)
+    tgt = np.zeros((D, L2), dtype=np.int32)
+    sgn = np.zeros((D, L2), dtype=np.int8)
+    _check(lib().scocg_hubbard_tables(h.ptr, spin, ctypes.byref(d), states.ctypes.data, tgt.ctypes.data,
+                                      sgn.ctypes.data), "scocg_hubbard_tables")
+    return states, tgt, sgn
+
+
+def _hub_slots(h: Handle) -> int:
+    return 2 * int(getattr(h, "L"))

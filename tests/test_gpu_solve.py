@@ -1,0 +1,245 @@
+"""GPU parity of the shifted-COCG path (through the C ABI) against the CPU oracle.
+
+Tolerances: FP64 mode 1e-10 relative on every G element (the target the
+method's FP64 recurrences reach); MIXED mode 1e-6 relative on G at the sizes
+below (complex64 vectors, FP64 scalars).  Fixed-iteration comparisons (tol = 0,
+max_iter = n) compare the same iterate on both sides; converged comparisons use
+a residual tolerance small enough that both sides sit far below 1e-10 from the
+exact G.
+"""
+import numpy as np
+import pytest
+
+from paper_0802_0748_gb300 import inputs
+from oracle import dense
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def S():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0802_0748_gb300 import scocg
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return scocg
+
+
+def relerr(a, b):
+    a = np.asarray(a); b = np.asarray(b)
+    return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300)))
+
+
+def cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def gpu_solve(S, h_csr, shifts, b, *, proj_idx=None, proj_vec=None, tol, opts=None):
+    h = S.scocg_create_csr(h_csr.rowptr, h_csr.col, h_csr.val, opts=opts)
+    try:
+        G, info = S.scocg_solve(h, shifts, cuda(b), proj_idx=proj_idx,
+                                proj_vec=None if proj_vec is None else cuda(proj_vec), tol=tol)
+        return G.cpu().numpy()[0], info
+    finally:
+        S.scocg_destroy(h)
+
+
+# ------------------------------------------------------------------ apply
+@pytest.mark.parametrize("layout", [0, 1])
+def test_apply_fp64_matches_oracle(S, oracle_mod, layout):
+    for h_csr in (inputs.anderson_csr(5, seed=3), inputs.chain_csr(1000)):
+        h = S.scocg_create_csr(h_csr.rowptr, h_csr.col, h_csr.val, opts=S.SolveOptions(layout=layout))
+        x = inputs.random_unit_complex(h_csr.n, 4)
+        z = 0.37 + 0.011j
+        y = S.scocg_apply(h, z, cuda(x)).cpu().numpy()
+        ref = oracle_mod.apply_shifted(h_csr.rowptr, h_csr.col, h_csr.val, z, x)
+        assert np.max(np.abs(y - ref)) <= 1e-14 * np.max(np.abs(ref))
+        S.scocg_destroy(h)
+
+
+def test_apply_mixed_matches_oracle(S, oracle_mod):
+    h_csr = inputs.anderson_csr(5, seed=3)
+    h = S.scocg_create_csr(h_csr.rowptr, h_csr.col, h_csr.val)
+    x = inputs.random_unit_complex(h_csr.n, 4).astype(np.complex64)
+    z = np.complex64(0.37 + 0.011j)
+    y = S.scocg_apply(h, complex(z), cuda(x), precision=S.MIXED).cpu().numpy()
+    ref = oracle_mod.apply_shifted(h_csr.rowptr, h_csr.col, h_csr.val, complex(z), x.astype(np.complex128))
+    assert np.max(np.abs(y - ref)) <= 1e-6 * np.max(np.abs(ref))
+    S.scocg_destroy(h)
+
+
+# ------------------------------------------------------------------ FP64 parity
+@pytest.mark.parametrize("layout", [0, 1])
+def test_fixed_iterations_match_oracle_anderson(S, oracle_mod, layout):
+    """Same iterate n on both sides: G_n element by element to 1e-10 (BSR4 and CSR layouts)."""
+    h = inputs.anderson_csr(6, seed=5)                     # 864 rows: 27 units of 32
+    b = inputs.random_unit_complex(h.n, 9)
+    C = np.stack([np.conj(b), inputs.random_unit_complex(h.n, 10), inputs.random_unit_complex(h.n, 11)])
+    shifts = np.linspace(-5, 5, 40) + 0.05j
+    seed = oracle_mod.default_seed(shifts)
+    for n_it in (1, 7, 60):
+        g, info = gpu_solve(S, h, shifts, b, proj_vec=C, tol=0.0,
+                            opts=S.SolveOptions(max_iter=n_it, layout=layout))
+        ref = oracle_mod.shifted_cocg(h.rowptr, h.col, h.val, shifts, b, proj_vec=C, tol=0.0,
+                                      max_iter=n_it, seed=seed)
+        assert info["status"] == 1 and info["iters"] == n_it
+        assert relerr(g, ref.G) < 1e-10, n_it
+
+
+def test_chain_converged_matches_closed_form_and_oracle(S, oracle_mod):
+    """Config-1 shape at L=1000 (ragged: 1000 = 31 units + 8 rows), unit projections."""
+    L = 1000
+    h = inputs.chain_csr(L)
+    shifts = np.linspace(-2.5, 2.5, 64) + 0.01j
+    b = np.zeros(L, complex); b[0] = 1
+    g, info = gpu_solve(S, h, shifts, b, proj_idx=[0, 3, L - 1], tol=1e-13)
+    assert info["status"] == 0
+    ref = oracle_mod.shifted_cocg(h.rowptr, h.col, h.val, shifts, b, proj_idx=[0, 3, L - 1], tol=1e-13)
+    assert relerr(g, ref.G) < 1e-10
+    assert relerr(g[0], dense.chain_g00_exact(L, -1.0, shifts)) < 1e-10
+
+
+def test_config1_full_size(S, oracle_mod):
+    """Open chain L=4096, b=e_0, 64 shifts in [-2.5, 2.5] + 0.01i, FP64 (tol 1e-10 and 1e-13)."""
+    wl = inputs.workload("chain", "full")
+    h = wl.csr
+    exact = dense.chain_g00_exact(4096, -1.0, wl.shifts)
+    g13, info13 = gpu_solve(S, h, wl.shifts, wl.rhs[0], proj_idx=[0], tol=1e-13)
+    assert info13["status"] == 0
+    assert relerr(g13[0], exact) < 1e-10
+    ref = oracle_mod.shifted_cocg(h.rowptr, h.col, h.val, wl.shifts, wl.rhs[0], proj_idx=[0], tol=1e-13)
+    assert relerr(g13, ref.G) < 1e-10
+    g10, info10 = gpu_solve(S, h, wl.shifts, wl.rhs[0], proj_idx=[0], tol=wl.tol)
+    assert info10["status"] == 0 and np.all(info10["resid"] <= wl.tol)
+    # stated tolerance: |dG| <= ||r|| / Im z
+    assert np.all(np.abs(g10[0] - exact) <= wl.tol / wl.shifts.imag * 1.001)
+
+
+def test_seed_switching_matches_oracle(S, oracle_mod):
+    h = inputs.anderson_csr(4, seed=17)
+    b = inputs.random_unit_complex(h.n, 11)
+    shifts = np.concatenate([[30.0 + 1.0j], np.linspace(-3, 3, 6) + 0.02j, [-25.0 + 0.5j]])
+    g, info = gpu_solve(S, h, shifts, b, proj_vec=[np.conj(b)], tol=1e-12, opts=S.SolveOptions(seed=0))
+    ref = oracle_mod.shifted_cocg(h.rowptr, h.col, h.val, shifts, b, proj_vec=[np.conj(b)], tol=1e-12,
+                                  seed=0)
+    assert info["status"] == 0 and info["n_switch"] == ref.n_switch >= 1
+    assert info["seed_final"] == ref.seed
+    assert relerr(g, ref.G) < 1e-10
+    exact = dense.green_dense(h.dense(), shifts, b, [np.conj(b)])
+    assert relerr(g, exact) < 1e-9
+
+
+def test_fixed_iterations_after_switch(S, oracle_mod):
+    h = inputs.anderson_csr(3, seed=23)
+    b = inputs.random_unit_complex(h.n, 13)
+    shifts = np.array([40.0 + 2.0j, -0.4 + 0.05j, 0.9 + 0.05j, 2.5 + 0.1j])
+    g, info = gpu_solve(S, h, shifts, b, proj_idx=[0, 5], tol=1e-9, opts=S.SolveOptions(seed=0, max_iter=30))
+    ref = oracle_mod.shifted_cocg(h.rowptr, h.col, h.val, shifts, b, proj_idx=[0, 5], tol=1e-9,
+                                  max_iter=30, seed=0)
+    assert info["n_switch"] == ref.n_switch >= 1
+    assert np.array_equal(info["freeze_iter"][0], ref.iters)
+    assert relerr(g, ref.G) < 1e-10
+
+
+def test_not_converged_and_zero_rhs(S, oracle_mod):
+    h = inputs.anderson_csr(3, seed=19)
+    b = inputs.random_unit_complex(h.n, 1)
+    g, info = gpu_solve(S, h, [0.1 + 0.001j, 0.5 + 0.001j], b, proj_idx=[0], tol=1e-14,
+                        opts=S.SolveOptions(max_iter=3))
+    assert info["status"] == 1 and info["iters"] == 3
+    ref = oracle_mod.shifted_cocg(h.rowptr, h.col, h.val, [0.1 + 0.001j, 0.5 + 0.001j], b, proj_idx=[0],
+                                  tol=1e-14, max_iter=3)
+    assert relerr(g, ref.G) < 1e-12
+    g0, info0 = gpu_solve(S, h, [0.1 + 0.1j], np.zeros(h.n, complex), proj_idx=[0], tol=1e-10)
+    assert info0["status"] == 0 and np.all(g0 == 0)
+
+
+def test_many_shifts_and_grid_override(S, oracle_mod):
+    """4096 shifts (more than the threads of one CTA) and a forced small grid."""
+    h = inputs.anderson_csr(4, seed=29)
+    b = inputs.random_unit_complex(h.n, 2)
+    shifts = np.linspace(-6, 6, 4096) + 0.1j
+    ref = oracle_mod.shifted_cocg(h.rowptr, h.col, h.val, shifts[::64], b, proj_idx=[7], tol=0.0,
+                                  max_iter=40, seed=0)
+    for grid in (0, 8):
+        g, info = gpu_solve(S, h, shifts, b, proj_idx=[7], tol=0.0,
+                            opts=S.SolveOptions(max_iter=40, grid=grid, seed=0))
+        assert relerr(g[:, ::64], ref.G) < 1e-10
+
+
+# ------------------------------------------------------------------ errors
+def test_invalid_inputs(S):
+    h = inputs.anderson_csr(3, seed=1)
+    bad = h.val.copy(); bad[5] += 1.0
+    with pytest.raises(S.ScocgError) as e:
+        S.scocg_create_csr(h.rowptr, h.col, bad)
+    assert e.value.code == S.ERR_UNSYMMETRIC
+    badc = h.col.copy(); badc[0] = h.n + 3
+    with pytest.raises(S.ScocgError) as e:
+        S.scocg_create_csr(h.rowptr, badc, h.val)
+    assert e.value.code == S.ERR_INVALID
+    hh = S.scocg_create_csr(h.rowptr, h.col, h.val)
+    b = cuda(inputs.random_unit_complex(h.n, 1))
+    with pytest.raises(S.ScocgError):
+        S.scocg_solve(hh, [0.1 + 0.1j], b, proj_idx=[h.n], tol=1e-8)
+    S.scocg_destroy(hh)
+
+
+def test_fault_injection_timeout_and_breakdown(S):
+    """A CTA that skips a barrier arrival ends the solve with TIMEOUT; a NaN
+    alpha ends it with BREAKDOWN; the handle and the context stay usable."""
+    h_csr = inputs.anderson_csr(4, seed=31)
+    b = cuda(inputs.random_unit_complex(h_csr.n, 3))
+    shifts = np.linspace(-2, 2, 8) + 0.05j
+    h = S.scocg_create_csr(h_csr.rowptr, h_csr.col, h_csr.val,
+                           opts=S.SolveOptions(debug_inject=1, timeout_ms=300.0))
+    with pytest.raises(S.ScocgError) as e:
+        S.scocg_solve(h, shifts, b, proj_idx=[0], tol=1e-10)
+    assert e.value.code == S.ERR_TIMEOUT
+    S.scocg_set_opts(h, S.SolveOptions(debug_inject=2))
+    with pytest.raises(S.ScocgError) as e:
+        S.scocg_solve(h, shifts, b, proj_idx=[0], tol=1e-10)
+    assert e.value.code == S.ERR_BREAKDOWN
+    S.scocg_set_opts(h, S.SolveOptions())
+    G, info = S.scocg_solve(h, shifts, b, proj_idx=[0], tol=1e-10)
+    assert info["status"] == 0
+    S.scocg_destroy(h)
+
+
+# ------------------------------------------------------------------ MIXED
+def test_mixed_matches_fp64_oracle(S, oracle_mod):
+    """complex64 vectors, FP32 H (exact), FP64 scalars: G within 1e-6 relative."""
+    h = inputs.anderson_csr(6, seed=5)
+    b = inputs.random_unit_complex(h.n, 9)
+    shifts = np.linspace(-5, 5, 32) + 0.05j
+    ref = oracle_mod.shifted_cocg(h.rowptr, h.col, h.val, shifts, b, proj_vec=[np.conj(b)], tol=1e-12)
+    for rep in (0, -1):
+        g, info = gpu_solve(S, h, shifts, b, proj_vec=[np.conj(b)], tol=1e-7,
+                            opts=S.SolveOptions(precision=S.MIXED, replace_every=rep))
+        assert info["status"] == 0
+        err = relerr(g, ref.G)
+        print(f"mixed replace_every={rep}: max rel err {err:.2e}, replacements {info['n_replace']}")
+        assert err < 1e-6
+
+
+# ------------------------------------------------------------------ full size, bench launch shape
+def test_config2_full_size_fixed_iterations(S, oracle_mod):
+    """64^3 x 4 Anderson (1,048,576 rows), 512 shifts, the bench's launch: after 25
+    iterations a 12-shift sample (with the seed) matches the oracle run on those shifts."""
+    wl = inputs.workload("anderson", "full", bounds=(-6.09, 6.47))
+    h = wl.csr
+    seed = oracle_mod.default_seed(wl.shifts)
+    sample = np.unique(np.concatenate([[seed], np.linspace(0, 511, 11).astype(int)]))
+    n_it = 25
+    g, info = gpu_solve(S, h, wl.shifts, wl.rhs[0], proj_vec=wl.proj_vec, tol=0.0,
+                        opts=S.SolveOptions(max_iter=n_it))
+    ref = oracle_mod.shifted_cocg(h.rowptr, h.col, h.val, wl.shifts[sample], wl.rhs[0],
+                                  proj_vec=wl.proj_vec, tol=0.0, max_iter=n_it,
+                                  seed=int(np.where(sample == seed)[0][0]))
+    assert relerr(g[:, sample], ref.G) < 1e-10
+    gm, infom = gpu_solve(S, h, wl.shifts, wl.rhs[0], proj_vec=wl.proj_vec, tol=0.0,
+                          opts=S.SolveOptions(max_iter=n_it, precision=S.MIXED))
+    assert relerr(gm[:, sample], ref.G) < 1e-5
