@@ -29,24 +29,35 @@ def _inputs() -> list[Path]:
     return files
 
 
-def up_to_date() -> bool:
-    if not LIB.exists():
+def lib_path(checked: bool = False) -> Path:
+    return BUILD / "checked" / "libscocg.so" if checked else LIB
+
+
+def up_to_date(checked: bool = False) -> bool:
+    lib = lib_path(checked)
+    if not lib.exists():
         return False
-    t = LIB.stat().st_mtime
+    t = lib.stat().st_mtime
     return all(f.stat().st_mtime <= t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False) -> Path:
-    """Compile every CUDA source for sm_103a and link the shared library."""
-    if not force and up_to_date():
-        return LIB
-    obj_dir = BUILD / "obj"
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> Path:
+    """Compile every CUDA source for sm_103a and link the shared library.
+
+    checked=True builds the bounds-checked variant (-DSCOCG_CHECKED) into
+    _build/checked/: every data-dependent index is tested and a bad one is
+    reported by the solve instead of being used."""
+    lib = lib_path(checked)
+    if not force and up_to_date(checked):
+        return lib
+    obj_dir = lib.parent / "obj"
     obj_dir.mkdir(parents=True, exist_ok=True)
     nvcc = _nvcc()
+    extra = ["-DSCOCG_CHECKED"] if checked else []
 
     def compile_one(src: str) -> Path:
         out = obj_dir / (Path(src).stem + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", str(CSRC / src), "-o", str(out)]
+        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", str(CSRC / src), "-o", str(out)]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -56,13 +67,13 @@ def build(force: bool = False, verbose: bool = False) -> Path:
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB.with_suffix(f".{os.getpid()}.tmp")
+    tmp = lib.with_suffix(f".{os.getpid()}.tmp")
     cmd = [nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", *map(str, objs), "-o", str(tmp)]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -295,6 +295,7 @@ static int solve_one_rhs(scocg_ctx* h, const double2* d_z, int K, int seed, cons
     a.stats = &h->d_ctrl->stats;
     a.G = G;
     a.debug_inject = h->opts.debug_inject;
+    a.dbg = h->d_ctrl->dbg;
     cudaError_t e = cudaMemsetAsync(h->d_ctrl, 0, sizeof(Ctrl), h->stream);
     if (e != cudaSuccess) return cuda_status(e);
     if (h->kind == HandleKind::kHubbard) e = hubbard_launch_solve(a, h->hub, grid, h->stream);
@@ -340,43 +341,43 @@ extern "C" int scocg_solve(scocg_handle h, const scocg_c128* shifts, int nshift,
     if ((int64_t)grid * kBlock < K) return SCOCG_ERR_INVALID;
     const int strideB = 3 + 2 * M + 1;
 
-    // workspace layout
+    // workspace layout: the same sequence of pieces is measured, then carved
     const size_t vbytes = (mixed ? sizeof(float2) : sizeof(double2)) * (size_t)n;
-    size_t need = 0;
-    auto add = [&](size_t b) { need += ((b + 255) / 256) * 256; };
-    add(vbytes); add(vbytes);                                  // r, q
-    if (mixed) { add(vbytes); add(vbytes); add(vbytes); add(sizeof(double2) * n); }
-    if (mixed && proj_vec) add(sizeof(float2) * (size_t)n * M);
-    add(sizeof(int64_t) * M);
-    add(sizeof(double2) * K);                                  // z
-    add(sizeof(double2) * K * 4); add(sizeof(double2) * (size_t)K * M * 2);
-    add(sizeof(int) * K * 2); add(sizeof(double) * K);
-    add(sizeof(double) * grid * 4); add(sizeof(double) * grid * strideB); add(sizeof(double) * grid * 4);
-    cudaError_t e = h->ws.reserve(need);
-    if (e != cudaSuccess) return cuda_status(e);
-    Workspace& W = h->ws;
-    void* r = W.get(vbytes);
-    void* q = W.get(vbytes);
-    void *ps = nullptr, *xh = nullptr, *xl = nullptr;
+    void *r = nullptr, *q = nullptr, *ps = nullptr, *xh = nullptr, *xl = nullptr, *cvec = nullptr;
     double2* xd = nullptr;
-    if (mixed) { ps = W.get(vbytes); xh = W.get(vbytes); xl = W.get(vbytes); xd = (double2*)W.get(sizeof(double2) * n); }
-    void* cvec = nullptr;
-    if (mixed && proj_vec) cvec = W.get(sizeof(float2) * (size_t)n * M);
-    int64_t* d_cidx = (int64_t*)W.get(sizeof(int64_t) * M);
-    double2* d_z = (double2*)W.get(sizeof(double2) * K);
-    ShiftState S;
-    S.pi_prev = (double2*)W.get(sizeof(double2) * K);
-    S.pi_cur = (double2*)W.get(sizeof(double2) * K);
-    S.sigma = (double2*)W.get(sizeof(double2) * K);
-    S.alpha_k = (double2*)W.get(sizeof(double2) * K);
-    S.P = (double2*)W.get(sizeof(double2) * (size_t)K * M);
-    S.X = (double2*)W.get(sizeof(double2) * (size_t)K * M);
-    S.frozen = (int*)W.get(sizeof(int) * K);
-    S.iters = (int*)W.get(sizeof(int) * K);
-    S.resid = (double*)W.get(sizeof(double) * K);
-    double* partA = (double*)W.get(sizeof(double) * grid * 4);
-    double* partB = (double*)W.get(sizeof(double) * grid * strideB);
-    double* partC = (double*)W.get(sizeof(double) * grid * 4);
+    int64_t* d_cidx = nullptr;
+    double2* d_z = nullptr;
+    ShiftState S{};
+    double *partA = nullptr, *partB = nullptr, *partC = nullptr;
+    auto carve = [&](Carver& c) {
+        r = c.take(vbytes);
+        q = c.take(vbytes);
+        if (mixed) {
+            ps = c.take(vbytes); xh = c.take(vbytes); xl = c.take(vbytes);
+            xd = (double2*)c.take(sizeof(double2) * n);
+        }
+        if (mixed && proj_vec) cvec = c.take(sizeof(float2) * (size_t)n * M);
+        d_cidx = (int64_t*)c.take(sizeof(int64_t) * M);
+        d_z = (double2*)c.take(sizeof(double2) * K);
+        S.pi_prev = (double2*)c.take(sizeof(double2) * K);
+        S.pi_cur = (double2*)c.take(sizeof(double2) * K);
+        S.sigma = (double2*)c.take(sizeof(double2) * K);
+        S.alpha_k = (double2*)c.take(sizeof(double2) * K);
+        S.P = (double2*)c.take(sizeof(double2) * (size_t)K * M);
+        S.X = (double2*)c.take(sizeof(double2) * (size_t)K * M);
+        S.frozen = (int*)c.take(sizeof(int) * K);
+        S.iters = (int*)c.take(sizeof(int) * K);
+        S.resid = (double*)c.take(sizeof(double) * K);
+        partA = (double*)c.take(sizeof(double) * grid * 4);
+        partB = (double*)c.take(sizeof(double) * grid * strideB);
+        partC = (double*)c.take(sizeof(double) * grid * kPartC);
+    };
+    Carver measure{nullptr, 0};
+    carve(measure);
+    cudaError_t e = h->ws.reserve(measure.off);
+    if (e != cudaSuccess) return cuda_status(e);
+    Carver cut{static_cast<char*>(h->ws.base), 0};
+    carve(cut);
 
     e = cudaMemcpyAsync(d_z, shifts, sizeof(double2) * K, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && mixed && proj_vec) {
@@ -417,6 +418,12 @@ extern "C" int scocg_solve(scocg_handle h, const scocg_c128* shifts, int nshift,
         if (e == cudaSuccess) e = cudaMemcpyAsync(h_resid.data(), S.resid, sizeof(double) * K, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { worst = cuda_status(e); break; }
+        if (c.dbg[0]) {
+            std::fprintf(stderr, "scocg checked build: out-of-range index at site %llu: %lld (limit %lld)\n",
+                         c.dbg[1], (long long)c.dbg[2], (long long)c.dbg[3]);
+            worst = SCOCG_ERR_INVALID;
+            break;
+        }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev0, ev1);
         total_ms += ms;

@@ -16,6 +16,19 @@ struct Ctrl {
     int status;
     int pad;
     SolveStats stats;
+    unsigned long long dbg[4];   // checked builds: (flag, site, index, limit)
+};
+
+// Sequential carving of a buffer into 256-byte aligned pieces; with a null
+// base it only measures (every piece returns nullptr, `off` is the total).
+struct Carver {
+    char* base;
+    size_t off;
+    void* take(size_t bytes) {
+        void* p = base ? base + off : nullptr;
+        off += ((bytes + 255) / 256) * 256;
+        return p;
+    }
 };
 
 // Grow-only device workspace carved into 256-byte aligned pieces.

@@ -146,6 +146,22 @@ __device__ __forceinline__ void set_error(int* status, int code) {
     if (old == 1) atomicCAS(status, 1, code);
 }
 
+// ---------------------------------------------------------------- checked build
+// With -DSCOCG_CHECKED every data-dependent index is tested before use: a bad
+// one is recorded in dbg[0..3] = (1, site, index, limit) and the access is
+// skipped.  Without it the test compiles away.
+#ifdef SCOCG_CHECKED
+__device__ __forceinline__ bool chk(unsigned long long* dbg, int site, long long idx, long long lim) {
+    if (idx >= 0 && idx < lim) return true;
+    if (dbg && atomicCAS(dbg, 0ull, 1ull) == 0ull) {
+        dbg[1] = (unsigned long long)site; dbg[2] = (unsigned long long)idx; dbg[3] = (unsigned long long)lim;
+    }
+    return false;
+}
+#else
+__device__ __forceinline__ bool chk(unsigned long long*, int, long long, long long) { return true; }
+#endif
+
 // ---------------------------------------------------------------- reductions
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

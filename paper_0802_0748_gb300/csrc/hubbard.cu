@@ -99,6 +99,7 @@ struct ApplyHubbard {
     int S, D_up, D_dn, L, ring;
     double t, U, V;
     int64_t n;
+    unsigned long long* dbg;
 
     __device__ __forceinline__ uint32_t partner(uint32_t x) const {
         // bit i of the result = occupation of the bond partner i + 1 (and 0 for i = L - 1 on a ring)
@@ -130,6 +131,7 @@ struct ApplyHubbard {
         for (int j = 0; j < S; ++j) {
             const int e = hop_dn[(size_t)d * S + j];
             if (e < 0) break;
+            if (!chk(dbg, 20, e >> 1, D_dn)) continue;
             const VV xv = xrow[e >> 1];
             const T c = (e & 1) ? -tt : tt;
             acc.x += c * xv.x; acc.y += c * xv.y;
@@ -137,6 +139,7 @@ struct ApplyHubbard {
         for (int j = 0; j < S; ++j) {
             const int e = hop_up[(size_t)u * S + j];
             if (e < 0) break;
+            if (!chk(dbg, 21, e >> 1, D_up)) continue;
             const VV xv = x[(size_t)(e >> 1) * D_dn + d];
             const T c = (e & 1) ? -tt : tt;
             acc.x += c * xv.x; acc.y += c * xv.y;
@@ -158,6 +161,7 @@ static ApplyHubbard<R> make_apply(const Hubbard& hb) {
     ap.ring = hb.periodic && hb.L >= 3;
     ap.t = hb.t; ap.U = hb.U; ap.V = hb.V;
     ap.n = (int64_t)hb.D_up * hb.D_dn;
+    ap.dbg = nullptr;
     return ap;
 }
 
@@ -173,6 +177,7 @@ int hubbard_max_ctas(const Hubbard& hb, bool mixed, int num_sms) {
 template <typename R>
 cudaError_t hubbard_launch_solve(const SolveArgs<R>& a, const Hubbard& hb, int grid, cudaStream_t st) {
     ApplyHubbard<R> ap = make_apply<R>(hb);
+    ap.dbg = a.dbg;
     void* args[] = {(void*)&a, (void*)&ap};
     return cudaLaunchCooperativeKernel((const void*)cocg_persistent<R, ApplyHubbard<R>>, dim3(grid), dim3(kBlock),
                                        args, 0, st);

@@ -54,19 +54,19 @@ template <typename R>
 cudaError_t launch_solve(const SolveArgs<R>& a, const Layout& h, int grid, cudaStream_t st) {
     switch (h.kind) {
         case LayoutKind::kBsr4: {
-            ApplyBSR4<R> ap{h.unit_off, h.bcol, pick<R>(h, h.bval64, h.bval32), h.n};
+            ApplyBSR4<R> ap{h.unit_off, h.bcol, pick<R>(h, h.bval64, h.bval32), h.n, h.nslots, a.dbg};
             return coop_launch(a, ap, grid, st);
         }
         case LayoutKind::kCsr1: {
-            ApplyCSR<R, 1> ap{h.rowptr, h.col, pick<R>(h, h.val64, h.val32), h.n};
+            ApplyCSR<R, 1> ap{h.rowptr, h.col, pick<R>(h, h.val64, h.val32), h.n, h.nnz, a.dbg};
             return coop_launch(a, ap, grid, st);
         }
         case LayoutKind::kCsr4: {
-            ApplyCSR<R, 4> ap{h.rowptr, h.col, pick<R>(h, h.val64, h.val32), h.n};
+            ApplyCSR<R, 4> ap{h.rowptr, h.col, pick<R>(h, h.val64, h.val32), h.n, h.nnz, a.dbg};
             return coop_launch(a, ap, grid, st);
         }
         case LayoutKind::kCsr16: {
-            ApplyCSR<R, 16> ap{h.rowptr, h.col, pick<R>(h, h.val64, h.val32), h.n};
+            ApplyCSR<R, 16> ap{h.rowptr, h.col, pick<R>(h, h.val64, h.val32), h.n, h.nnz, a.dbg};
             return coop_launch(a, ap, grid, st);
         }
     }
@@ -97,13 +97,13 @@ template <typename R, typename VV>
 static cudaError_t apply_dispatch(const Layout& h, int64_t nunits, VV zs, const VV* x, VV* y, cudaStream_t st) {
     switch (h.kind) {
         case LayoutKind::kBsr4:
-            return apply_one<R, VV>(ApplyBSR4<R>{h.unit_off, h.bcol, pick<R>(h, h.bval64, h.bval32), h.n}, nunits, zs, x, y, st);
+            return apply_one<R, VV>(ApplyBSR4<R>{h.unit_off, h.bcol, pick<R>(h, h.bval64, h.bval32), h.n, h.nslots, nullptr}, nunits, zs, x, y, st);
         case LayoutKind::kCsr1:
-            return apply_one<R, VV>(ApplyCSR<R, 1>{h.rowptr, h.col, pick<R>(h, h.val64, h.val32), h.n}, nunits, zs, x, y, st);
+            return apply_one<R, VV>(ApplyCSR<R, 1>{h.rowptr, h.col, pick<R>(h, h.val64, h.val32), h.n, h.nnz, nullptr}, nunits, zs, x, y, st);
         case LayoutKind::kCsr4:
-            return apply_one<R, VV>(ApplyCSR<R, 4>{h.rowptr, h.col, pick<R>(h, h.val64, h.val32), h.n}, nunits, zs, x, y, st);
+            return apply_one<R, VV>(ApplyCSR<R, 4>{h.rowptr, h.col, pick<R>(h, h.val64, h.val32), h.n, h.nnz, nullptr}, nunits, zs, x, y, st);
         case LayoutKind::kCsr16:
-            return apply_one<R, VV>(ApplyCSR<R, 16>{h.rowptr, h.col, pick<R>(h, h.val64, h.val32), h.n}, nunits, zs, x, y, st);
+            return apply_one<R, VV>(ApplyCSR<R, 16>{h.rowptr, h.col, pick<R>(h, h.val64, h.val32), h.n, h.nnz, nullptr}, nunits, zs, x, y, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -27,6 +27,8 @@
 
 namespace scocg {
 
+constexpr int kPartC = 10;   // active, best |pi|, arg, bad, pi_prev, pi_cur, alpha_k of arg
+
 struct ShiftState {          // device arrays, [K] or [K][M]
     double2* pi_prev;
     double2* pi_cur;
@@ -76,6 +78,8 @@ struct ApplyCSR {
     const int* col;
     const R* val;
     int64_t n;
+    int64_t nnz;
+    unsigned long long* dbg;
 
     template <typename VV>
     __device__ __forceinline__ bool operator()(int64_t unit, int lane, VV zs, const VV* x,
@@ -85,7 +89,11 @@ struct ApplyCSR {
         VV acc = vzero<VV>();
         if (row < n) {
             const int e0 = rowptr[row], e1 = rowptr[row + 1];
-            for (int e = e0 + l; e < e1; e += LPR) cfma_r(acc, ld_stream(val + e), x[ld_stream(col + e)]);
+            if (chk(dbg, 1, e0, nnz + 1) && chk(dbg, 2, e1, nnz + 1))
+                for (int e = e0 + l; e < e1; e += LPR) {
+                    const int c = ld_stream(col + e);
+                    if (chk(dbg, 3, c, n)) cfma_r(acc, ld_stream(val + e), x[c]);
+                }
         }
 #pragma unroll
         for (int o = LPR / 2; o > 0; o >>= 1) {
@@ -112,6 +120,8 @@ struct ApplyBSR4 {
     const int* bcol;         // [slots][8]
     const R* bval;           // [slots][8][4][4]
     int64_t n;
+    int64_t nslots;
+    unsigned long long* dbg;
 
     __device__ __forceinline__ static void load_row(const float* p, float (&v)[4]) {
         const float4 t = ld_stream(reinterpret_cast<const float4*>(p));
@@ -124,8 +134,8 @@ struct ApplyBSR4 {
     }
 
     template <typename VV>
-    __device__ __forceinline__ static void block_fma(VV& acc, int cb, const R (&v)[4], const VV* x) {
-        if (cb >= 0) {
+    __device__ __forceinline__ void block_fma(VV& acc, int cb, const R (&v)[4], const VV* x) const {
+        if (cb >= 0 && chk(dbg, 5, (long long)cb * 4 + 3, n)) {
             VV xv[4];
             load4(x + (size_t)cb * 4, xv);
 #pragma unroll
@@ -138,7 +148,8 @@ struct ApplyBSR4 {
                                                int64_t& row, VV& w) const {
         const int br = lane >> 2, rr = lane & 3;
         row = unit * 32 + lane;
-        const int s0 = unit_off[unit], s1 = unit_off[unit + 1];
+        int s0 = unit_off[unit], s1 = unit_off[unit + 1];
+        if (!chk(dbg, 4, s1, nslots + 1) || !chk(dbg, 4, s0, s1 + 1)) s0 = s1 = 0;
         VV acc = vzero<VV>();
         int s = s0;
         for (; s + 4 <= s1; s += 4) {                 // four slots in flight
@@ -196,12 +207,13 @@ struct SolveArgs {
     // per-CTA partials
     double* partA;             // [grid][4]
     double* partB;             // [grid][strideB]
-    double* partC;             // [grid][4]
+    double* partC;             // [grid][kPartC]
     int strideB;
     GridSync sync;
     SolveStats* stats;
     double2* G;                // out [nproj][K] for this right-hand side
     int debug_inject;
+    unsigned long long* dbg;   // checked builds: first out-of-range index
 };
 
 // Shared per-CTA copy of the seed scalars; every CTA holds identical values.

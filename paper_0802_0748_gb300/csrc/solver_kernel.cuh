@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
         }
         double v1[1] = {nb};
         block_sum_n<1>(v1, s.scratch, s_part);
-        if (tid == 0) a.partC[(size_t)cta * 4] = s_part[0];
+        if (tid == 0) a.partC[(size_t)cta * kPartC] = s_part[0];
         __syncthreads();
         r_partials(a, rbeg, rend, s, s_part, myB);
         if (owns) {
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
         if (tid < 4) s_flag[tid] = 0;
         if (!grid_barrier(a.sync, epoch)) return;
         grid_sum(a.partB, a.strideB, nred, s.red);
-        grid_sum(a.partC, 4, 1, s.red + nred);
+        grid_sum(a.partC, kPartC, 1, s.red + nred);
         if (tid == 0) {
             s.rho = c2(s.red[0], s.red[1]);
             s.bnorm = sqrt(s.red[nred]);
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
         }
         if (tid < M) {
             s.cr_cur[tid] = dense_proj ? c2(s.red[3 + 2 * tid], s.red[4 + 2 * tid])
-                                       : Vec<R>::wide(__ldcg(a.r + a.cidx[tid]));
+                                       : (chk(a.dbg, 12, a.cidx[tid], a.n) ? Vec<R>::wide(__ldcg(a.r + a.cidx[tid])) : c2(0, 0));
         }
         __syncthreads();
         if (s.bnorm == 0.0) {                 // b = 0: x = 0 solves every shift
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
         grid_sum(a.partB, a.strideB, nred, s.red);
         if (tid < M) {
             s.cr_next[tid] = dense_proj ? c2(s.red[3 + 2 * tid], s.red[4 + 2 * tid])
-                                        : Vec<R>::wide(__ldcg(a.r + a.cidx[tid]));
+                                        : (chk(a.dbg, 12, a.cidx[tid], a.n) ? Vec<R>::wide(__ldcg(a.r + a.cidx[tid])) : c2(0, 0));
         }
         __syncthreads();
 
@@ -301,33 +301,43 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
             if (tid == 0) {
                 for (int w = 1; w < kWarps; ++w)
                     if (s_min[w] < best || (s_min[w] == best && s_arg[w] < arg)) { best = s_min[w]; arg = s_arg[w]; }
-                double* pc = a.partC + (size_t)cta * 4;
+                // the candidate's recurrence values travel with it, so that no CTA
+                // reads them after their owner has rebased them below
+                double* pc = a.partC + (size_t)cta * kPartC;
                 pc[0] = (double)s_flag[0]; pc[1] = best; pc[2] = (double)arg; pc[3] = (double)s_flag[1];
+                if (arg < a.K && chk(a.dbg, 10, arg, a.K)) {
+                    const double2 pp = a.S.pi_prev[arg], pq = a.S.pi_cur[arg], ak = a.S.alpha_k[arg];
+                    pc[4] = pp.x; pc[5] = pp.y; pc[6] = pq.x; pc[7] = pq.y; pc[8] = ak.x; pc[9] = ak.y;
+                }
             }
             if (!grid_barrier(a.sync, epoch)) return;
+            __shared__ double s_sw[6];
             if (tid == 0) {
                 double tot = 0, bad = 0, gbest = INFINITY;
-                int garg = 0x7fffffff;
+                int garg = 0x7fffffff, gc = -1;
                 for (int c = 0; c < G; ++c) {
-                    const double* pc = a.partC + (size_t)c * 4;
+                    const double* pc = a.partC + (size_t)c * kPartC;
                     tot += __ldcg(pc); bad += __ldcg(pc + 3);
                     const double b2 = __ldcg(pc + 1);
                     const int a2 = (int)__ldcg(pc + 2);
-                    if (b2 < gbest || (b2 == gbest && a2 < garg)) { gbest = b2; garg = a2; }
+                    if (b2 < gbest || (b2 == gbest && a2 < garg)) { gbest = b2; garg = a2; gc = c; }
                 }
                 int st = 0;
                 if (bad != 0.0) st = SCOCG_ERR_BREAKDOWN;
                 else if (tot == 0.0) st = SCOCG_OK;
                 else if (!a.allow_switch) st = SCOCG_ERR_BREAKDOWN;
+                else if (gc < 0 || !chk(a.dbg, 11, garg, a.K)) st = SCOCG_ERR_BREAKDOWN;
+                else
+                    for (int j = 0; j < 6; ++j) s_sw[j] = __ldcg(a.partC + (size_t)gc * kPartC + 4 + j);
                 s_flag[2] = st;
                 s_flag[3] = garg;
             }
             __syncthreads();
             if (s_flag[2] != 0) { status = s_flag[2]; break; }
             const int s2 = s_flag[3];
-            const double2 pin = __ldcg(a.S.pi_prev + s2);      // pi^{s'}_n
-            const double2 pin1 = __ldcg(a.S.pi_cur + s2);      // pi^{s'}_{n+1}
-            const double2 alpha_s2 = __ldcg(a.S.alpha_k + s2); // alpha^{s'}_n
+            const double2 pin = c2(s_sw[0], s_sw[1]);        // pi^{s'}_n
+            const double2 pin1 = c2(s_sw[2], s_sw[3]);       // pi^{s'}_{n+1}
+            const double2 alpha_s2 = c2(s_sw[4], s_sw[5]);   // alpha^{s'}_n
             // r' = r_{n+1} / pi'_{n+1};  q' = (r_n / pi'_n - r_{n+1} / pi'_{n+1}) / alpha'_n,
             // with r_n = r_{n+1} + alpha_n q_n
             const double2 inv1 = cdiv(c2(1, 0), pin1);
@@ -394,7 +404,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
                 }
                 if (tid < M) {
                     s.cr_cur[tid] = dense_proj ? c2(s.red[3 + 2 * tid], s.red[4 + 2 * tid])
-                                               : Vec<R>::wide(__ldcg(a.r + a.cidx[tid]));
+                                               : (chk(a.dbg, 12, a.cidx[tid], a.n) ? Vec<R>::wide(__ldcg(a.r + a.cidx[tid])) : c2(0, 0));
                 }
                 __syncthreads();
             }

@@ -13,7 +13,11 @@ from pathlib import Path
 
 import numpy as np
 
-LIB_PATH = Path(__file__).resolve().parent / "_build" / "libscocg.so"
+import os
+
+# SCOCG_LIB=checked selects the bounds-checked build (see build.py)
+LIB_PATH = Path(__file__).resolve().parent / "_build" / (
+    "checked/libscocg.so" if os.environ.get("SCOCG_LIB") == "checked" else "libscocg.so")
 
 OK, NOT_CONVERGED = 0, 1
 ERR_INVALID, ERR_CUDA, ERR_OOM, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_UNSYMMETRIC = -1, -2, -3, -4, -5, -6
