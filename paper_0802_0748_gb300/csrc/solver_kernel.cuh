@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
             const double2 t1 = cmul(s.alpha, a.S.sigma[k]);
             const double2 t2 = cdiv(cmul(s.alpha, s.beta_prev), s.alpha_prev);
             const double2 pn = cadd(cmul(cadd(c2(1, 0), t1), pc), cmul(t2, csub(pc, pp)));
-            if (cabs2(pn) == 0.0 || !cfinite(pn)) {
+            if (cabs2(pn) == 0.0 || !cfinite(pn) || !isfinite(cabs_(pn))) {
                 my_bad = 1;
             } else {
                 const double2 ak = cmul(cdiv(pc, pn), s.alpha);

@@ -303,3 +303,15 @@ def test_iterates_after_switch_equal_plain_cocg(oracle_mod):
         d = oracle_mod.shifted_cocg(h.rowptr, h.col, h.val, shifts[k:k + 1], b, proj_idx=[0],
                                     tol=0.0, max_iter=n, seed=0, want_x=True)
         assert np.linalg.norm(a.X[k] - d.X[0]) < 1e-9 * np.linalg.norm(d.X[0])
+
+
+def test_fixed_iterates_are_seed_independent_before_ritz_convergence(oracle_mod):
+    """Early iterates do not depend on the seed (same Krylov space, Eq. inv_KS)."""
+    h = small_anderson(L=6, seed=5)
+    b = inputs.random_unit_complex(h.n, 9)
+    shifts = np.linspace(-5, 5, 12) + 0.05j
+    a = oracle_mod.shifted_cocg(h.rowptr, h.col, h.val, shifts, b, proj_vec=[np.conj(b)], tol=0.0,
+                                max_iter=20, seed=3)
+    c = oracle_mod.shifted_cocg(h.rowptr, h.col, h.val, shifts, b, proj_vec=[np.conj(b)], tol=0.0,
+                                max_iter=20, seed=8)
+    assert relerr(a.G, c.G) < 1e-10
