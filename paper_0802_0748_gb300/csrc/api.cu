@@ -267,6 +267,11 @@ extern "C" int scocg_apply(scocg_handle h, scocg_c128 z, const void* x, void* y,
 // ---------------------------------------------------------------- solve
 namespace scocg {
 
+#ifdef SCOCG_CHECKED
+static int* g_trace = nullptr;   // host-mapped flight recorder of the checked build
+static int g_trace_n = 0;
+#endif
+
 template <typename R>
 static int solve_one_rhs(scocg_ctx* h, const double2* d_z, int K, int seed, const double2* b,
                          const int64_t* d_cidx, const void* cvec, int M, double tol, double2* G,
@@ -296,10 +301,36 @@ static int solve_one_rhs(scocg_ctx* h, const double2* d_z, int K, int seed, cons
     a.G = G;
     a.debug_inject = h->opts.debug_inject;
     a.dbg = h->d_ctrl->dbg;
+    a.trace = nullptr;
+#ifdef SCOCG_CHECKED
+    // flight recorder: per CTA (iteration, phase) in host-mapped memory, printed
+    // after the solve whatever its outcome
+    if (g_trace_n < grid) {
+        if (g_trace) cudaFreeHost(g_trace);
+        g_trace = nullptr;
+        g_trace_n = 0;
+        if (cudaHostAlloc((void**)&g_trace, sizeof(int) * 2 * grid, cudaHostAllocMapped) == cudaSuccess)
+            g_trace_n = grid;
+    }
+    if (g_trace) {
+        for (int i = 0; i < 2 * grid; ++i) g_trace[i] = -1;
+        int* d_trace = nullptr;
+        if (cudaHostGetDevicePointer((void**)&d_trace, g_trace, 0) == cudaSuccess) a.trace = d_trace;
+    }
+#endif
     cudaError_t e = cudaMemsetAsync(h->d_ctrl, 0, sizeof(Ctrl), h->stream);
     if (e != cudaSuccess) return cuda_status(e);
     if (h->kind == HandleKind::kHubbard) e = hubbard_launch_solve(a, h->hub, grid, h->stream);
     else e = launch_solve<R>(a, L, grid, h->stream);
+#ifdef SCOCG_CHECKED
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (a.trace) {
+        std::fprintf(stderr, "scocg trace (%s):", cudaGetErrorString(e));
+        for (int c = 0; c < grid && c < 16; ++c)
+            std::fprintf(stderr, " [%d:%d]", ((volatile int*)g_trace)[2 * c], ((volatile int*)g_trace)[2 * c + 1]);
+        std::fprintf(stderr, "\n");
+    }
+#endif
     return cuda_status(e);
 }
 

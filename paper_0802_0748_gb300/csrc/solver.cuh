@@ -214,6 +214,7 @@ struct SolveArgs {
     double2* G;                // out [nproj][K] for this right-hand side
     int debug_inject;
     unsigned long long* dbg;   // checked builds: first out-of-range index
+    int* trace;                // checked builds: host-mapped (iteration, phase) per CTA
 };
 
 // Shared per-CTA copy of the seed scalars; every CTA holds identical values.

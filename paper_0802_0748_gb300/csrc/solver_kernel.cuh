@@ -67,6 +67,19 @@ __device__ __forceinline__ void r_partials(const SolveArgs<R>& a, int64_t rbeg, 
     finish_r_partials(a, acc, rbeg, rend, s, s_part, part);
 }
 
+#ifdef SCOCG_CHECKED
+#define SCOCG_TRACE(ph)                                                    \
+    do {                                                                   \
+        if (threadIdx.x == 0 && a.trace) {                                 \
+            volatile int* t_ = a.trace + 2 * blockIdx.x;                   \
+            t_[0] = s.n; t_[1] = (ph);                                     \
+            __threadfence_system();                                        \
+        }                                                                  \
+    } while (0)
+#else
+#define SCOCG_TRACE(ph) do { } while (0)
+#endif
+
 template <typename R, class Apply>
 __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, Apply ap) {
     using V = typename Vec<R>::T;
@@ -151,6 +164,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
 
     // ------------------------------------------------------------ iterations
     while (status == 0) {
+        SCOCG_TRACE(1);
         // ---- phase A: q_n = (z_s - H) r_n + beta_{n-1} q_{n-1}; partial r_n^T q_n
         {
             const V zs = Vec<R>::make(s.zs);
@@ -174,7 +188,9 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
                 pa[3] = (double)s_flag[1];   // a pi^k of this CTA became zero or non-finite
             }
         }
+        SCOCG_TRACE(2);
         if (!grid_barrier(a.sync, epoch, a.debug_inject == 1 && cta == 0 && s.n == 3)) return;
+        SCOCG_TRACE(3);
         grid_sum(a.partA, 4, 4, s.red);
         if (tid == 0) {
             const double2 rq = c2(s.red[0], s.red[1]);
@@ -227,7 +243,9 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
             __syncthreads();
             finish_r_partials(a, acc, rbeg, rend, s, s_part, myB);
         }
+        SCOCG_TRACE(4);
         if (!grid_barrier(a.sync, epoch)) return;
+        SCOCG_TRACE(5);
         grid_sum(a.partB, a.strideB, nred, s.red);
         if (tid < M) {
             s.cr_next[tid] = dense_proj ? c2(s.red[3 + 2 * tid], s.red[4 + 2 * tid])
@@ -285,7 +303,9 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
         __syncthreads();
 
         // ---- seed switching (Sec. III.C) once the seed has converged
+        SCOCG_TRACE(6);
         if (seed_conv) {
+            SCOCG_TRACE(7);
             // local candidate: the unconverged shift with the smallest |pi| (largest residual)
             double best = INFINITY;
             int arg = 0x7fffffff;
@@ -310,7 +330,9 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
                     pc[4] = pp.x; pc[5] = pp.y; pc[6] = pq.x; pc[7] = pq.y; pc[8] = ak.x; pc[9] = ak.y;
                 }
             }
+            SCOCG_TRACE(8);
             if (!grid_barrier(a.sync, epoch)) return;
+            SCOCG_TRACE(9);
             __shared__ double s_sw[6];
             if (tid == 0) {
                 double tot = 0, bad = 0, gbest = INFINITY;
@@ -335,6 +357,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
             __syncthreads();
             if (s_flag[2] != 0) { status = s_flag[2]; break; }
             const int s2 = s_flag[3];
+            SCOCG_TRACE(10 + 100 * s2);
             const double2 pin = c2(s_sw[0], s_sw[1]);        // pi^{s'}_n
             const double2 pin1 = c2(s_sw[2], s_sw[3]);       // pi^{s'}_{n+1}
             const double2 alpha_s2 = c2(s_sw[4], s_sw[5]);   // alpha^{s'}_n
@@ -349,7 +372,8 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
                 a.q[i] = vcfma(v_cb, qi, vcfma(v_ca, ri, vzero<V>()));
                 a.r[i] = vcfma(v_inv1, ri, vzero<V>());
             }
-            if (owns) {
+            SCOCG_TRACE(11);
+            if (owns && chk(a.dbg, 13, s2, a.K)) {
                 const int k = k_own;
                 if (k == s2) {
                     a.S.pi_prev[k] = c2(1, 0); a.S.pi_cur[k] = c2(1, 0);
@@ -372,7 +396,9 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
                 s.replace_on = 0;        // the new seed's full solution is not tracked
             }
             if (tid < M) s.cr_cur[tid] = cmul(s.cr_cur[tid], inv1);
+            SCOCG_TRACE(12);
             if (!grid_barrier(a.sync, epoch)) return;
+            SCOCG_TRACE(13);
         }
 
         // ---- MIXED: FP64 true-residual replacement r_{n+1} = b - (z_s - H) x_{n+1}
@@ -412,6 +438,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
     }
 
     // ------------------------------------------------------------ outputs
+    SCOCG_TRACE(20);
     if (owns) {
         for (int m = 0; m < M; ++m) a.G[(size_t)m * a.K + k_own] = a.S.X[(size_t)k_own * M + m];
     }
