@@ -67,8 +67,11 @@ typedef enum {
 typedef struct {
     int precision;        /* scocg_precision                                          */
     int max_iter;         /* iteration cap per solve; 0 -> 100000                     */
-    int replace_every;    /* MIXED: FP64 true-residual replacement interval in
-                             iterations; 0 -> 200; < 0 disables it                    */
+    int replace_every;    /* MIXED: FP64 true-residual replacement of the seed every
+                             this many iterations; 0 or < 0 disables it (default).
+                             Replacing the seed residual injects the seed's rounding
+                             gap into every shift's recurrence, scaled by 1/pi^k, so
+                             it improves the seed but not the other shifts           */
     int seed;             /* seed shift index; < 0 or out of range -> the seed rule:
                              smallest Im z, then Re z nearest the median Re z, then
                              the lowest index                                         */

@@ -50,7 +50,7 @@ void fill_opts(scocg_opts& o, const scocg_opts* in) {
     std::memset(&o, 0, sizeof(o));
     if (in) o = *in;
     if (o.max_iter <= 0) o.max_iter = 100000;
-    if (o.replace_every == 0) o.replace_every = 200;
+    if (o.replace_every < 0) o.replace_every = 0;
     if (o.timeout_ms <= 0) o.timeout_ms = 10000.0;
     if (o.precision != SCOCG_FP64 && o.precision != SCOCG_MIXED) o.precision = -1;
     if (o.layout != 0 && o.layout != 1) o.precision = -1;

@@ -85,6 +85,7 @@ __device__ __forceinline__ double2 ld_l2(const double2* p) { return __ldcg(p); }
 __device__ __forceinline__ float2 ld_l2(const float2* p) { return __ldcg(p); }
 __device__ __forceinline__ double ld_l2(const double* p) { return __ldcg(p); }
 
+#ifndef SCOCG_HOST_EMULATION
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -100,6 +101,7 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p) {
     asm volatile("ld.volatile.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+#endif
 
 // ---------------------------------------------------------------- barrier
 // Device-wide barrier for a cooperative (co-resident) grid.  `count` only ever

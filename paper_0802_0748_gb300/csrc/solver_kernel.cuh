@@ -80,6 +80,10 @@ __device__ __forceinline__ void r_partials(const SolveArgs<R>& a, int64_t rbeg, 
 #define SCOCG_TRACE(ph) do { } while (0)
 #endif
 
+// Decision word of the per-iteration checks: kGoOn continues, any other value
+// ends the solve with that status (SCOCG_OK is 0, so 0 cannot mean "go on").
+constexpr int kGoOn = 0x7fffffff;
+
 template <typename R, class Apply>
 __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, Apply ap) {
     using V = typename Vec<R>::T;
@@ -107,7 +111,8 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
     unsigned long long epoch = 0;
     const int k_own = cta + tid * G;          // the shift this thread owns (if < K)
     const bool owns = k_own < a.K;
-    int status = 0;
+    int status = SCOCG_NOT_CONVERGED;
+    bool done = false;
 
     // ------------------------------------------------------------ init: r_0 = b, q_{-1} = 0
     {
@@ -159,11 +164,12 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
         if (s.bnorm == 0.0) {                 // b = 0: x = 0 solves every shift
             if (owns) { a.S.frozen[k_own] = 1; a.S.resid[k_own] = 0.0; }
             status = SCOCG_OK;
+            done = true;
         }
     }
 
     // ------------------------------------------------------------ iterations
-    while (status == 0) {
+    while (!done) {
         SCOCG_TRACE(1);
         // ---- phase A: q_n = (z_s - H) r_n + beta_{n-1} q_{n-1}; partial r_n^T q_n
         {
@@ -195,7 +201,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
         if (tid == 0) {
             const double2 rq = c2(s.red[0], s.red[1]);
             const int active = s.n == 0 ? a.K : (int)s.red[2];
-            int st = 0;
+            int st = kGoOn;
             if (s.n > 0 && s.red[3] != 0.0) st = SCOCG_ERR_BREAKDOWN;
             else if (active == 0) st = SCOCG_OK;
             else if (s.n >= a.max_iter) st = SCOCG_NOT_CONVERGED;
@@ -210,7 +216,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
             s_flag[2] = st;
         }
         __syncthreads();
-        if (s_flag[2] != 0) { status = s_flag[2]; break; }
+        if (s_flag[2] != kGoOn) { status = s_flag[2]; break; }
 
         // ---- phase B: r_{n+1} = r_n - alpha_n q_n; partials rho, ||r||^2, c^T r
         {
@@ -344,7 +350,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
                     const int a2 = (int)__ldcg(pc + 2);
                     if (b2 < gbest || (b2 == gbest && a2 < garg)) { gbest = b2; garg = a2; gc = c; }
                 }
-                int st = 0;
+                int st = kGoOn;
                 if (bad != 0.0) st = SCOCG_ERR_BREAKDOWN;
                 else if (tot == 0.0) st = SCOCG_OK;
                 else if (!a.allow_switch) st = SCOCG_ERR_BREAKDOWN;
@@ -355,7 +361,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
                 s_flag[3] = garg;
             }
             __syncthreads();
-            if (s_flag[2] != 0) { status = s_flag[2]; break; }
+            if (s_flag[2] != kGoOn) { status = s_flag[2]; break; }
             const int s2 = s_flag[3];
             SCOCG_TRACE(10 + 100 * s2);
             const double2 pin = c2(s_sw[0], s_sw[1]);        // pi^{s'}_n
@@ -449,7 +455,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
         a.stats->n_replace = s.n_replace;
         a.stats->shift_iters = s.shift_iters;
         a.stats->status = status;
-        atomicCAS(a.sync.status, 0, status);
+        if (status != SCOCG_OK) atomicCAS(a.sync.status, 0, status);
     }
 }
 
