@@ -29,31 +29,35 @@ def _inputs() -> list[Path]:
     return files
 
 
-def lib_path(checked: bool = False) -> Path:
+def lib_path(checked: bool = False, variant: str = "") -> Path:
+    if variant:
+        return BUILD / variant / "libscocg.so"
     return BUILD / "checked" / "libscocg.so" if checked else LIB
 
 
-def up_to_date(checked: bool = False) -> bool:
-    lib = lib_path(checked)
+def up_to_date(checked: bool = False, variant: str = "") -> bool:
+    lib = lib_path(checked, variant)
     if not lib.exists():
         return False
     t = lib.stat().st_mtime
     return all(f.stat().st_mtime <= t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False, checked: bool = False) -> Path:
+def build(force: bool = False, verbose: bool = False, checked: bool = False, variant: str = "",
+          defines: tuple = ()) -> Path:
     """Compile every CUDA source for sm_103a and link the shared library.
 
     checked=True builds the bounds-checked variant (-DSCOCG_CHECKED) into
     _build/checked/: every data-dependent index is tested and a bad one is
-    reported by the solve instead of being used."""
-    lib = lib_path(checked)
-    if not force and up_to_date(checked):
+    reported by the solve instead of being used.  variant/defines build other
+    instrumented variants (e.g. -DSCOCG_PHASE_TIMERS) into _build/<variant>/."""
+    lib = lib_path(checked, variant)
+    if not force and up_to_date(checked, variant):
         return lib
     obj_dir = lib.parent / "obj"
     obj_dir.mkdir(parents=True, exist_ok=True)
     nvcc = _nvcc()
-    extra = ["-DSCOCG_CHECKED"] if checked else []
+    extra = (["-DSCOCG_CHECKED"] if checked else []) + [f"-D{d}" for d in defines]
 
     def compile_one(src: str) -> Path:
         out = obj_dir / (Path(src).stem + ".o")

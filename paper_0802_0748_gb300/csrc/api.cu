@@ -302,6 +302,22 @@ static int solve_one_rhs(scocg_ctx* h, const double2* d_z, int K, int seed, cons
     a.debug_inject = h->opts.debug_inject;
     a.dbg = h->d_ctrl->dbg;
     a.trace = nullptr;
+    a.phase_ns = nullptr;
+#ifdef SCOCG_PHASE_TIMERS
+    // phase timers: [grid][8] ns in host-mapped memory, summed over CTAs and printed
+    static unsigned long long* h_ns = nullptr;
+    static int h_ns_n = 0;
+    if (h_ns_n < grid) {
+        if (h_ns) cudaFreeHost(h_ns);
+        h_ns = nullptr; h_ns_n = 0;
+        if (cudaHostAlloc((void**)&h_ns, sizeof(unsigned long long) * 8 * grid, cudaHostAllocMapped) == cudaSuccess)
+            h_ns_n = grid;
+    }
+    if (h_ns) {
+        std::memset(h_ns, 0, sizeof(unsigned long long) * 8 * grid);
+        cudaHostGetDevicePointer((void**)&a.phase_ns, h_ns, 0);
+    }
+#endif
 #ifdef SCOCG_CHECKED
     // flight recorder: per CTA (iteration, phase) in host-mapped memory, printed
     // after the solve whatever its outcome
@@ -322,6 +338,17 @@ static int solve_one_rhs(scocg_ctx* h, const double2* d_z, int K, int seed, cons
     if (e != cudaSuccess) return cuda_status(e);
     if (h->kind == HandleKind::kHubbard) e = hubbard_launch_solve(a, h->hub, grid, h->stream);
     else e = launch_solve<R>(a, L, grid, h->stream);
+#ifdef SCOCG_PHASE_TIMERS
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (h_ns) {
+        double tot[8] = {0};
+        for (int c = 0; c < grid; ++c)
+            for (int k = 0; k < 8; ++k) tot[k] += (double)((volatile unsigned long long*)h_ns)[8 * c + k];
+        std::fprintf(stderr, "scocg phase ms (CTA average): A %.3f bar1 %.3f red1+B %.3f bar2 %.3f red2+C %.3f tail %.3f\n",
+                     tot[0] / grid * 1e-6, tot[1] / grid * 1e-6, tot[2] / grid * 1e-6, tot[3] / grid * 1e-6,
+                     tot[4] / grid * 1e-6, tot[7] / grid * 1e-6);
+    }
+#endif
 #ifdef SCOCG_CHECKED
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (a.trace) {
@@ -394,6 +421,7 @@ extern "C" int scocg_solve(scocg_handle h, const scocg_c128* shifts, int nshift,
         S.pi_cur = (double2*)c.take(sizeof(double2) * K);
         S.sigma = (double2*)c.take(sizeof(double2) * K);
         S.alpha_k = (double2*)c.take(sizeof(double2) * K);
+        S.inv_cur = (double2*)c.take(sizeof(double2) * K);
         S.P = (double2*)c.take(sizeof(double2) * (size_t)K * M);
         S.X = (double2*)c.take(sizeof(double2) * (size_t)K * M);
         S.frozen = (int*)c.take(sizeof(int) * K);
@@ -468,7 +496,8 @@ extern "C" int scocg_solve(scocg_handle h, const scocg_c128* shifts, int nshift,
         siters += c.stats.shift_iters;
         if (info) {
             if (info->freeze_iter) std::memcpy(info->freeze_iter + (size_t)j * K, h_iters.data(), sizeof(int) * K);
-            if (info->resid) std::memcpy(info->resid + (size_t)j * K, h_resid.data(), sizeof(double) * K);
+            if (info->resid)   // the kernel keeps squared residual estimates
+                for (int k = 0; k < K; ++k) info->resid[(size_t)j * K + k] = std::sqrt(h_resid[k]);
         }
     }
     cudaEventDestroy(ev0); cudaEventDestroy(ev1);

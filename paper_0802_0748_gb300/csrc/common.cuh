@@ -27,11 +27,21 @@ __host__ __device__ __forceinline__ double cabs_(double2 a) { return hypot(a.x, 
 // |b| near the limits of the exponent range neither overflows nor underflows.
 __host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
     if (fabs(b.x) >= fabs(b.y)) {
-        double r = b.y / b.x, d = b.x + b.y * r;
-        return c2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+        const double r = b.y / b.x, inv = 1.0 / (b.x + b.y * r);
+        return c2((a.x + a.y * r) * inv, (a.y - a.x * r) * inv);
     } else {
-        double r = b.x / b.y, d = b.x * r + b.y;
-        return c2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+        const double r = b.x / b.y, inv = 1.0 / (b.x * r + b.y);
+        return c2((a.x * r + a.y) * inv, (a.y * r - a.x) * inv);
+    }
+}
+// 1 / b with the same scaling
+__host__ __device__ __forceinline__ double2 crecip(double2 b) {
+    if (fabs(b.x) >= fabs(b.y)) {
+        const double r = b.y / b.x, inv = 1.0 / (b.x + b.y * r);
+        return c2(inv, -r * inv);
+    } else {
+        const double r = b.x / b.y, inv = 1.0 / (b.x * r + b.y);
+        return c2(r * inv, -inv);
     }
 }
 __host__ __device__ __forceinline__ bool cfinite(double2 a) { return isfinite(a.x) && isfinite(a.y); }
@@ -170,6 +180,11 @@ __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 
 // Sum `nval` per-thread doubles over the CTA; the result lands in out[0..nval)
 // (shared memory) and is visible to all threads after the call.  `scratch`
@@ -191,12 +206,23 @@ __device__ __forceinline__ void block_sum(const double* vals, int nval, double* 
 
 // Deterministic grid reduction of per-CTA partials part[cta * stride + j],
 // j < nval: every CTA computes bit-identical sums (same data, same order).
+// The loads of a lane are issued together (up to 16 per lane, grids up to 512
+// CTAs in one round) so that the reduction costs one L2 round trip.
 __device__ __forceinline__ void grid_sum(const double* part, int stride, int nval, double* out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int G = gridDim.x;
     for (int j = warp; j < nval; j += kWarps) {
         double s = 0.0;
-        for (int c = lane; c < G; c += 32) s += __ldcg(part + (size_t)c * stride + j);
+        for (int c0 = 0; c0 < G; c0 += 32 * 16) {
+            double v[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int c = c0 + lane + 32 * u;
+                v[u] = c < G ? __ldcg(part + (size_t)c * stride + j) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 16; ++u) s += v[u];
+        }
         s = warp_sum(s);
         if (lane == 0) out[j] = s;
     }

@@ -34,11 +34,12 @@ struct ShiftState {          // device arrays, [K] or [K][M]
     double2* pi_cur;
     double2* sigma;
     double2* alpha_k;        // alpha^k_n of the last update (needed by a switch)
+    double2* inv_cur;        // 1 / pi^k_n
     double2* P;              // [K][M] c_m^T p^k
     double2* X;              // [K][M] c_m^T x^k
     int* frozen;
     int* iters;
-    double* resid;
+    double* resid;           // squared residual estimate (||r_k|| / ||b||)^2
 };
 
 struct SolveStats {          // device, written by CTA 0
@@ -215,12 +216,14 @@ struct SolveArgs {
     int debug_inject;
     unsigned long long* dbg;   // checked builds: first out-of-range index
     int* trace;                // checked builds: host-mapped (iteration, phase) per CTA
+    unsigned long long* phase_ns;  // phase-timer builds: [grid][8] accumulated ns
 };
 
 // Shared per-CTA copy of the seed scalars; every CTA holds identical values.
 struct SeedScalars {
     double2 alpha, alpha_prev, beta_prev, rho, rho_prev, zs;
-    double rnorm, bnorm;
+    double2 t2;                 // alpha_n beta_{n-1} / alpha_{n-1}
+    double rnorm, bnorm, rn_b;  // rn_b = ||r_{n+1}|| / ||b||
     int seed, active, n;
     int replace_on, n_switch, n_replace;
     long long shift_iters;

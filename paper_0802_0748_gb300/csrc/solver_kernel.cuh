@@ -5,13 +5,15 @@
 
 namespace scocg {
 
-template <int NV>
-__device__ __forceinline__ void block_sum_n(double (&v)[NV], double* scratch, double* out) {
+// CTA sum of per-thread values: the warp-level part in the values' own type
+// (FP32 for complex64 vectors), the sum over warps in FP64.
+template <int NV, typename T>
+__device__ __forceinline__ void block_sum_n(T (&v)[NV], double* scratch, double* out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
-        double t = warp_sum(v[j]);
-        if (lane == 0) scratch[warp * NV + j] = t;
+        const T t = warp_sum(v[j]);
+        if (lane == 0) scratch[warp * NV + j] = (double)t;
     }
     __syncthreads();
     if (threadIdx.x < NV) {
@@ -46,13 +48,12 @@ template <typename R>
 __device__ __forceinline__ void finish_r_partials(const SolveArgs<R>& a, const R (&acc)[5], int64_t rbeg,
                                                   int64_t rend, SeedScalars& s, double* s_part, double* part) {
     const int tid = threadIdx.x;
-    double v[5] = {acc[0], acc[1], acc[2], acc[3], acc[4]};
+    R v[5] = {acc[0], acc[1], acc[2], acc[3], acc[4]};
     block_sum_n<5>(v, s.scratch, s_part);
     if (tid < 5) part[tid] = s_part[tid];
     for (int m = 1; m < a.nproj && a.cvec; ++m) {
-        R w[2] = {0, 0};
-        for (int64_t i = rbeg + tid; i < rend; i += kBlock) acc_bil(w[0], w[1], a.cvec[(size_t)m * a.n + i], a.r[i]);
-        double w2[2] = {w[0], w[1]};
+        R w2[2] = {0, 0};
+        for (int64_t i = rbeg + tid; i < rend; i += kBlock) acc_bil(w2[0], w2[1], a.cvec[(size_t)m * a.n + i], a.r[i]);
         block_sum_n<2>(w2, s.scratch, s_part);
         if (tid < 2) part[3 + 2 * m + tid] = s_part[tid];
     }
@@ -78,6 +79,22 @@ __device__ __forceinline__ void r_partials(const SolveArgs<R>& a, int64_t rbeg, 
     } while (0)
 #else
 #define SCOCG_TRACE(ph) do { } while (0)
+#endif
+
+// Optional per-phase wall-time accounting (-DSCOCG_PHASE_TIMERS): thread 0 of
+// each CTA adds the time spent since the previous mark to slot `k` of its row in
+// a.phase_ns ([grid][8] nanoseconds).
+#ifdef SCOCG_PHASE_TIMERS
+#define SCOCG_MARK(k)                                                      \
+    do {                                                                   \
+        if (threadIdx.x == 0 && a.phase_ns) {                              \
+            const uint64_t t_ = globaltimer_ns();                          \
+            a.phase_ns[8 * blockIdx.x + (k)] += t_ - t_mark;               \
+            t_mark = t_;                                                   \
+        }                                                                  \
+    } while (0)
+#else
+#define SCOCG_MARK(k) do { } while (0)
 #endif
 
 // Decision word of the per-iteration checks: kGoOn continues, any other value
@@ -113,6 +130,9 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
     const bool owns = k_own < a.K;
     int status = SCOCG_NOT_CONVERGED;
     bool done = false;
+#ifdef SCOCG_PHASE_TIMERS
+    uint64_t t_mark = globaltimer_ns();
+#endif
 
     // ------------------------------------------------------------ init: r_0 = b, q_{-1} = 0
     {
@@ -133,7 +153,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
         r_partials(a, rbeg, rend, s, s_part, myB);
         if (owns) {
             const int k = k_own;
-            a.S.pi_prev[k] = c2(1, 0); a.S.pi_cur[k] = c2(1, 0);
+            a.S.pi_prev[k] = c2(1, 0); a.S.pi_cur[k] = c2(1, 0); a.S.inv_cur[k] = c2(1, 0);
             a.S.sigma[k] = csub(a.z[k], a.z[a.seed]);
             a.S.alpha_k[k] = c2(0, 0);
             for (int m = 0; m < M; ++m) { a.S.P[(size_t)k * M + m] = c2(0, 0); a.S.X[(size_t)k * M + m] = c2(0, 0); }
@@ -171,6 +191,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
     // ------------------------------------------------------------ iterations
     while (!done) {
         SCOCG_TRACE(1);
+        SCOCG_MARK(7);
         // ---- phase A: q_n = (z_s - H) r_n + beta_{n-1} q_{n-1}; partial r_n^T q_n
         {
             const V zs = Vec<R>::make(s.zs);
@@ -185,8 +206,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
                     acc_bil(rq[0], rq[1], a.r[row], qn);
                 }
             }
-            double v[2] = {rq[0], rq[1]};
-            block_sum_n<2>(v, s.scratch, s_part);
+            block_sum_n<2>(rq, s.scratch, s_part);
             if (tid == 0) {
                 double* pa = a.partA + (size_t)cta * 4;
                 pa[0] = s_part[0]; pa[1] = s_part[1];
@@ -195,8 +215,10 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
             }
         }
         SCOCG_TRACE(2);
+        SCOCG_MARK(0);
         if (!grid_barrier(a.sync, epoch, a.debug_inject == 1 && cta == 0 && s.n == 3)) return;
         SCOCG_TRACE(3);
+        SCOCG_MARK(1);
         grid_sum(a.partA, 4, 4, s.red);
         if (tid == 0) {
             const double2 rq = c2(s.red[0], s.red[1]);
@@ -250,46 +272,56 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
             finish_r_partials(a, acc, rbeg, rend, s, s_part, myB);
         }
         SCOCG_TRACE(4);
+        SCOCG_MARK(2);
         if (!grid_barrier(a.sync, epoch)) return;
         SCOCG_TRACE(5);
+        SCOCG_MARK(3);
         grid_sum(a.partB, a.strideB, nred, s.red);
         if (tid < M) {
             s.cr_next[tid] = dense_proj ? c2(s.red[3 + 2 * tid], s.red[4 + 2 * tid])
                                         : (chk(a.dbg, 12, a.cidx[tid], a.n) ? Vec<R>::wide(__ldcg(a.r + a.cidx[tid])) : c2(0, 0));
         }
+        if (tid == 0) {
+            s.t2 = cdiv(cmul(s.alpha, s.beta_prev), s.alpha_prev);
+            s.rn_b = sqrt(s.red[2]) / s.bnorm;
+        }
         __syncthreads();
 
         // ---- phase C: per-shift scalar recurrences for this CTA's shifts
+        // (one complex reciprocal per shift; 1/pi^k_n is carried between
+        // iterations and residuals are compared squared)
         const double2 rho_new = c2(s.red[0], s.red[1]);
         const double rnorm_new = sqrt(s.red[2]);
-        const bool seed_conv = a.tol > 0.0 && shift_resid(rnorm_new, c2(1, 0), s.bnorm) <= a.tol;
+        const double tol2 = a.tol * a.tol;
+        const double rn_b2 = s.rn_b * s.rn_b;
+        const bool seed_conv = a.tol > 0.0 && rn_b2 <= tol2;   // the seed has pi = 1
         int my_active = 0, my_bad = 0;
         if (owns && !a.S.frozen[k_own]) {
             const int k = k_own;
-            const double2 pp = a.S.pi_prev[k], pc = a.S.pi_cur[k];
-            const double2 ratio = cdiv(pp, pc);
+            const double2 pp = a.S.pi_prev[k], pc = a.S.pi_cur[k], ic = a.S.inv_cur[k];
+            const double2 ratio = cmul(pp, ic);                        // pi_{n-1} / pi_n
             const double2 beta_k = cmul(cmul(ratio, ratio), s.beta_prev);
-            const double2 inv_pi = cdiv(c2(1, 0), pc);
-            const double2 t1 = cmul(s.alpha, a.S.sigma[k]);
-            const double2 t2 = cdiv(cmul(s.alpha, s.beta_prev), s.alpha_prev);
-            const double2 pn = cadd(cmul(cadd(c2(1, 0), t1), pc), cmul(t2, csub(pc, pp)));
-            if (cabs2(pn) == 0.0 || !cfinite(pn) || !isfinite(cabs_(pn))) {
+            const double2 pn = cadd(cmul(cadd(c2(1, 0), cmul(s.alpha, a.S.sigma[k])), pc),
+                                    cmul(s.t2, csub(pc, pp)));
+            const double2 in = crecip(pn);
+            if (cabs2(pn) == 0.0 || !cfinite(pn) || !cfinite(in)) {
                 my_bad = 1;
             } else {
-                const double2 ak = cmul(cdiv(pc, pn), s.alpha);
+                const double2 ak = cmul(cmul(pc, in), s.alpha);         // alpha^k_n
                 for (int m = 0; m < M; ++m) {
                     const size_t o = (size_t)k * M + m;
-                    const double2 P = cadd(cmul(s.cr_cur[m], inv_pi), cmul(beta_k, a.S.P[o]));
+                    const double2 P = cadd(cmul(s.cr_cur[m], ic), cmul(beta_k, a.S.P[o]));
                     a.S.P[o] = P;
                     a.S.X[o] = cadd(a.S.X[o], cmul(ak, P));
                 }
                 a.S.alpha_k[k] = ak;
                 a.S.pi_prev[k] = pc;
                 a.S.pi_cur[k] = pn;
-                const double res = shift_resid(rnorm_new, pn, s.bnorm);
-                a.S.resid[k] = res;
+                a.S.inv_cur[k] = in;
+                const double res2 = rn_b2 * cabs2(in);
+                a.S.resid[k] = res2;
                 a.S.iters[k] = s.n + 1;
-                if (a.tol > 0.0 && res <= a.tol) a.S.frozen[k] = 1;
+                if (a.tol > 0.0 && res2 <= tol2) a.S.frozen[k] = 1;
                 else my_active = 1;
             }
         }
@@ -310,12 +342,13 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
 
         // ---- seed switching (Sec. III.C) once the seed has converged
         SCOCG_TRACE(6);
+        SCOCG_MARK(4);
         if (seed_conv) {
             SCOCG_TRACE(7);
             // local candidate: the unconverged shift with the smallest |pi| (largest residual)
             double best = INFINITY;
             int arg = 0x7fffffff;
-            if (owns && !a.S.frozen[k_own]) { best = cabs_(a.S.pi_cur[k_own]); arg = k_own; }
+            if (owns && !a.S.frozen[k_own]) { best = -cabs2(a.S.inv_cur[k_own]); arg = k_own; }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 const double ob = __shfl_xor_sync(0xffffffffu, best, o);
@@ -382,10 +415,11 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
             if (owns && chk(a.dbg, 13, s2, a.K)) {
                 const int k = k_own;
                 if (k == s2) {
-                    a.S.pi_prev[k] = c2(1, 0); a.S.pi_cur[k] = c2(1, 0);
+                    a.S.pi_prev[k] = c2(1, 0); a.S.pi_cur[k] = c2(1, 0); a.S.inv_cur[k] = c2(1, 0);
                 } else {
                     a.S.pi_prev[k] = cdiv(a.S.pi_prev[k], pin);
                     a.S.pi_cur[k] = cdiv(a.S.pi_cur[k], pin1);
+                    a.S.inv_cur[k] = cmul(a.S.inv_cur[k], pin1);
                 }
                 a.S.sigma[k] = csub(a.z[k], a.z[s2]);
             }

@@ -16,8 +16,9 @@ import numpy as np
 import os
 
 # SCOCG_LIB=checked selects the bounds-checked build (see build.py)
+_variant = os.environ.get("SCOCG_LIB", "")
 LIB_PATH = Path(__file__).resolve().parent / "_build" / (
-    "checked/libscocg.so" if os.environ.get("SCOCG_LIB") == "checked" else "libscocg.so")
+    f"{_variant}/libscocg.so" if _variant else "libscocg.so")
 
 OK, NOT_CONVERGED = 0, 1
 ERR_INVALID, ERR_CUDA, ERR_OOM, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_UNSYMMETRIC = -1, -2, -3, -4, -5, -6
