@@ -188,14 +188,25 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+PREC_NAMES = {"fp64": 0, "mixed": 1}
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz
+
+
+def fp64_flops_per_iter(n: int, nnz: int, nproj_dense: int) -> float:
+    """FP64 flops of one seed iteration: the apply (complex x real: 4 flops per
+    stored entry, 8 per row for z_s r), q update 8, r^T q 8, r update 8,
+    r^T r 8, ||r||^2 4, c^T r 8 per dense projection (flops per row)."""
+    return 4.0 * nnz + n * (8 + 8 + 8 + 8 + 8 + 4 + 8 * nproj_dense)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--no-fp64-leg", action="store_true", help="skip the FP64 comparison number")
+    ap.add_argument("--precision", default="fp64", choices=sorted(PREC_NAMES))
+    ap.add_argument("--compare", default="mixed", help="comma list of other precisions timed once beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--max-iter", type=int, default=0, help="cap on seed iterations (0 = to convergence)")
     args = ap.parse_args()
@@ -227,6 +238,7 @@ def main():
     b_d = torch.from_numpy(wl.rhs[0]).to(dev)
     c_d = torch.from_numpy(wl.proj_vec).to(dev)
     stream = torch.cuda.current_stream()
+    prec = PREC_NAMES[args.precision]
 
     def step(precision, max_iter=0):
         opts = scocg.SolveOptions(precision=precision, max_iter=max_iter)
@@ -235,7 +247,6 @@ def main():
         scocg.scocg_destroy(hh)
         return G, info
 
-    prec = scocg.MIXED if args.precision == "mixed" else scocg.FP64
     for _ in range(args.warmup):
         step(prec, args.max_iter)
     torch.cuda.synchronize()
@@ -253,9 +264,9 @@ def main():
     barrier(ws)
     ms = ev0.elapsed_time(ev1)
     ms_max = max_over_ranks(ms, ws)
-    siters = sum(i["shift_iters"] for i in infos)
-    total_siters = sum_over_ranks(siters, ws)
+    total_siters = sum_over_ranks(sum(i["shift_iters"] for i in infos), ws)
     value = total_siters / (ms_max * 1e-3)
+    G_main = G.cpu().numpy()[0]
 
     # end-to-end through the C ABI with host buffers (copies inside the timed region)
     rp_h, col_h, val_h = h.rowptr, h.col, h.val
@@ -265,14 +276,14 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        hh = scocg.scocg_create_csr(rp_h, col_h, val_h, opts=scocg.SolveOptions(precision=prec,
-                                                                                 max_iter=args.max_iter))
+        hh = scocg.scocg_create_csr(rp_h, col_h, val_h,
+                                    opts=scocg.SolveOptions(precision=prec, max_iter=args.max_iter))
         bd = b_h.to(dev, non_blocking=True)
         cd = c_h.to(dev, non_blocking=True)
-        G, info = scocg.scocg_solve(hh, wl.shifts, bd, proj_vec=cd, tol=TOL)
-        g_host = G.cpu()
+        Ge, info_e = scocg.scocg_solve(hh, wl.shifts, bd, proj_vec=cd, tol=TOL)
+        g_host = Ge.cpu()
         scocg.scocg_destroy(hh)
-        e2e_siters += info["shift_iters"]
+        e2e_siters += info_e["shift_iters"]
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
     e2e_value = sum_over_ranks(e2e_siters, ws) / e2e_s
@@ -280,37 +291,48 @@ def main():
     d2h = g_host.numel() * 16
 
     # roofline of the persistent solve kernel (CUDA events on its stream, inside the library)
-    hbm, peak_kind = peaks()
     kern_s = statistics.mean(i["seconds"] for i in infos)
     iters = statistics.mean(i["iters"] for i in infos)
-    bytes_launch = infos[0]["bytes_per_iter"] * iters
-    achieved = bytes_launch / kern_s / 1e9
+    us_per_iter = kern_s / iters * 1e6
     digest = kernel_digest()
-    tkey = "mixed" if prec == scocg.MIXED else "fp64"
+    hbm, peak_kind = peaks()
+    if prec == scocg.FP64:
+        flops = fp64_flops_per_iter(h.n, h.nnz, 1) * iters
+        achieved = flops / kern_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
+                "frac": achieved / FP64_PEAK_TFLOPS, "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz",
+                "hbm_GBs_algorithmic": infos[0]["bytes_per_iter"] * iters / kern_s / 1e9}
+    else:
+        achieved = infos[0]["bytes_per_iter"] * iters / kern_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "peak_kind": peak_kind}
+    tkey = args.precision
     traffic = None
-    if TRAFFIC["digest"] == digest and TRAFFIC[tkey] is not None:
+    if TRAFFIC["digest"] == digest and TRAFFIC.get(tkey) is not None:
         traffic = TRAFFIC[tkey] * iters
+    roof.update({"traffic": traffic, "kernel": "cocg_persistent (one launch per solve)",
+                 "us_per_iter": us_per_iter, "iters": iters, "kernel_digest": digest})
 
     extra = {}
-    if not args.no_fp64_leg and prec == scocg.MIXED:
-        step(scocg.FP64, args.max_iter)
+    for other in [p for p in args.compare.split(",") if p and p != args.precision]:
+        po = PREC_NAMES[other]
+        mi = args.max_iter or int(max(i["iters"] for i in infos))
+        step(po, mi)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        G64, i64 = step(scocg.FP64, args.max_iter)
+        Go, io = step(po, mi)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms64 = max_over_ranks(e0.elapsed_time(e1), ws)
-        v64 = sum_over_ranks(i64["shift_iters"], ws) / (ms64 * 1e-3)
-        gm = G.cpu().numpy()[0, 0]
-        gd = G64.cpu().numpy()[0, 0]
-        extra["fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": ms64, "iters": i64["iters"],
-                         "kernel_s": i64["seconds"],
-                         "bytes_per_iter": i64["bytes_per_iter"],
-                         "fp64_alu_bound_note": "FP64 FMA rate on this GPU is ~0.6 T/s"}
-        extra["mixed_vs_fp64"] = {"speedup": value / v64,
-                                  "max_rel_G_diff": float(np.max(np.abs(gm - gd) / np.abs(gd))),
-                                  "median_rel_G_diff": float(np.median(np.abs(gm - gd) / np.abs(gd)))}
+        mso = max_over_ranks(e0.elapsed_time(e1), ws)
+        vo = sum_over_ranks(io["shift_iters"], ws) / (mso * 1e-3)
+        go = Go.cpu().numpy()[0]
+        rel = np.abs(go - G_main) / np.abs(G_main)
+        extra[other] = {"value": vo, "unit": UNIT, "ms_per_step": mso, "iters": io["iters"],
+                        "converged": io["status"] == 0, "us_per_iter": io["seconds"] / io["iters"] * 1e6,
+                        "hbm_GBs_algorithmic": io["bytes_per_iter"] / (io["seconds"] / io["iters"]) / 1e9,
+                        "max_iter_cap": mi, "speedup_vs_main_per_iter": us_per_iter / (io["seconds"] / io["iters"] * 1e6),
+                        "max_rel_G_diff_vs_main": float(rel.max()), "median_rel_G_diff_vs_main": float(np.median(rel))}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -325,19 +347,17 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32+f64" if prec == scocg.MIXED else "f64", "data": "synthetic",
+                "dtype": {"fp64": "f64", "mixed": "f32+f64"}[args.precision], "data": "synthetic",
                 "config": {"workload": "anderson-64^3x4 (1,048,576 rows, 29,360,128 nnz), 512 shifts, eta 1e-3",
                            "tol": TOL, "precision": tkey, "parallelism": f"replicas x{ws}",
                            "l2": "inputs larger than L2 (H 125-242 MB per iteration)",
                            "iters": infos[0]["iters"], "n_switch": infos[0]["n_switch"],
-                           "n_replace": infos[0]["n_replace"]},
-                "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                             "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
-                             "kernel": "cocg_persistent (one launch per solve)"},
+                           "status": infos[0]["status"]},
+                "roofline": roof,
                 "clocks": clk.summary(),
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},
-                "gpu_launches": args.steps * (5 + 2),
+                "gpu_launches": args.steps * (5 + 1 + (1 if prec == scocg.MIXED else 0)),
                 "cpu_baseline": cpu}
         line.update(extra)
         print(json.dumps(line), flush=True)

@@ -250,6 +250,7 @@ def test_config2_full_size_fixed_iterations(S, oracle_mod):
                                       proj_vec=wl.proj_vec, tol=0.0, max_iter=n_it,
                                       seed=int(np.where(sample == seed)[0][0]))
         assert relerr(g[:, sample], ref.G) < bound, n_it
+    # complex64 vectors: |dG/G| ~ eps32 ||H|| / eta ~ 4e-4 at eta = 1e-3
     gm, infom = gpu_solve(S, h, wl.shifts, wl.rhs[0], proj_vec=wl.proj_vec, tol=0.0,
                           opts=S.SolveOptions(max_iter=n_it, precision=S.MIXED))
-    assert relerr(gm[:, sample], ref.G) < 1e-5
+    assert relerr(gm[:, sample], ref.G) < 2e-3
