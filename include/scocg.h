@@ -56,10 +56,16 @@ typedef enum {
 } scocg_status;
 
 typedef enum {
-    SCOCG_FP64 = 0,   /* complex128 vectors, FP64 H values and arithmetic            */
-    SCOCG_MIXED = 1   /* complex64 vectors and FP32 H values with FP32 arithmetic in
-                         the H apply and vector updates; FP64 seed scalars, FP64
-                         shift recurrences and periodic FP64 residual replacement   */
+    SCOCG_FP64 = 0,     /* complex128 vectors, FP64 H values and arithmetic          */
+    SCOCG_MIXED = 1,    /* complex64 vectors and FP32 H values with FP32 arithmetic in
+                           the H apply and vector updates; FP64 seed scalars, FP64
+                           shift recurrences, optional FP64 residual replacement.
+                           G carries an error of order eps32 ||H|| / Im z         */
+    SCOCG_MIXED_DF = 2  /* compensated FP32: each vector entry is a pair of FP32
+                           numbers (hi + lo, about 44 significant bits), FP32 H
+                           values, every vector operation in FP32 arithmetic with
+                           error-free transformations (TwoSum, FMA TwoProd); FP64
+                           seed scalars and shift recurrences.  CSR handles only. */
 } scocg_precision;
 
 /* Options, fixed at create time (scocg_set_opts changes them later).
@@ -152,6 +158,8 @@ int scocg_set_opts(scocg_handle h, const scocg_opts *opts);
  *   precision SCOCG_FP64: x, y device complex128 [N]
  *   precision SCOCG_MIXED: x, y device complex64 [N] (float re, im pairs),
  *                          arithmetic in FP32 with FP32 values of H
+ *   precision SCOCG_MIXED_DF: x, y device float4 [N] {re.hi, im.hi, re.lo, im.lo}
+ *                          (value = hi + lo), compensated FP32 arithmetic
  * Synchronises the stream.
  */
 int scocg_apply(scocg_handle h, scocg_c128 z, const void *x, void *y, int precision);

@@ -52,7 +52,7 @@ void fill_opts(scocg_opts& o, const scocg_opts* in) {
     if (o.max_iter <= 0) o.max_iter = 100000;
     if (o.replace_every < 0) o.replace_every = 0;
     if (o.timeout_ms <= 0) o.timeout_ms = 10000.0;
-    if (o.precision != SCOCG_FP64 && o.precision != SCOCG_MIXED) o.precision = -1;
+    if (o.precision != SCOCG_FP64 && o.precision != SCOCG_MIXED && o.precision != SCOCG_MIXED_DF) o.precision = -1;
     if (o.layout != 0 && o.layout != 1) o.precision = -1;
 }
 
@@ -254,12 +254,15 @@ Layout scocg_ctx::layout(bool prefer_csr) const {
 
 // ---------------------------------------------------------------- apply
 extern "C" int scocg_apply(scocg_handle h, scocg_c128 z, const void* x, void* y, int precision) {
-    if (!h || !x || !y || (precision != SCOCG_FP64 && precision != SCOCG_MIXED)) return SCOCG_ERR_INVALID;
+    if (!h || !x || !y || (precision != SCOCG_FP64 && precision != SCOCG_MIXED && precision != SCOCG_MIXED_DF))
+        return SCOCG_ERR_INVALID;
     cudaError_t e;
-    if (h->kind == HandleKind::kHubbard)
+    if (h->kind == HandleKind::kHubbard) {
+        if (precision == SCOCG_MIXED_DF) return SCOCG_ERR_INVALID;
         e = hubbard_apply(h->hub, precision == SCOCG_MIXED, c2(z.re, z.im), x, y, h->stream);
-    else
-        e = launch_apply(h->layout(false), precision == SCOCG_MIXED, c2(z.re, z.im), x, y, h->stream);
+    } else {
+        e = launch_apply(h->layout(false), precision, c2(z.re, z.im), x, y, h->stream);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     return cuda_status(e);
 }
@@ -366,6 +369,11 @@ __global__ void k_to_c64(int64_t n, const double2* in, float2* out) {
     if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
 }
 
+__global__ void k_to_df(int64_t n, const double2* in, float4* out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = df_from(in[i]);
+}
+
 int algorithmic_bytes_note(void) { return 0; }
 
 }  // namespace scocg
@@ -381,7 +389,10 @@ extern "C" int scocg_solve(scocg_handle h, const scocg_c128* shifts, int nshift,
     if (proj_idx)
         for (int64_t j = 0; j < (int64_t)nrhs * nproj; ++j)
             if (proj_idx[j] < 0 || proj_idx[j] >= h->n) return SCOCG_ERR_INVALID;
-    const bool mixed = h->opts.precision == SCOCG_MIXED;
+    const int prec = h->opts.precision;
+    const bool mixed = prec == SCOCG_MIXED;
+    const bool dfm = prec == SCOCG_MIXED_DF;
+    if (dfm && h->kind == HandleKind::kHubbard) return SCOCG_ERR_INVALID;
     const int64_t n = h->n;
     const int K = nshift, M = nproj;
     const int seed = (h->opts.seed >= 0 && h->opts.seed < K) ? h->opts.seed : default_seed(shifts, K);
@@ -389,7 +400,7 @@ extern "C" int scocg_solve(scocg_handle h, const scocg_c128* shifts, int nshift,
 
     const Layout L = h->kind == HandleKind::kHubbard ? Layout{} : h->layout(false);
     int maxco = h->kind == HandleKind::kHubbard ? hubbard_max_ctas(h->hub, mixed, h->num_sms)
-                                                 : max_coresident_ctas(L, mixed, h->num_sms);
+                                                 : max_coresident_ctas(L, prec, h->num_sms);
     if (maxco <= 0) return SCOCG_ERR_CUDA;
     const int rpu = h->kind == HandleKind::kHubbard ? 32 : rows_per_unit(L.kind);
     const int64_t nunits = h->kind == HandleKind::kHubbard ? h->hub.nunits : (n + rpu - 1) / rpu;
@@ -400,7 +411,8 @@ extern "C" int scocg_solve(scocg_handle h, const scocg_c128* shifts, int nshift,
     const int strideB = 3 + 2 * M + 1;
 
     // workspace layout: the same sequence of pieces is measured, then carved
-    const size_t vbytes = (mixed ? sizeof(float2) : sizeof(double2)) * (size_t)n;
+    const size_t velem = mixed ? sizeof(float2) : (dfm ? sizeof(float4) : sizeof(double2));
+    const size_t vbytes = velem * (size_t)n;
     void *r = nullptr, *q = nullptr, *ps = nullptr, *xh = nullptr, *xl = nullptr, *cvec = nullptr;
     double2* xd = nullptr;
     int64_t* d_cidx = nullptr;
@@ -414,7 +426,7 @@ extern "C" int scocg_solve(scocg_handle h, const scocg_c128* shifts, int nshift,
             ps = c.take(vbytes); xh = c.take(vbytes); xl = c.take(vbytes);
             xd = (double2*)c.take(sizeof(double2) * n);
         }
-        if (mixed && proj_vec) cvec = c.take(sizeof(float2) * (size_t)n * M);
+        if ((mixed || dfm) && proj_vec) cvec = c.take(velem * (size_t)n * M);
         d_cidx = (int64_t*)c.take(sizeof(int64_t) * M);
         d_z = (double2*)c.take(sizeof(double2) * K);
         S.pi_prev = (double2*)c.take(sizeof(double2) * K);
@@ -444,8 +456,13 @@ extern "C" int scocg_solve(scocg_handle h, const scocg_c128* shifts, int nshift,
         k_to_c64<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(tot, (const double2*)proj_vec, (float2*)cvec);
         e = cudaGetLastError();
     }
+    if (e == cudaSuccess && dfm && proj_vec) {
+        const int64_t tot = n * M;
+        k_to_df<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(tot, (const double2*)proj_vec, (float4*)cvec);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return cuda_status(e);
-    const void* cv = proj_vec ? (mixed ? cvec : proj_vec) : nullptr;
+    const void* cv = proj_vec ? ((mixed || dfm) ? cvec : proj_vec) : nullptr;
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEventCreate(&ev0); cudaEventCreate(&ev1);
@@ -463,12 +480,14 @@ extern "C" int scocg_solve(scocg_handle h, const scocg_c128* shifts, int nshift,
         const double2* b = static_cast<const double2*>(rhs) + (size_t)j * n;
         double2* G = reinterpret_cast<double2*>(G_out) + (size_t)j * M * K;
         cudaEventRecord(ev0, s);
-        int st = mixed ? solve_one_rhs<float>(h, d_z, K, seed, b, proj_idx ? d_cidx : nullptr, cv, M, tol, G, grid, S,
-                                              partA, partB, partC, strideB, (float2*)r, (float2*)q, (float2*)ps,
-                                              (float2*)xh, (float2*)xl, xd, L)
-                       : solve_one_rhs<double>(h, d_z, K, seed, b, proj_idx ? d_cidx : nullptr, cv, M, tol, G, grid,
-                                               S, partA, partB, partC, strideB, (double2*)r, (double2*)q, nullptr,
-                                               nullptr, nullptr, nullptr, L);
+        const int64_t* ci = proj_idx ? d_cidx : nullptr;
+        int st = mixed ? solve_one_rhs<float>(h, d_z, K, seed, b, ci, cv, M, tol, G, grid, S, partA, partB, partC,
+                                              strideB, (float2*)r, (float2*)q, (float2*)ps, (float2*)xh,
+                                              (float2*)xl, xd, L)
+               : dfm ? solve_one_rhs<DF>(h, d_z, K, seed, b, ci, cv, M, tol, G, grid, S, partA, partB, partC,
+                                         strideB, (float4*)r, (float4*)q, nullptr, nullptr, nullptr, nullptr, L)
+                     : solve_one_rhs<double>(h, d_z, K, seed, b, ci, cv, M, tol, G, grid, S, partA, partB, partC,
+                                             strideB, (double2*)r, (double2*)q, nullptr, nullptr, nullptr, nullptr, L);
         cudaEventRecord(ev1, s);
         if (st != SCOCG_OK) { worst = st; break; }
         Ctrl c;
@@ -508,23 +527,24 @@ extern "C" int scocg_solve(scocg_handle h, const scocg_c128* shifts, int nshift,
         info->n_replace = nrep;
         info->shift_iters = siters;
         info->seconds = total_ms * 1e-3;
-        info->bytes_per_iter = h->bytes_per_iter(mixed, proj_vec != nullptr, M);
+        info->bytes_per_iter = h->bytes_per_iter(prec, proj_vec != nullptr, M);
     }
     return worst;
 }
 
-double scocg_ctx::bytes_per_iter(bool mixed, bool dense_proj, int M) const {
+double scocg_ctx::bytes_per_iter(int prec, bool dense_proj, int M) const {
+    const bool mixed = prec == SCOCG_MIXED;
     // Algorithmic bytes of one seed iteration: H once in the device layout,
     // plus every vector pass the kernel makes (phase A: gather r, read and
     // write q; phase B: read r and q, write r, read each dense c_m; MIXED adds
     // the seed p (read, write) and the compensated x (two vectors read, write)).
-    const double vb = mixed ? 8.0 : 16.0;
+    const double vb = mixed ? 8.0 : 16.0;   // FP64 and compensated FP32 entries are both 16 bytes
     double hbytes;
     if (kind == HandleKind::kHubbard) {
         hbytes = hub.table_bytes;
     } else {
         const Layout L = layout(false);
-        const double rb = mixed ? 4.0 : 8.0;
+        const double rb = prec == SCOCG_FP64 ? 8.0 : 4.0;
         if (L.kind == LayoutKind::kBsr4) hbytes = (double)nslots * 8 * (4 + 16 * rb) + 4.0 * (nunits_bsr + 1);
         else hbytes = (double)nnz * (4 + rb) + 4.0 * (n + 1);
     }

@@ -86,7 +86,7 @@ struct scocg_ctx {
 
     void free_all();
     scocg::Layout layout(bool prefer_csr) const;
-    double bytes_per_iter(bool mixed, bool dense_proj, int M) const;
+    double bytes_per_iter(int prec, bool dense_proj, int M) const;
 };
 
 namespace scocg {

@@ -64,6 +64,7 @@ template <> struct Vec<float> {
 template <typename T> __device__ __forceinline__ T vzero();
 template <> __device__ __forceinline__ double2 vzero<double2>() { return make_double2(0.0, 0.0); }
 template <> __device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ float4 vzero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
 // acc += v * x for a real value v and a complex x (FMA in the vector's precision)
 __device__ __forceinline__ void cfma_r(double2& acc, double v, double2 x) {
@@ -81,6 +82,29 @@ __device__ __forceinline__ float2 vcfma(float2 a, float2 b, float2 c) {
 }
 __device__ __forceinline__ double2 vsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 vsub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+// ---------------------------------------------------------------- compensated FP32
+}  // namespace scocg
+#include "dfloat.cuh"
+namespace scocg {
+
+// Precision tag of the compensated mode: vectors of float4 {re.hi, im.hi,
+// re.lo, im.lo}, FP32 H values, FP32 arithmetic with error-free transforms.
+struct DF {};
+template <> struct Vec<DF> {
+    using T = float4;
+    __device__ static __forceinline__ T make(double2 a) { return df_from(a); }
+    __device__ static __forceinline__ double2 wide(T a) { return df_to(a); }
+};
+// H value type of each precision
+template <typename R> struct ValT { using T = R; };
+template <> struct ValT<DF> { using T = float; };
+// per-thread accumulator type of the dot products
+template <typename R> struct Acc { using T = R; };
+template <> struct Acc<DF> { using T = dfs; };
+__device__ __forceinline__ double to_double(float v) { return (double)v; }
+__device__ __forceinline__ double to_double(double v) { return v; }
+__device__ __forceinline__ double to_double(dfs v) { return (double)v.hi + (double)v.lo; }
 
 // ---------------------------------------------------------------- loads
 // Streaming loads for H (read once per iteration, larger than L2): evict first.

@@ -19,24 +19,27 @@ static int occupancy_of() {
     return nb;
 }
 
-template <typename R>
-static const R* pick(const Layout& h, const double* d, const float* f);
+// H values of each precision: FP64 for FP64 vectors, FP32 otherwise
+template <typename W>
+static const W* pick(const Layout& h, const double* d, const float* f);
 template <> const double* pick<double>(const Layout&, const double* d, const float*) { return d; }
 template <> const float* pick<float>(const Layout&, const double*, const float* f) { return f; }
 
 template <typename R>
 static int dispatch_occ(const Layout& h) {
+    using W = typename ValT<R>::T;
     switch (h.kind) {
-        case LayoutKind::kBsr4: return occupancy_of<R, ApplyBSR4<R>>();
-        case LayoutKind::kCsr1: return occupancy_of<R, ApplyCSR<R, 1>>();
-        case LayoutKind::kCsr4: return occupancy_of<R, ApplyCSR<R, 4>>();
-        case LayoutKind::kCsr16: return occupancy_of<R, ApplyCSR<R, 16>>();
+        case LayoutKind::kBsr4: return occupancy_of<R, ApplyBSR4<W>>();
+        case LayoutKind::kCsr1: return occupancy_of<R, ApplyCSR<W, 1>>();
+        case LayoutKind::kCsr4: return occupancy_of<R, ApplyCSR<W, 4>>();
+        case LayoutKind::kCsr16: return occupancy_of<R, ApplyCSR<W, 16>>();
     }
     return 0;
 }
 
-int max_coresident_ctas(const Layout& h, bool mixed, int num_sms) {
-    const int occ = mixed ? dispatch_occ<float>(h) : dispatch_occ<double>(h);
+int max_coresident_ctas(const Layout& h, int precision, int num_sms) {
+    const int occ = precision == SCOCG_MIXED ? dispatch_occ<float>(h)
+                  : precision == SCOCG_MIXED_DF ? dispatch_occ<DF>(h) : dispatch_occ<double>(h);
     return occ * num_sms;
 }
 
@@ -52,21 +55,22 @@ int rows_per_unit(LayoutKind k) {
 
 template <typename R>
 cudaError_t launch_solve(const SolveArgs<R>& a, const Layout& h, int grid, cudaStream_t st) {
+    using W = typename ValT<R>::T;
     switch (h.kind) {
         case LayoutKind::kBsr4: {
-            ApplyBSR4<R> ap{h.unit_off, h.bcol, pick<R>(h, h.bval64, h.bval32), h.n, h.nslots, a.dbg};
+            ApplyBSR4<W> ap{h.unit_off, h.bcol, pick<W>(h, h.bval64, h.bval32), h.n, h.nslots, a.dbg};
             return coop_launch(a, ap, grid, st);
         }
         case LayoutKind::kCsr1: {
-            ApplyCSR<R, 1> ap{h.rowptr, h.col, pick<R>(h, h.val64, h.val32), h.n, h.nnz, a.dbg};
+            ApplyCSR<W, 1> ap{h.rowptr, h.col, pick<W>(h, h.val64, h.val32), h.n, h.nnz, a.dbg};
             return coop_launch(a, ap, grid, st);
         }
         case LayoutKind::kCsr4: {
-            ApplyCSR<R, 4> ap{h.rowptr, h.col, pick<R>(h, h.val64, h.val32), h.n, h.nnz, a.dbg};
+            ApplyCSR<W, 4> ap{h.rowptr, h.col, pick<W>(h, h.val64, h.val32), h.n, h.nnz, a.dbg};
             return coop_launch(a, ap, grid, st);
         }
         case LayoutKind::kCsr16: {
-            ApplyCSR<R, 16> ap{h.rowptr, h.col, pick<R>(h, h.val64, h.val32), h.n, h.nnz, a.dbg};
+            ApplyCSR<W, 16> ap{h.rowptr, h.col, pick<W>(h, h.val64, h.val32), h.n, h.nnz, a.dbg};
             return coop_launch(a, ap, grid, st);
         }
     }
@@ -74,6 +78,7 @@ cudaError_t launch_solve(const SolveArgs<R>& a, const Layout& h, int grid, cudaS
 }
 template cudaError_t launch_solve<double>(const SolveArgs<double>&, const Layout&, int, cudaStream_t);
 template cudaError_t launch_solve<float>(const SolveArgs<float>&, const Layout&, int, cudaStream_t);
+template cudaError_t launch_solve<DF>(const SolveArgs<DF>&, const Layout&, int, cudaStream_t);
 
 // ---------------------------------------------------------------- one apply
 template <typename R, typename VV, class Apply>
@@ -108,11 +113,13 @@ static cudaError_t apply_dispatch(const Layout& h, int64_t nunits, VV zs, const 
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_apply(const Layout& h, bool mixed, double2 z, const void* x, void* y, cudaStream_t st) {
+cudaError_t launch_apply(const Layout& h, int precision, double2 z, const void* x, void* y, cudaStream_t st) {
     const int64_t nunits = (h.n + rows_per_unit(h.kind) - 1) / rows_per_unit(h.kind);
-    if (mixed)
+    if (precision == SCOCG_MIXED)
         return apply_dispatch<float, float2>(h, nunits, make_float2((float)z.x, (float)z.y), (const float2*)x,
                                              (float2*)y, st);
+    if (precision == SCOCG_MIXED_DF)
+        return apply_dispatch<float, float4>(h, nunits, df_from(z), (const float4*)x, (float4*)y, st);
     return apply_dispatch<double, double2>(h, nunits, z, (const double2*)x, (double2*)y, st);
 }
 

@@ -70,6 +70,9 @@ __device__ __forceinline__ void load4(const float2* p, float2 (&x)[4]) {
 __device__ __forceinline__ void load4(const double2* p, double2 (&x)[4]) {
     x[0] = p[0]; x[1] = p[1]; x[2] = p[2]; x[3] = p[3];
 }
+__device__ __forceinline__ void load4(const float4* p, float4 (&x)[4]) {
+    x[0] = p[0]; x[1] = p[1]; x[2] = p[2]; x[3] = p[3];
+}
 
 template <typename R, int LPR>
 struct ApplyCSR {

@@ -1,6 +1,8 @@
 // Body of the persistent single-right-hand-side shifted-COCG kernel.  See
 // solver.cuh for the algorithm; this file holds the phases.
 #pragma once
+#include <type_traits>
+
 #include "solver.cuh"
 
 namespace scocg {
@@ -13,7 +15,7 @@ __device__ __forceinline__ void block_sum_n(T (&v)[NV], double* scratch, double*
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
         const T t = warp_sum(v[j]);
-        if (lane == 0) scratch[warp * NV + j] = (double)t;
+        if (lane == 0) scratch[warp * NV + j] = to_double(t);
     }
     __syncthreads();
     if (threadIdx.x < NV) {
@@ -33,10 +35,22 @@ __device__ __forceinline__ void acc_bil(float& re, float& im, float2 u, float2 v
 }
 __device__ __forceinline__ void acc_nrm(double& s, double2 u) { s = fma(u.x, u.x, fma(u.y, u.y, s)); }
 __device__ __forceinline__ void acc_nrm(float& s, float2 u) { s = fmaf(u.x, u.x, fmaf(u.y, u.y, s)); }
+// compensated: products exact to DF, sums with TwoSum
+__device__ __forceinline__ void acc_bil(dfs& re, dfs& im, float4 u, float4 v) {
+    df_acc_prod(re, cre(u), cre(v));
+    df_acc_prod(re, df_neg(cim(u)), cim(v));
+    df_acc_prod(im, cre(u), cim(v));
+    df_acc_prod(im, cim(u), cre(v));
+}
+__device__ __forceinline__ void acc_nrm(dfs& s, float4 u) {
+    df_acc_prod(s, cre(u), cre(u));
+    df_acc_prod(s, cim(u), cim(u));
+}
 
 // Per-thread accumulation of the r partials: rho = r^T r, ||r||^2, c_0^T r.
 template <typename R>
-__device__ __forceinline__ void acc_r(R (&acc)[5], typename Vec<R>::T ri, const typename Vec<R>::T* c0) {
+__device__ __forceinline__ void acc_r(typename Acc<R>::T (&acc)[5], typename Vec<R>::T ri,
+                                     const typename Vec<R>::T* c0) {
     acc_bil(acc[0], acc[1], ri, ri);
     acc_nrm(acc[2], ri);
     if (c0) acc_bil(acc[3], acc[4], *c0, ri);
@@ -45,14 +59,16 @@ __device__ __forceinline__ void acc_r(R (&acc)[5], typename Vec<R>::T ri, const 
 // CTA sum of the accumulated partials into part[0..5); the extra dense
 // projections m >= 1 are summed in separate passes over r into part[3 + 2m].
 template <typename R>
-__device__ __forceinline__ void finish_r_partials(const SolveArgs<R>& a, const R (&acc)[5], int64_t rbeg,
-                                                  int64_t rend, SeedScalars& s, double* s_part, double* part) {
+__device__ __forceinline__ void finish_r_partials(const SolveArgs<R>& a, const typename Acc<R>::T (&acc)[5],
+                                                  int64_t rbeg, int64_t rend, SeedScalars& s, double* s_part,
+                                                  double* part) {
+    using AT = typename Acc<R>::T;
     const int tid = threadIdx.x;
-    R v[5] = {acc[0], acc[1], acc[2], acc[3], acc[4]};
+    AT v[5] = {acc[0], acc[1], acc[2], acc[3], acc[4]};
     block_sum_n<5>(v, s.scratch, s_part);
     if (tid < 5) part[tid] = s_part[tid];
     for (int m = 1; m < a.nproj && a.cvec; ++m) {
-        R w2[2] = {0, 0};
+        AT w2[2] = {};
         for (int64_t i = rbeg + tid; i < rend; i += kBlock) acc_bil(w2[0], w2[1], a.cvec[(size_t)m * a.n + i], a.r[i]);
         block_sum_n<2>(w2, s.scratch, s_part);
         if (tid < 2) part[3 + 2 * m + tid] = s_part[tid];
@@ -62,9 +78,9 @@ __device__ __forceinline__ void finish_r_partials(const SolveArgs<R>& a, const R
 template <typename R>
 __device__ __forceinline__ void r_partials(const SolveArgs<R>& a, int64_t rbeg, int64_t rend,
                                            SeedScalars& s, double* s_part, double* part) {
-    R acc[5] = {0, 0, 0, 0, 0};
+    typename Acc<R>::T acc[5] = {};
     for (int64_t i = rbeg + threadIdx.x; i < rend; i += kBlock)
-        acc_r(acc, a.r[i], a.cvec ? a.cvec + i : nullptr);
+        acc_r<R>(acc, a.r[i], a.cvec ? a.cvec + i : nullptr);
     finish_r_partials(a, acc, rbeg, rend, s, s_part, part);
 }
 
@@ -104,7 +120,8 @@ constexpr int kGoOn = 0x7fffffff;
 template <typename R, class Apply>
 __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, Apply ap) {
     using V = typename Vec<R>::T;
-    constexpr bool kMixed = sizeof(R) == 4;
+    using AT = typename Acc<R>::T;
+    constexpr bool kMixed = std::is_same<R, float>::value;   // complex64 vectors
     __shared__ SeedScalars s;
     __shared__ double s_part[8];
     __shared__ int s_flag[4];
@@ -196,7 +213,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
         {
             const V zs = Vec<R>::make(s.zs);
             const V bp = Vec<R>::make(s.beta_prev);
-            R rq[2] = {0, 0};
+            AT rq[2] = {};
             for (int64_t u = u_first; u < u_end; u += u_step) {
                 int64_t row;
                 V w;
@@ -245,7 +262,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
             const V al = Vec<R>::make(s.alpha);
             const V bp = Vec<R>::make(s.beta_prev);
             const bool track_x = kMixed && s.replace_on;
-            R acc[5] = {0, 0, 0, 0, 0};
+            AT acc[5] = {};
             for (int64_t i = rbeg + tid; i < rend; i += kBlock) {
                 const V ro = a.r[i];
                 if constexpr (kMixed) {
@@ -266,7 +283,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
                 }
                 const V rn = vsub(ro, vcfma(al, a.q[i], vzero<V>()));
                 a.r[i] = rn;
-                acc_r(acc, rn, a.cvec ? a.cvec + i : nullptr);
+                acc_r<R>(acc, rn, a.cvec ? a.cvec + i : nullptr);
             }
             __syncthreads();
             finish_r_partials(a, acc, rbeg, rend, s, s_part, myB);

@@ -29,11 +29,11 @@ struct Layout {
 };
 
 int rows_per_unit(LayoutKind k);
-int max_coresident_ctas(const Layout& h, bool mixed, int num_sms);
+int max_coresident_ctas(const Layout& h, int precision, int num_sms);
 
 template <typename R>
 cudaError_t launch_solve(const SolveArgs<R>& a, const Layout& h, int grid, cudaStream_t st);
 
-cudaError_t launch_apply(const Layout& h, bool mixed, double2 z, const void* x, void* y, cudaStream_t st);
+cudaError_t launch_apply(const Layout& h, int precision, double2 z, const void* x, void* y, cudaStream_t st);
 
 }  // namespace scocg

@@ -22,7 +22,7 @@ LIB_PATH = Path(__file__).resolve().parent / "_build" / (
 
 OK, NOT_CONVERGED = 0, 1
 ERR_INVALID, ERR_CUDA, ERR_OOM, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_UNSYMMETRIC = -1, -2, -3, -4, -5, -6
-FP64, MIXED = 0, 1
+FP64, MIXED, MIXED_DF = 0, 1, 2
 
 EXPORTED = [
     "scocg_create_csr", "scocg_create_hubbard", "scocg_dim", "scocg_set_opts", "scocg_apply",
@@ -198,11 +198,12 @@ def scocg_set_opts(h: Handle, opts: SolveOptions) -> None:
 
 
 def scocg_apply(h: Handle, z: complex, x, precision: int = FP64):
-    """y = (z I - H) x; x is a CUDA complex128 (FP64) or complex64 (MIXED) tensor."""
+    """y = (z I - H) x; x is a CUDA complex128 (FP64), complex64 (MIXED) or
+    float32 [N, 4] {re.hi, im.hi, re.lo, im.lo} (MIXED_DF) tensor."""
     import torch
-    want = torch.complex64 if precision == MIXED else torch.complex128
-    if x.dtype != want or not x.is_cuda:
-        raise TypeError(f"x must be a CUDA {want} tensor")
+    want = {FP64: torch.complex128, MIXED: torch.complex64, MIXED_DF: torch.float32}[precision]
+    if x.dtype != want or not x.is_cuda or (precision == MIXED_DF and x.shape[-1] != 4):
+        raise TypeError(f"x must be a CUDA {want} tensor" + (" of shape [N, 4]" if precision == MIXED_DF else ""))
     x = x.contiguous()
     y = torch.empty_like(x)
     _check(lib().scocg_apply(h.ptr, c128(float(np.real(z)), float(np.imag(z))), _dev(x), _dev(y), precision),

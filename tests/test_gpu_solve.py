@@ -254,3 +254,71 @@ def test_config2_full_size_fixed_iterations(S, oracle_mod):
     gm, infom = gpu_solve(S, h, wl.shifts, wl.rhs[0], proj_vec=wl.proj_vec, tol=0.0,
                           opts=S.SolveOptions(max_iter=n_it, precision=S.MIXED))
     assert relerr(gm[:, sample], ref.G) < 2e-3
+
+
+# ------------------------------------------------------------------ compensated FP32
+def to_df(x):
+    """complex128 [N] -> float32 [N, 4] {re.hi, im.hi, re.lo, im.lo} (hi + lo split)."""
+    hi = x.astype(np.complex64)
+    lo = (x - hi.astype(np.complex128)).astype(np.complex64)
+    return np.stack([hi.real, hi.imag, lo.real, lo.imag], axis=1).astype(np.float32)
+
+
+def from_df(v):
+    v = v.astype(np.float64)
+    return (v[:, 0] + v[:, 2]) + 1j * (v[:, 1] + v[:, 3])
+
+
+@pytest.mark.parametrize("layout", [0, 1])
+def test_apply_df_matches_oracle(S, oracle_mod, layout):
+    """Compensated FP32 apply: FP32 values of H (exact here) times hi+lo vectors."""
+    h_csr = inputs.anderson_csr(5, seed=3)
+    h = S.scocg_create_csr(h_csr.rowptr, h_csr.col, h_csr.val, opts=S.SolveOptions(layout=layout))
+    x = inputs.random_unit_complex(h_csr.n, 4)
+    xd = to_df(x)
+    z = 0.37 + 0.011j
+    y = from_df(S.scocg_apply(h, z, cuda(xd), precision=S.MIXED_DF).cpu().numpy())
+    ref = oracle_mod.apply_shifted(h_csr.rowptr, h_csr.col, h_csr.val, z, from_df(xd))
+    assert np.max(np.abs(y - ref)) <= 1e-12 * np.max(np.abs(ref))
+    S.scocg_destroy(h)
+
+
+def test_df_converged_matches_oracle(S, oracle_mod):
+    """Compensated FP32 vectors reach FP64-level results: converged G to 1e-8."""
+    h = inputs.anderson_csr(6, seed=5)
+    b = inputs.random_unit_complex(h.n, 9)
+    shifts = np.linspace(-5, 5, 32) + 0.05j
+    ref = oracle_mod.shifted_cocg(h.rowptr, h.col, h.val, shifts, b, proj_vec=[np.conj(b)], tol=1e-12)
+    g, info = gpu_solve(S, h, shifts, b, proj_vec=[np.conj(b)], tol=1e-12,
+                        opts=S.SolveOptions(precision=S.MIXED_DF))
+    assert info["status"] == 0
+    assert relerr(g, ref.G) < 1e-8
+    exact = dense.green_dense(h.dense(), shifts, b, [np.conj(b)])
+    assert relerr(g, exact) < 1e-8
+
+
+def test_df_switching_and_unit_projections(S, oracle_mod):
+    h = inputs.anderson_csr(4, seed=17)
+    b = inputs.random_unit_complex(h.n, 11)
+    shifts = np.concatenate([[30.0 + 1.0j], np.linspace(-3, 3, 6) + 0.02j, [-25.0 + 0.5j]])
+    g, info = gpu_solve(S, h, shifts, b, proj_idx=[0, 9, h.n - 1], tol=1e-11,
+                        opts=S.SolveOptions(seed=0, precision=S.MIXED_DF))
+    assert info["status"] == 0 and info["n_switch"] >= 1
+    C = np.zeros((3, h.n), complex); C[0, 0] = C[1, 9] = C[2, h.n - 1] = 1
+    exact = dense.green_dense(h.dense(), shifts, b, C)
+    assert relerr(g, exact) < 1e-7
+
+
+def test_config2_full_size_df(S, oracle_mod):
+    """64^3 x 4 Anderson, 512 shifts, compensated FP32, the bench's launch: 12
+    iterations on a 12-shift sample against the FP64 oracle."""
+    wl = inputs.workload("anderson", "full", bounds=(-6.09, 6.47))
+    h = wl.csr
+    seed = oracle_mod.default_seed(wl.shifts)
+    sample = np.unique(np.concatenate([[seed], np.linspace(0, 511, 11).astype(int)]))
+    g, info = gpu_solve(S, h, wl.shifts, wl.rhs[0], proj_vec=wl.proj_vec, tol=0.0,
+                        opts=S.SolveOptions(max_iter=12, precision=S.MIXED_DF))
+    ref = oracle_mod.shifted_cocg(h.rowptr, h.col, h.val, wl.shifts[sample], wl.rhs[0],
+                                  proj_vec=wl.proj_vec, tol=0.0, max_iter=12,
+                                  seed=int(np.where(sample == seed)[0][0]))
+    assert relerr(g[:, sample], ref.G) < 1e-9
