@@ -184,6 +184,12 @@ cudaError_t hubbard_launch_solve(const SolveArgs<R>& a, const Hubbard& hb, int g
 }
 template cudaError_t hubbard_launch_solve<double>(const SolveArgs<double>&, const Hubbard&, int, cudaStream_t);
 template cudaError_t hubbard_launch_solve<float>(const SolveArgs<float>&, const Hubbard&, int, cudaStream_t);
+// the compensated FP32 mode is not built for the Hubbard apply (the C ABI
+// rejects it before launching)
+template <>
+cudaError_t hubbard_launch_solve<DF>(const SolveArgs<DF>&, const Hubbard&, int, cudaStream_t) {
+    return cudaErrorNotSupported;
+}
 
 template <typename VV, class Apply>
 __global__ void __launch_bounds__(256) k_hub_apply(Apply ap, int64_t nunits, VV zs, const VV* x, VV* y) {
