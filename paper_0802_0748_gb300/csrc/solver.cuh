@@ -74,6 +74,25 @@ __device__ __forceinline__ void load4(const float4* p, float4 (&x)[4]) {
     x[0] = p[0]; x[1] = p[1]; x[2] = p[2]; x[3] = p[3];
 }
 
+// acc += the accumulator of the lane at distance o (xor), for the row sums
+// split over several lanes
+__device__ __forceinline__ void lane_add(double2& acc, int o) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+}
+__device__ __forceinline__ void lane_add(float2& acc, int o) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+}
+__device__ __forceinline__ void lane_add(float4& acc, int o) {   // compensated: DF sums
+    float4 w;
+    w.x = __shfl_xor_sync(0xffffffffu, acc.x, o);
+    w.y = __shfl_xor_sync(0xffffffffu, acc.y, o);
+    w.z = __shfl_xor_sync(0xffffffffu, acc.z, o);
+    w.w = __shfl_xor_sync(0xffffffffu, acc.w, o);
+    acc = cpack(df_add(df_norm(acc.x, acc.z), df_norm(w.x, w.z)), df_add(df_norm(acc.y, acc.w), df_norm(w.y, w.w)));
+}
+
 template <typename R, int LPR>
 struct ApplyCSR {
     static constexpr int kRowsPerUnit = 32 / LPR;
@@ -100,10 +119,7 @@ struct ApplyCSR {
                 }
         }
 #pragma unroll
-        for (int o = LPR / 2; o > 0; o >>= 1) {
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-        }
+        for (int o = LPR / 2; o > 0; o >>= 1) lane_add(acc, o);
         if (row < n && l == 0) {
             w = vsub(vcfma(zs, x[row], vzero<VV>()), acc);
             return true;
