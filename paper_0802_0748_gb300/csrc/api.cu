@@ -280,8 +280,11 @@ static int solve_one_rhs(scocg_ctx* h, const double2* d_z, int K, int seed, cons
                          const int64_t* d_cidx, const void* cvec, int M, double tol, double2* G,
                          int grid, ShiftState S, double* partA, double* partB, double* partC, int strideB,
                          typename Vec<R>::T* r, typename Vec<R>::T* q, typename Vec<R>::T* pseed,
-                         typename Vec<R>::T* xhi, typename Vec<R>::T* xlo, double2* xd, const Layout& L) {
+                         typename Vec<R>::T* xhi, typename Vec<R>::T* xlo, double2* xd, const Layout& L,
+                         double2* Xf = nullptr, double2* Pf = nullptr) {
     SolveArgs<R> a{};
+    a.Xf = Xf;
+    a.Pf = Pf;
     a.n = h->n;
     a.rows_per_unit = h->kind == HandleKind::kHubbard ? 32 : rows_per_unit(L.kind);
     a.nunits = h->kind == HandleKind::kHubbard ? h->hub.nunits : (h->n + a.rows_per_unit - 1) / a.rows_per_unit;
@@ -300,6 +303,7 @@ static int solve_one_rhs(scocg_ctx* h, const double2* d_z, int K, int seed, cons
     a.sync.count = &h->d_ctrl->count;
     a.sync.status = &h->d_ctrl->status;
     a.sync.timeout_ns = (uint64_t)(h->opts.timeout_ms * 1e6);
+    a.sync.nctas = grid;
     a.stats = &h->d_ctrl->stats;
     a.G = G;
     a.debug_inject = h->opts.debug_inject;
@@ -381,6 +385,17 @@ int algorithmic_bytes_note(void) { return 0; }
 extern "C" int scocg_solve(scocg_handle h, const scocg_c128* shifts, int nshift, const void* rhs, int nrhs,
                            const int64_t* proj_idx, const void* proj_vec, int nproj, double tol,
                            scocg_c128* G_out, scocg_info* info) {
+    if (!h) return SCOCG_ERR_INVALID;
+    return solve_impl(h, shifts, nshift, rhs, nrhs, proj_idx, proj_vec, nproj, tol, G_out, info,
+                      h->opts.precision, nullptr, nullptr);
+}
+
+// The solve driver.  prec selects the vector precision; Xf/Pf (device
+// complex128 [nshift][N] each, FP64 only, one right-hand side) switch on the
+// full-vector mode that forms every shift's solution x_k.
+int scocg::solve_impl(scocg_ctx* h, const scocg_c128* shifts, int nshift, const void* rhs, int nrhs,
+                      const int64_t* proj_idx, const void* proj_vec, int nproj, double tol, scocg_c128* G_out,
+                      scocg_info* info, int prec, double2* Xf, double2* Pf) {
     if (!h || !shifts || nshift < 1 || nshift > 4096 || !rhs || nrhs < 1 || nproj < 1 ||
         nproj > kMaxProj || !G_out || (proj_idx == nullptr) == (proj_vec == nullptr) || !(tol >= 0.0))
         return SCOCG_ERR_INVALID;
@@ -389,7 +404,8 @@ extern "C" int scocg_solve(scocg_handle h, const scocg_c128* shifts, int nshift,
     if (proj_idx)
         for (int64_t j = 0; j < (int64_t)nrhs * nproj; ++j)
             if (proj_idx[j] < 0 || proj_idx[j] >= h->n) return SCOCG_ERR_INVALID;
-    const int prec = h->opts.precision;
+    if (Xf && (prec != SCOCG_FP64 || nrhs != 1 || nshift > kMaxFullShifts || !Pf)) return SCOCG_ERR_INVALID;
+    const size_t dyn_smem = Xf ? (size_t)nshift * kFullSmem : 0;
     const bool mixed = prec == SCOCG_MIXED;
     const bool dfm = prec == SCOCG_MIXED_DF;
     if (dfm && h->kind == HandleKind::kHubbard) return SCOCG_ERR_INVALID;
@@ -399,8 +415,8 @@ extern "C" int scocg_solve(scocg_handle h, const scocg_c128* shifts, int nshift,
     cudaStream_t s = h->stream;
 
     const Layout L = h->kind == HandleKind::kHubbard ? Layout{} : h->layout(false);
-    int maxco = h->kind == HandleKind::kHubbard ? hubbard_max_ctas(h->hub, mixed, h->num_sms)
-                                                 : max_coresident_ctas(L, prec, h->num_sms);
+    int maxco = h->kind == HandleKind::kHubbard ? hubbard_max_ctas(h->hub, mixed, h->num_sms, dyn_smem)
+                                                 : max_coresident_ctas(L, prec, h->num_sms, dyn_smem);
     if (maxco <= 0) return SCOCG_ERR_CUDA;
     const int rpu = h->kind == HandleKind::kHubbard ? 32 : rows_per_unit(L.kind);
     const int64_t nunits = h->kind == HandleKind::kHubbard ? h->hub.nunits : (n + rpu - 1) / rpu;
@@ -487,7 +503,8 @@ extern "C" int scocg_solve(scocg_handle h, const scocg_c128* shifts, int nshift,
                : dfm ? solve_one_rhs<DF>(h, d_z, K, seed, b, ci, cv, M, tol, G, grid, S, partA, partB, partC,
                                          strideB, (float4*)r, (float4*)q, nullptr, nullptr, nullptr, nullptr, L)
                      : solve_one_rhs<double>(h, d_z, K, seed, b, ci, cv, M, tol, G, grid, S, partA, partB, partC,
-                                             strideB, (double2*)r, (double2*)q, nullptr, nullptr, nullptr, nullptr, L);
+                                             strideB, (double2*)r, (double2*)q, nullptr, nullptr, nullptr, nullptr, L,
+                                             Xf, Pf);
         cudaEventRecord(ev1, s);
         if (st != SCOCG_OK) { worst = st; break; }
         Ctrl c;

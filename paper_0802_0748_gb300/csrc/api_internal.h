@@ -97,9 +97,14 @@ int default_seed(const scocg_c128* z, int K);
 
 // Hubbard (hubbard.cu)
 cudaError_t hubbard_apply(const Hubbard& hb, bool mixed, double2 z, const void* x, void* y, cudaStream_t st);
-int hubbard_max_ctas(const Hubbard& hb, bool mixed, int num_sms);
+int hubbard_max_ctas(const Hubbard& hb, bool mixed, int num_sms, size_t dyn_smem = 0);
 template <typename R>
 cudaError_t hubbard_launch_solve(const SolveArgs<R>& a, const Hubbard& hb, int grid, cudaStream_t st);
+
+constexpr int kMaxFullShifts = 512;   // shifts per full-vector launch (dynamic shared memory)
+int solve_impl(scocg_ctx* h, const scocg_c128* shifts, int nshift, const void* rhs, int nrhs,
+               const int64_t* proj_idx, const void* proj_vec, int nproj, double tol, scocg_c128* G_out,
+               scocg_info* info, int prec, double2* Xf, double2* Pf);
 
 // full-vector solve and gradient (adjoint.cu)
 int solve_full_impl(scocg_ctx* h, const scocg_c128* shifts, int nshift, const void* rhs, double tol, void* X_out,

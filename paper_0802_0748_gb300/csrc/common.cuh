@@ -138,8 +138,9 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p) {
 #endif
 
 // ---------------------------------------------------------------- barrier
-// Device-wide barrier for a cooperative (co-resident) grid.  `count` only ever
-// grows: barrier number b completes when it reaches (b + 1) * gridDim.x.  The
+// Barrier over the `nctas` co-resident CTAs of one solve (the whole grid, or
+// one system's share of a multi-system launch).  `count` only ever grows:
+// barrier number b completes when it reaches (b + 1) * nctas.  The
 // wait gives up after `timeout_ns`, records SCOCG_ERR_TIMEOUT in *status and
 // returns false; it also returns false as soon as any CTA has recorded an
 // error, so that every CTA leaves the kernel instead of waiting.
@@ -147,6 +148,7 @@ struct GridSync {
     unsigned long long* count;
     int* status;
     uint64_t timeout_ns;
+    int nctas;
 };
 
 __device__ __forceinline__ bool grid_barrier(const GridSync& g, unsigned long long& epoch,
@@ -155,7 +157,7 @@ __device__ __forceinline__ bool grid_barrier(const GridSync& g, unsigned long lo
     __syncthreads();
     if (threadIdx.x == 0) {
         ++epoch;
-        const unsigned long long target = epoch * gridDim.x;
+        const unsigned long long target = epoch * (unsigned long long)g.nctas;
         __threadfence();
         if (!skip_arrival) atomicAdd(g.count, 1ull);
         int ok = 1;
@@ -232,9 +234,8 @@ __device__ __forceinline__ void block_sum(const double* vals, int nval, double* 
 // j < nval: every CTA computes bit-identical sums (same data, same order).
 // The loads of a lane are issued together (up to 16 per lane, grids up to 512
 // CTAs in one round) so that the reduction costs one L2 round trip.
-__device__ __forceinline__ void grid_sum(const double* part, int stride, int nval, double* out) {
+__device__ __forceinline__ void grid_sum(const double* part, int stride, int nval, double* out, int G) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int G = gridDim.x;
     for (int j = warp; j < nval; j += kWarps) {
         double s = 0.0;
         for (int c0 = 0; c0 < G; c0 += 32 * 16) {

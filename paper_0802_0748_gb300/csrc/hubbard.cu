@@ -165,11 +165,13 @@ static ApplyHubbard<R> make_apply(const Hubbard& hb) {
     return ap;
 }
 
-int hubbard_max_ctas(const Hubbard& hb, bool mixed, int num_sms) {
+int hubbard_max_ctas(const Hubbard& hb, bool mixed, int num_sms, size_t dyn_smem) {
     int nb = 0;
     cudaError_t e = mixed
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cocg_persistent<float, ApplyHubbard<float>>, kBlock, 0)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cocg_persistent<double, ApplyHubbard<double>>, kBlock, 0);
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cocg_persistent<float, ApplyHubbard<float>>, kBlock,
+                                                        dyn_smem)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cocg_persistent<double, ApplyHubbard<double>>, kBlock,
+                                                        dyn_smem);
     (void)hb;
     return e == cudaSuccess ? nb * num_sms : 0;
 }
@@ -179,8 +181,9 @@ cudaError_t hubbard_launch_solve(const SolveArgs<R>& a, const Hubbard& hb, int g
     ApplyHubbard<R> ap = make_apply<R>(hb);
     ap.dbg = a.dbg;
     void* args[] = {(void*)&a, (void*)&ap};
+    const size_t smem = a.Xf ? (size_t)a.K * kFullSmem : 0;
     return cudaLaunchCooperativeKernel((const void*)cocg_persistent<R, ApplyHubbard<R>>, dim3(grid), dim3(kBlock),
-                                       args, 0, st);
+                                       args, smem, st);
 }
 template cudaError_t hubbard_launch_solve<double>(const SolveArgs<double>&, const Hubbard&, int, cudaStream_t);
 template cudaError_t hubbard_launch_solve<float>(const SolveArgs<float>&, const Hubbard&, int, cudaStream_t);

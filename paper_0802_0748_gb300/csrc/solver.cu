@@ -8,13 +8,15 @@ namespace scocg {
 template <typename R, class Apply>
 static cudaError_t coop_launch(const SolveArgs<R>& a, const Apply& ap, int grid, cudaStream_t st) {
     void* args[] = {(void*)&a, (void*)&ap};
-    return cudaLaunchCooperativeKernel((const void*)cocg_persistent<R, Apply>, dim3(grid), dim3(kBlock), args, 0, st);
+    const size_t smem = a.Xf ? (size_t)a.K * kFullSmem : 0;
+    return cudaLaunchCooperativeKernel((const void*)cocg_persistent<R, Apply>, dim3(grid), dim3(kBlock), args, smem,
+                                       st);
 }
 
 template <typename R, class Apply>
-static int occupancy_of() {
+static int occupancy_of(size_t smem) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cocg_persistent<R, Apply>, kBlock, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cocg_persistent<R, Apply>, kBlock, smem) != cudaSuccess)
         return 0;
     return nb;
 }
@@ -26,20 +28,20 @@ template <> const double* pick<double>(const Layout&, const double* d, const flo
 template <> const float* pick<float>(const Layout&, const double*, const float* f) { return f; }
 
 template <typename R>
-static int dispatch_occ(const Layout& h) {
+static int dispatch_occ(const Layout& h, size_t smem) {
     using W = typename ValT<R>::T;
     switch (h.kind) {
-        case LayoutKind::kBsr4: return occupancy_of<R, ApplyBSR4<W>>();
-        case LayoutKind::kCsr1: return occupancy_of<R, ApplyCSR<W, 1>>();
-        case LayoutKind::kCsr4: return occupancy_of<R, ApplyCSR<W, 4>>();
-        case LayoutKind::kCsr16: return occupancy_of<R, ApplyCSR<W, 16>>();
+        case LayoutKind::kBsr4: return occupancy_of<R, ApplyBSR4<W>>(smem);
+        case LayoutKind::kCsr1: return occupancy_of<R, ApplyCSR<W, 1>>(smem);
+        case LayoutKind::kCsr4: return occupancy_of<R, ApplyCSR<W, 4>>(smem);
+        case LayoutKind::kCsr16: return occupancy_of<R, ApplyCSR<W, 16>>(smem);
     }
     return 0;
 }
 
-int max_coresident_ctas(const Layout& h, int precision, int num_sms) {
-    const int occ = precision == SCOCG_MIXED ? dispatch_occ<float>(h)
-                  : precision == SCOCG_MIXED_DF ? dispatch_occ<DF>(h) : dispatch_occ<double>(h);
+int max_coresident_ctas(const Layout& h, int precision, int num_sms, size_t dyn_smem) {
+    const int occ = precision == SCOCG_MIXED ? dispatch_occ<float>(h, dyn_smem)
+                  : precision == SCOCG_MIXED_DF ? dispatch_occ<DF>(h, dyn_smem) : dispatch_occ<double>(h, dyn_smem);
     return occ * num_sms;
 }
 

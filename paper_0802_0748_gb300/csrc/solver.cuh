@@ -236,7 +236,12 @@ struct SolveArgs {
     unsigned long long* dbg;   // checked builds: first out-of-range index
     int* trace;                // checked builds: host-mapped (iteration, phase) per CTA
     unsigned long long* phase_ns;  // phase-timer builds: [grid][8] accumulated ns
+    // full-vector mode (FP64 only): per-shift solutions and directions, [K][n];
+    // needs K * kFullSmem bytes of dynamic shared memory
+    double2* Xf;
+    double2* Pf;
 };
+constexpr int kFullSmem = 3 * 16 + 4;   // per shift: 1/pi_n, beta^k, alpha^k, active flag
 
 // Shared per-CTA copy of the seed scalars; every CTA holds identical values.
 struct SeedScalars {

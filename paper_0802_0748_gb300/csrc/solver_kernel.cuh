@@ -88,7 +88,7 @@ __device__ __forceinline__ void r_partials(const SolveArgs<R>& a, int64_t rbeg, 
 #define SCOCG_TRACE(ph)                                                    \
     do {                                                                   \
         if (threadIdx.x == 0 && a.trace) {                                 \
-            volatile int* t_ = a.trace + 2 * blockIdx.x;                   \
+            volatile int* t_ = a.trace + 2 * cta;                          \
             t_[0] = s.n; t_[1] = (ph);                                     \
             __threadfence_system();                                        \
         }                                                                  \
@@ -105,7 +105,7 @@ __device__ __forceinline__ void r_partials(const SolveArgs<R>& a, int64_t rbeg, 
     do {                                                                   \
         if (threadIdx.x == 0 && a.phase_ns) {                              \
             const uint64_t t_ = globaltimer_ns();                          \
-            a.phase_ns[8 * blockIdx.x + (k)] += t_ - t_mark;               \
+            a.phase_ns[8 * cta + (k)] += t_ - t_mark;                      \
             t_mark = t_;                                                   \
         }                                                                  \
     } while (0)
@@ -117,18 +117,21 @@ __device__ __forceinline__ void r_partials(const SolveArgs<R>& a, int64_t rbeg, 
 // ends the solve with that status (SCOCG_OK is 0, so 0 cannot mean "go on").
 constexpr int kGoOn = 0x7fffffff;
 
+// The whole solve of one system, run by its G co-resident CTAs (this one is
+// number cta among them).
 template <typename R, class Apply>
-__global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, Apply ap) {
+__device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap, const int G, const int cta) {
     using V = typename Vec<R>::T;
     using AT = typename Acc<R>::T;
     constexpr bool kMixed = std::is_same<R, float>::value;   // complex64 vectors
+    constexpr bool kFull = std::is_same<R, double>::value;   // full-vector mode compiled (FP64 only)
     __shared__ SeedScalars s;
     __shared__ double s_part[8];
     __shared__ int s_flag[4];
     __shared__ double s_min[kWarps];
     __shared__ int s_arg[kWarps];
 
-    const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+    const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     // phase A visits units: a contiguous range per CTA, or (strided applies) the
     // units cta + G * (warp + kWarps * j) so that all CTAs sweep the unit space
@@ -161,6 +164,9 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
             if constexpr (kMixed) {
                 a.p_seed[i] = vzero<V>(); a.x_hi[i] = vzero<V>(); a.x_lo[i] = vzero<V>();
             }
+            if constexpr (kFull)
+                if (a.Xf)
+                    for (int k = 0; k < a.K; ++k) { a.Xf[(size_t)k * a.n + i] = c2(0, 0); a.Pf[(size_t)k * a.n + i] = c2(0, 0); }
             nb = fma(bi.x, bi.x, fma(bi.y, bi.y, nb));
         }
         double v1[1] = {nb};
@@ -178,8 +184,8 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
         }
         if (tid < 4) s_flag[tid] = 0;
         if (!grid_barrier(a.sync, epoch)) return;
-        grid_sum(a.partB, a.strideB, nred, s.red);
-        grid_sum(a.partC, kPartC, 1, s.red + nred);
+        grid_sum(a.partB, a.strideB, nred, s.red, G);
+        grid_sum(a.partC, kPartC, 1, s.red + nred, G);
         if (tid == 0) {
             s.rho = c2(s.red[0], s.red[1]);
             s.bnorm = sqrt(s.red[nred]);
@@ -236,7 +242,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
         if (!grid_barrier(a.sync, epoch, a.debug_inject == 1 && cta == 0 && s.n == 3)) return;
         SCOCG_TRACE(3);
         SCOCG_MARK(1);
-        grid_sum(a.partA, 4, 4, s.red);
+        grid_sum(a.partA, 4, 4, s.red, G);
         if (tid == 0) {
             const double2 rq = c2(s.red[0], s.red[1]);
             const int active = s.n == 0 ? a.K : (int)s.red[2];
@@ -257,6 +263,36 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
         __syncthreads();
         if (s_flag[2] != kGoOn) { status = s_flag[2]; break; }
 
+        // ---- full-vector mode: this iteration's shift scalars for all shifts
+        // (every CTA computes them, with the same arithmetic as phase C)
+        if constexpr (kFull) {
+            if (a.Xf) {
+                extern __shared__ double2 s_full[];
+                double2* s_inv = s_full;
+                double2* s_bet = s_full + a.K;
+                double2* s_alp = s_full + 2 * a.K;
+                int* s_act = reinterpret_cast<int*>(s_full + 3 * a.K);
+                const double2 t2 = cdiv(cmul(s.alpha, s.beta_prev), s.alpha_prev);
+                for (int k = tid; k < a.K; k += kBlock) {
+                    int act = 0;
+                    if (!__ldcg(a.S.frozen + k)) {
+                        const double2 pp = __ldcg(a.S.pi_prev + k), pc = __ldcg(a.S.pi_cur + k);
+                        const double2 ic = __ldcg(a.S.inv_cur + k);
+                        const double2 ratio = cmul(pp, ic);
+                        const double2 pn = cadd(cmul(cadd(c2(1, 0), cmul(s.alpha, __ldcg(a.S.sigma + k))), pc),
+                                                cmul(t2, csub(pc, pp)));
+                        const double2 in = crecip(pn);
+                        s_inv[k] = ic;
+                        s_bet[k] = cmul(cmul(ratio, ratio), s.beta_prev);
+                        s_alp[k] = cmul(cmul(pc, in), s.alpha);
+                        act = 1;
+                    }
+                    s_act[k] = act;
+                }
+                __syncthreads();
+            }
+        }
+
         // ---- phase B: r_{n+1} = r_n - alpha_n q_n; partials rho, ||r||^2, c^T r
         {
             const V al = Vec<R>::make(s.alpha);
@@ -265,6 +301,21 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
             AT acc[5] = {};
             for (int64_t i = rbeg + tid; i < rend; i += kBlock) {
                 const V ro = a.r[i];
+                if constexpr (kFull) {
+                    if (a.Xf) {
+                        // p^k_n = r_n / pi^k_n + beta^k_{n-1} p^k_{n-1};  x^k_{n+1} = x^k_n + alpha^k_n p^k_n
+                        extern __shared__ double2 s_full[];
+                        const int* s_act = reinterpret_cast<const int*>(s_full + 3 * a.K);
+                        const double2 rw = Vec<R>::wide(ro);
+                        for (int k = 0; k < a.K; ++k) {
+                            if (!s_act[k]) continue;
+                            const size_t o = (size_t)k * a.n + i;
+                            const double2 p = vcfma(s_full[a.K + k], a.Pf[o], cmul(rw, s_full[k]));
+                            a.Pf[o] = p;
+                            a.Xf[o] = vcfma(s_full[2 * a.K + k], p, a.Xf[o]);
+                        }
+                    }
+                }
                 if constexpr (kMixed) {
                     if (track_x) {
                         // p_n = r_n + beta_{n-1} p_{n-1};  x_{n+1} = x_n + alpha_n p_n (compensated sum)
@@ -293,7 +344,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
         if (!grid_barrier(a.sync, epoch)) return;
         SCOCG_TRACE(5);
         SCOCG_MARK(3);
-        grid_sum(a.partB, a.strideB, nred, s.red);
+        grid_sum(a.partB, a.strideB, nred, s.red, G);
         if (tid < M) {
             s.cr_next[tid] = dense_proj ? c2(s.red[3 + 2 * tid], s.red[4 + 2 * tid])
                                         : (chk(a.dbg, 12, a.cidx[tid], a.n) ? Vec<R>::wide(__ldcg(a.r + a.cidx[tid])) : c2(0, 0));
@@ -478,7 +529,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
                 if (!grid_barrier(a.sync, epoch)) return;
                 r_partials(a, rbeg, rend, s, s_part, myB);
                 if (!grid_barrier(a.sync, epoch)) return;
-                grid_sum(a.partB, a.strideB, nred, s.red);
+                grid_sum(a.partB, a.strideB, nred, s.red, G);
                 if (tid == 0) {
                     s.rho = c2(s.red[0], s.red[1]);
                     s.beta_prev = cdiv(s.rho, s.rho_prev);
@@ -508,6 +559,24 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, App
         a.stats->status = status;
         if (status != SCOCG_OK) atomicCAS(a.sync.status, 0, status);
     }
+}
+
+// One solve on the whole grid.
+template <typename R, class Apply>
+__global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, Apply ap) {
+    cocg_body(a, ap, (int)gridDim.x, (int)blockIdx.x);
+}
+
+// Several independent solves in one launch: CTAs [cta_off[s], cta_off[s+1])
+// run system s with its own arguments, barrier counter and partials.
+template <typename R, class Apply>
+__global__ void __launch_bounds__(kBlock, 2) cocg_multi(const SolveArgs<R>* args, const Apply* aps,
+                                                        const int* cta_off, int nsys) {
+    int sys = 0;
+    while (sys + 1 < nsys && cta_off[sys + 1] <= (int)blockIdx.x) ++sys;
+    const SolveArgs<R> a = args[sys];
+    const Apply ap = aps[sys];
+    cocg_body(a, ap, cta_off[sys + 1] - cta_off[sys], (int)blockIdx.x - cta_off[sys]);
 }
 
 }  // namespace scocg

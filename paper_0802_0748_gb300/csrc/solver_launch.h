@@ -29,7 +29,7 @@ struct Layout {
 };
 
 int rows_per_unit(LayoutKind k);
-int max_coresident_ctas(const Layout& h, int precision, int num_sms);
+int max_coresident_ctas(const Layout& h, int precision, int num_sms, size_t dyn_smem = 0);
 
 template <typename R>
 cudaError_t launch_solve(const SolveArgs<R>& a, const Layout& h, int grid, cudaStream_t st);

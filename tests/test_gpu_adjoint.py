@@ -1,0 +1,160 @@
+"""GPU full-vector solve and adjoint gradient (through the C ABI) against the
+oracle's full-vector solutions, dense references and central finite
+differences."""
+import numpy as np
+import pytest
+
+from paper_0802_0748_gb300 import inputs
+from oracle import dense
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def S():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0802_0748_gb300 import scocg
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return scocg
+
+
+def cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def relerr(a, b):
+    a = np.asarray(a); b = np.asarray(b)
+    return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300)))
+
+
+def test_solve_full_matches_oracle_vectors(S, oracle_mod):
+    """x_k for every shift, element by element, against the oracle's full vectors."""
+    h = inputs.anderson_csr(4, seed=41)
+    b = inputs.random_unit_complex(h.n, 2)
+    shifts = np.linspace(-4, 4, 24) + 0.05j
+    hh = S.scocg_create_csr(h.rowptr, h.col, h.val)
+    X, info = S.scocg_solve_full(hh, shifts, cuda(b), tol=1e-12)
+    S.scocg_destroy(hh)
+    ref = oracle_mod.shifted_cocg(h.rowptr, h.col, h.val, shifts, b, proj_idx=[0], tol=1e-12, want_x=True)
+    Xg = X.cpu().numpy()
+    assert info["status"] == 0
+    assert np.max(np.abs(Xg - ref.X)) < 1e-9 * np.max(np.abs(ref.X))
+    Hd = h.dense()
+    for k in (0, 11, 23):
+        xk = np.linalg.solve(shifts[k] * np.eye(h.n) - Hd, b)
+        assert np.linalg.norm(Xg[k] - xk) < 1e-9 * np.linalg.norm(xk)
+
+
+def test_solve_full_true_residual_full_size(S, oracle_mod):
+    """64^3 x 4 Anderson, 6 shifts, 150 iterations: the true residual b - (z_k - H) x_k
+    (oracle apply on the host) equals the recurrence residual the kernel reports."""
+    wl = inputs.workload("anderson", "full", bounds=(-6.09, 6.47))
+    h = wl.csr
+    shifts = wl.shifts[[0, 100, 255, 256, 400, 511]]
+    hh = S.scocg_create_csr(h.rowptr, h.col, h.val, opts=S.SolveOptions(max_iter=150))
+    X, info = S.scocg_solve_full(hh, shifts, cuda(wl.rhs[0]), tol=0.0)
+    S.scocg_destroy(hh)
+    Xg = X.cpu().numpy()
+    b = wl.rhs[0]
+    for k in range(len(shifts)):
+        tr = b - oracle_mod.apply_shifted(h.rowptr, h.col, h.val, shifts[k], Xg[k])
+        true_rel = np.linalg.norm(tr) / np.linalg.norm(b)
+        assert abs(true_rel - info["resid"][0, k]) <= 1e-8 * max(true_rel, 1e-3), k
+
+
+def test_grad_matches_dense(S):
+    """dL/dval for L = sum_k w_k Im G_00(z_k) against dG/dH_ab = (A^-T c)_a (A^-1 b)_b."""
+    h = inputs.anderson_csr(4, seed=4)
+    n = h.n
+    shifts = np.linspace(-5, 5, 16) + 0.05j
+    w = np.random.default_rng(4).normal(size=16)
+    b = np.zeros(n, complex); b[0] = 1
+    hh = S.scocg_create_csr(h.rowptr, h.col, h.val)
+    gbar = (1j * w).astype(np.complex128)[None, :]
+    g, info = S.scocg_grad(hh, shifts, cuda(b), cuda(gbar), proj_idx=[0], tol=1e-13)
+    S.scocg_destroy(hh)
+    gd = dense.grad_dense(h.dense(), shifts, b, b, gbar[0])
+    rows = np.repeat(np.arange(n), np.diff(h.rowptr))
+    ref = gd[rows, h.col]
+    assert np.max(np.abs(g.cpu().numpy() - ref)) < 1e-8 * np.max(np.abs(ref))
+
+
+def test_grad_dense_projection_adjoint_solve(S):
+    """c != b: the adjoint needs its own full-vector solve."""
+    h = inputs.anderson_csr(3, seed=5)
+    n = h.n
+    shifts = np.linspace(-4, 4, 8) + 0.1j
+    b = inputs.random_unit_complex(n, 1)
+    c = inputs.random_unit_complex(n, 2)
+    gbar = (np.random.default_rng(1).normal(size=8) + 1j * np.random.default_rng(2).normal(size=8))[None, :]
+    hh = S.scocg_create_csr(h.rowptr, h.col, h.val)
+    g, info = S.scocg_grad(hh, shifts, cuda(b), cuda(gbar), proj_vec=cuda(c[None, :]), tol=1e-13)
+    S.scocg_destroy(hh)
+    gd = dense.grad_dense(h.dense(), shifts, b, c, gbar[0])
+    rows = np.repeat(np.arange(n), np.diff(h.rowptr))
+    ref = gd[rows, h.col]
+    assert np.max(np.abs(g.cpu().numpy() - ref)) < 1e-8 * np.max(np.abs(ref))
+
+
+def test_autograd_function_matches_torch_dense(S):
+    """torch.autograd through the solve equals autograd through a dense torch inverse."""
+    from paper_0802_0748_gb300.autograd import shifted_green
+    h = inputs.anderson_csr(3, seed=6)
+    n = h.n
+    shifts = np.linspace(-3, 3, 6) + 0.1j
+    w = torch.tensor(np.random.default_rng(6).normal(size=6))
+    b = np.zeros(n, complex); b[0] = 1
+    val = torch.tensor(h.val, device="cuda", requires_grad=True)
+    G = shifted_green(val, torch.from_numpy(h.rowptr).cuda(), torch.from_numpy(h.col).cuda(), shifts, cuda(b),
+                      proj_idx=[0], tol=1e-13)
+    loss = (w.cuda() * G[0].imag).sum()
+    loss.backward()
+    # dense torch reference on the CPU
+    vt = torch.tensor(h.val, requires_grad=True)
+    rows = torch.from_numpy(np.repeat(np.arange(n), np.diff(h.rowptr)))
+    Hm = torch.zeros(n, n, dtype=torch.float64).index_put((rows, torch.from_numpy(h.col.astype(np.int64))), vt)
+    zs = torch.tensor(shifts)
+    eye = torch.eye(n, dtype=torch.complex128)
+    Gd = torch.stack([torch.linalg.inv(z * eye - Hm.to(torch.complex128))[0, 0] for z in zs])
+    (w * Gd.imag).sum().backward()
+    assert torch.allclose(val.grad.cpu(), vt.grad, rtol=1e-8, atol=1e-10)
+
+
+def test_config4_finite_differences(S):
+    """24^3 x 4 Anderson (55,296 rows), L = sum_k w_k Im G_00(z_k), 128 shifts, eta 0.02:
+    dL/dH on 20 seeded symmetric pairs against central differences (step 1e-6, FP64)."""
+    wl = inputs.workload("adjoint", "full", bounds=(-6.0, 6.4))
+    h = wl.csr
+    w = wl.weights
+    hh = S.scocg_create_csr(h.rowptr, h.col, h.val)
+    gbar = (1j * w).astype(np.complex128)[None, :]
+    b = cuda(wl.rhs[0])
+    g, info = S.scocg_grad(hh, wl.shifts, b, cuda(gbar), proj_idx=[0], tol=1e-13)
+    S.scocg_destroy(hh)
+    g = g.cpu().numpy()
+    assert np.all(np.isfinite(g))
+    rows = np.repeat(np.arange(h.n), np.diff(h.rowptr))
+    big = np.where((np.abs(g) >= 1e-3 * np.abs(g).max()) & (rows <= h.col))[0]
+    pick = np.random.default_rng(4).choice(big, size=20, replace=False)
+
+    def loss(vals):
+        hh2 = S.scocg_create_csr(h.rowptr, h.col, vals)
+        G, inf2 = S.scocg_solve(hh2, wl.shifts, b, proj_idx=[0], tol=1e-14)
+        S.scocg_destroy(hh2)
+        return float(np.sum(w * G.cpu().numpy()[0, 0].imag))
+
+    eps = 1e-6
+    gmax = np.abs(g).max()
+    for v in pick:
+        a_, c_ = rows[v], h.col[v]
+        mirror = np.where((rows == c_) & (h.col == a_))[0][0]
+        vp = h.val.copy(); vm = h.val.copy()
+        vp[v] += eps; vm[v] -= eps
+        if mirror != v:
+            vp[mirror] += eps; vm[mirror] -= eps
+        fd = (loss(vp) - loss(vm)) / (2 * eps)
+        an = g[v] + (g[mirror] if mirror != v else 0.0)
+        assert abs(fd - an) / max(abs(an), 1e-3 * gmax) < 1e-5, (v, fd, an)
