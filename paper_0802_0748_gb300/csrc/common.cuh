@@ -106,6 +106,14 @@ __device__ __forceinline__ double to_double(float v) { return (double)v; }
 __device__ __forceinline__ double to_double(double v) { return v; }
 __device__ __forceinline__ double to_double(dfs v) { return (double)v.hi + (double)v.lo; }
 
+// dynamic shared memory array (the host emulation used for CPU debugging of
+// the kernel source gives it static storage)
+#ifdef SCOCG_HOST_EMULATION
+#define SCOCG_DYN_SHARED(T, name) static T name[16384]
+#else
+#define SCOCG_DYN_SHARED(T, name) extern __shared__ T name[]
+#endif
+
 // ---------------------------------------------------------------- loads
 // Streaming loads for H (read once per iteration, larger than L2): evict first.
 __device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcs(p); }

@@ -130,6 +130,7 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
     __shared__ int s_flag[4];
     __shared__ double s_min[kWarps];
     __shared__ int s_arg[kWarps];
+    SCOCG_DYN_SHARED(double2, s_full);   // full-vector mode: per-shift scalars of the iteration
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -267,7 +268,6 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
         // (every CTA computes them, with the same arithmetic as phase C)
         if constexpr (kFull) {
             if (a.Xf) {
-                extern __shared__ double2 s_full[];
                 double2* s_inv = s_full;
                 double2* s_bet = s_full + a.K;
                 double2* s_alp = s_full + 2 * a.K;
@@ -304,7 +304,6 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
                 if constexpr (kFull) {
                     if (a.Xf) {
                         // p^k_n = r_n / pi^k_n + beta^k_{n-1} p^k_{n-1};  x^k_{n+1} = x^k_n + alpha^k_n p^k_n
-                        extern __shared__ double2 s_full[];
                         const int* s_act = reinterpret_cast<const int*>(s_full + 3 * a.K);
                         const double2 rw = Vec<R>::wide(ro);
                         for (int k = 0; k < a.K; ++k) {
