@@ -52,7 +52,9 @@ typedef enum {
     SCOCG_ERR_OOM = -3,         /* device allocation failed                         */
     SCOCG_ERR_BREAKDOWN = -4,   /* r^T r, r^T A p or a pi^k became zero / not finite */
     SCOCG_ERR_TIMEOUT = -5,     /* a device-wide barrier did not complete in time   */
-    SCOCG_ERR_UNSYMMETRIC = -6  /* CSR input is not structurally/numerically symmetric */
+    SCOCG_ERR_UNSYMMETRIC = -6, /* CSR input is not structurally/numerically symmetric */
+    SCOCG_ERR_TOO_LARGE = -7    /* problem exceeds the fixed scratch of
+                                   scocg_solve_csr_noalloc                          */
 } scocg_status;
 
 typedef enum {
@@ -207,6 +209,41 @@ int scocg_solve_full(scocg_handle h, const scocg_c128 *shifts, int nshift, const
 int scocg_grad(scocg_handle h, const scocg_c128 *shifts, int nshift, const void *rhs, int nrhs,
                const int64_t *proj_idx, const void *proj_vec, int nproj, double tol,
                const scocg_c128 *dL_dG, double *dL_dval, scocg_info *info);
+
+/*
+ * scocg_solve_csr_noalloc -- the FP64 solve of scocg_solve for one right-hand
+ * side, for callers that cannot allocate device memory when they solve (an
+ * application whose memory pool or arena owns all device memory, a real-time
+ * loop that must not take the allocator's locks, a host that reserves all
+ * memory up front).  It takes no handle and allocates nothing: no cudaMalloc,
+ * no cudaFree, no allocating library call.  The paper has no counterpart; this
+ * is an interface for such callers.
+ *
+ * Inputs and outputs belong to the caller:
+ *   n, nnz, rowptr[n+1] (device int32), col[nnz] (device int32), val[nnz]
+ *                        (device double): H in CSR; NOT validated -- H must be
+ *                        real symmetric with in-range indices
+ *   shifts[nshift]       host; rhs device complex128 [n]
+ *   proj_idx[nproj] host int64 | proj_vec device complex128 [nproj][n]
+ *   tol, max_iter (0 -> 100000), G_out device complex128 [nproj][nshift],
+ *   info (optional; info->seconds is 0), cuda_stream (NULL = default stream).
+ * The solve's scratch (r, q, per-shift state, partial sums, control block)
+ * lives in one fixed device array of 24 MiB compiled into the library, which
+ * every GPU that loads the library holds until the process exits.  Problems
+ * whose scratch does not fit return SCOCG_ERR_TOO_LARGE: about
+ * 2 * 16 * n + 120 * nshift * (1 + nproj) bytes plus ~40 KB, i.e. n up to
+ * about 780,000 rows at a few hundred shifts.
+ * The first call on a device looks the array's device address up with
+ * cudaGetSymbolAddress (with that device current); make that first call
+ * before any stream capture.  Every call reuses the same array and leaves its
+ * contents behind (the call clears what must start at zero), so calls whose
+ * work overlaps on the GPU -- from several threads or streams -- race: issue
+ * them one after another.
+ */
+int scocg_solve_csr_noalloc(int64_t n, int64_t nnz, const int32_t *rowptr, const int32_t *col,
+                            const double *val, const scocg_c128 *shifts, int nshift, const void *rhs,
+                            const int64_t *proj_idx, const void *proj_vec, int nproj, double tol,
+                            int max_iter, scocg_c128 *G_out, scocg_info *info, void *cuda_stream);
 
 /* Free the handle and everything it owns (NULL is ignored). */
 void scocg_destroy(scocg_handle h);

@@ -83,6 +83,7 @@ extern "C" const char* scocg_strerror(int code) {
         case SCOCG_ERR_BREAKDOWN: return "COCG breakdown (zero or non-finite r^T r, r^T A p or pi)";
         case SCOCG_ERR_TIMEOUT: return "device barrier timed out";
         case SCOCG_ERR_UNSYMMETRIC: return "matrix is not symmetric";
+        case SCOCG_ERR_TOO_LARGE: return "problem exceeds the fixed scratch of the no-allocation solve";
     }
     return "unknown status";
 }

@@ -21,13 +21,13 @@ LIB_PATH = Path(__file__).resolve().parent / "_build" / (
     f"{_variant}/libscocg.so" if _variant else "libscocg.so")
 
 OK, NOT_CONVERGED = 0, 1
-ERR_INVALID, ERR_CUDA, ERR_OOM, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_UNSYMMETRIC = -1, -2, -3, -4, -5, -6
+ERR_INVALID, ERR_CUDA, ERR_OOM, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_UNSYMMETRIC, ERR_TOO_LARGE = -1, -2, -3, -4, -5, -6, -7
 FP64, MIXED, MIXED_DF = 0, 1, 2
 
 EXPORTED = [
     "scocg_create_csr", "scocg_create_hubbard", "scocg_dim", "scocg_set_opts", "scocg_apply",
     "scocg_solve", "scocg_solve_full", "scocg_grad", "scocg_destroy", "scocg_strerror",
-    "scocg_hubbard_tables",
+    "scocg_hubbard_tables", "scocg_solve_csr_noalloc",
 ]
 
 
@@ -98,6 +98,8 @@ def lib() -> ctypes.CDLL:
         L.scocg_strerror.argtypes = [I]
         L.scocg_strerror.restype = ctypes.c_char_p
         L.scocg_hubbard_tables.argtypes = [P, I, ctypes.POINTER(ctypes.c_int32), P, P, P]
+        L.scocg_solve_csr_noalloc.argtypes = [I64, I64, P, P, P, P, I, P, P, P, I, D, I, P,
+                                              ctypes.POINTER(Info), P]
         for name in EXPORTED:
             if name not in ("scocg_destroy", "scocg_strerror"):
                 getattr(L, name).restype = ctypes.c_int
@@ -329,3 +331,33 @@ def scocg_hubbard_tables(h: Handle, spin: int):
 
 def _hub_slots(h: Handle) -> int:
     return 2 * int(getattr(h, "L"))
+
+
+def scocg_solve_csr_noalloc(rowptr32, col, val, shifts, rhs, proj_idx=None, proj_vec=None, tol: float = 1e-10,
+                            max_iter: int = 0, G_out=None, stream=None):
+    """scocg_solve_csr_noalloc: FP64 solve for callers that cannot allocate
+    device memory; the library itself allocates nothing (its scratch is a fixed
+    device array).  rowptr32/col: CUDA int32, val: CUDA float64, rhs: CUDA
+    complex128 [N], proj_vec: CUDA complex128 [nproj][N] or proj_idx: host ints.
+    G_out (CUDA complex128 [nproj][nshift]) may be passed in so that this call
+    allocates nothing on the torch side either.  Returns (G, info)."""
+    import torch
+    z, zp = _shifts(shifts)
+    K = z.size
+    n = rowptr32.numel() - 1
+    pidx_p = pvec_p = None
+    if proj_idx is not None:
+        pidx = np.ascontiguousarray(np.asarray(proj_idx, dtype=np.int64).ravel())
+        M = pidx.size
+        pidx_p = pidx.ctypes.data
+    else:
+        M = proj_vec.shape[0] if proj_vec.dim() == 2 else 1
+        pvec_p = _dev(proj_vec)
+    if G_out is None:
+        G_out = torch.zeros((M, K), dtype=torch.complex128, device=rhs.device)
+    info, it, rs = _info_struct(1, K)
+    code = lib().scocg_solve_csr_noalloc(n, col.numel(), _dev(rowptr32), _dev(col), _dev(val), zp, K, _dev(rhs),
+                                         pidx_p, pvec_p, M, float(tol), int(max_iter), _dev(G_out),
+                                         ctypes.byref(info), _stream_ptr(stream))
+    _check(code, "scocg_solve_csr_noalloc")
+    return G_out, _info_dict(info, it, rs, 1, K, code)
