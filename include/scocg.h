@@ -211,6 +211,33 @@ int scocg_grad(scocg_handle h, const scocg_c128 *shifts, int nshift, const void 
                const scocg_c128 *dL_dG, double *dL_dval, scocg_info *info);
 
 /*
+ * scocg_solve_multi -- several independent solves (systems of different sizes,
+ * one right-hand side each) in ONE cooperative launch: the GPU's co-resident
+ * CTAs are split among the systems (at least enough for each system's shifts,
+ * otherwise in proportion to its rows) and each system keeps its own barrier
+ * counter, partial sums and seed scalars.  Per system s:
+ *   hs[s]                CSR handle (all: same device, stream, precision and
+ *                        device layout kind)
+ *   shifts[s][nshift[s]] host shifts; rhs[s] device complex128 [N_s]
+ *   proj_idx[s][nproj[s]] host unit projections, or proj_vec[s] device
+ *                        complex128 [nproj[s]][N_s] (one of the two arrays of
+ *                        pointers is NULL)
+ *   G_out[s]             device complex128 [nproj[s]][nshift[s]]
+ *   info                 optional, [nsys] reports (seconds = the whole launch)
+ * use_graph = 1 captures the control-block resets and the launch into a CUDA
+ * graph on the first call and replays it while the handles, sizes and buffer
+ * pointers stay the same (shift values may change; they are copied before
+ * each replay).  One plan is cached per process; scocg_multi_release frees it.
+ * Returns the worst status over the systems.
+ */
+int scocg_solve_multi(int nsys, const scocg_handle *hs, const scocg_c128 *const *shifts, const int *nshift,
+                      const void *const *rhs, const int64_t *const *proj_idx, const void *const *proj_vec,
+                      const int *nproj, double tol, scocg_c128 *const *G_out, scocg_info *info, int use_graph);
+
+/* Free the cached multi-system plan (and its CUDA graph), if any. */
+void scocg_multi_release(void);
+
+/*
  * scocg_solve_csr_noalloc -- the FP64 solve of scocg_solve for one right-hand
  * side, for callers that cannot allocate device memory when they solve (an
  * application whose memory pool or arena owns all device memory, a real-time

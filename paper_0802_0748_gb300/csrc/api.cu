@@ -2,6 +2,7 @@
 // life cycle, argument checks, workspace management and the solve driver
 // that launches the persistent kernels.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -15,6 +16,11 @@ using namespace scocg;
 
 // ---------------------------------------------------------------- helpers
 namespace scocg {
+
+unsigned long long next_generation() {
+    static std::atomic<unsigned long long> g{1};
+    return g.fetch_add(1);
+}
 
 int cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return SCOCG_OK;
@@ -35,6 +41,7 @@ cudaError_t Workspace::reserve(size_t bytes) {
     if (bytes <= cap) return cudaSuccess;
     if (base) cudaFree(base);
     base = nullptr; cap = 0;
+    if (gen) *gen = next_generation();
     cudaError_t e = cudaMalloc(&base, bytes);
     if (e != cudaSuccess) { base = nullptr; return e; }
     cap = bytes;
@@ -101,6 +108,8 @@ int scocg::init_ctx(scocg_ctx* h, const scocg_opts* opts, void* stream) {
     if (!coop) return SCOCG_ERR_CUDA;
     e = cudaMalloc(&h->d_ctrl, sizeof(Ctrl));
     if (e != cudaSuccess) return cuda_status(e);
+    h->ws_gen = next_generation();
+    h->ws.gen = &h->ws_gen;
     return SCOCG_OK;
 }
 
@@ -114,6 +123,7 @@ void scocg_ctx::free_all() {
 
 extern "C" void scocg_destroy(scocg_handle h) {
     if (!h) return;
+    multi_forget(h);
     if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
     h->free_all();
     delete h;

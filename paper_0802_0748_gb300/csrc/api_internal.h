@@ -36,6 +36,7 @@ struct Workspace {
     void* base = nullptr;
     size_t cap = 0;
     size_t off = 0;
+    unsigned long long* gen = nullptr;   // bumped on every (re)allocation
     cudaError_t reserve(size_t bytes);   // resets the carve offset
     void* get(size_t bytes);
     void release();
@@ -83,6 +84,7 @@ struct scocg_ctx {
     // per-solve state
     scocg::Ctrl* d_ctrl = nullptr;
     scocg::Workspace ws;
+    unsigned long long ws_gen = 0;   // changes whenever ws is (re)allocated or the handle is new
 
     void free_all();
     scocg::Layout layout(bool prefer_csr) const;
@@ -91,6 +93,7 @@ struct scocg_ctx {
 
 namespace scocg {
 int cuda_status(cudaError_t e);
+unsigned long long next_generation();
 int init_ctx(scocg_ctx* h, const scocg_opts* opts, void* stream);
 void fill_opts(scocg_opts& o, const scocg_opts* in);
 int default_seed(const scocg_c128* z, int K);
@@ -105,6 +108,9 @@ constexpr int kMaxFullShifts = 512;   // shifts per full-vector launch (dynamic 
 int solve_impl(scocg_ctx* h, const scocg_c128* shifts, int nshift, const void* rhs, int nrhs,
                const int64_t* proj_idx, const void* proj_vec, int nproj, double tol, scocg_c128* G_out,
                scocg_info* info, int prec, double2* Xf, double2* Pf);
+
+// multi-system plans (multi.cu)
+void multi_forget(scocg_ctx* h);
 
 // full-vector solve and gradient (adjoint.cu)
 int solve_full_impl(scocg_ctx* h, const scocg_c128* shifts, int nshift, const void* rhs, double tol, void* X_out,

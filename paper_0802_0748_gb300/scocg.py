@@ -27,7 +27,7 @@ FP64, MIXED, MIXED_DF = 0, 1, 2
 EXPORTED = [
     "scocg_create_csr", "scocg_create_hubbard", "scocg_dim", "scocg_set_opts", "scocg_apply",
     "scocg_solve", "scocg_solve_full", "scocg_grad", "scocg_destroy", "scocg_strerror",
-    "scocg_hubbard_tables", "scocg_solve_csr_noalloc",
+    "scocg_hubbard_tables", "scocg_solve_csr_noalloc", "scocg_solve_multi", "scocg_multi_release",
 ]
 
 
@@ -100,8 +100,11 @@ def lib() -> ctypes.CDLL:
         L.scocg_hubbard_tables.argtypes = [P, I, ctypes.POINTER(ctypes.c_int32), P, P, P]
         L.scocg_solve_csr_noalloc.argtypes = [I64, I64, P, P, P, P, I, P, P, P, I, D, I, P,
                                               ctypes.POINTER(Info), P]
+        L.scocg_solve_multi.argtypes = [I, P, P, P, P, P, P, P, D, P, P, I]
+        L.scocg_multi_release.argtypes = []
+        L.scocg_multi_release.restype = None
         for name in EXPORTED:
-            if name not in ("scocg_destroy", "scocg_strerror"):
+            if name not in ("scocg_destroy", "scocg_strerror", "scocg_multi_release"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -361,3 +364,50 @@ def scocg_solve_csr_noalloc(rowptr32, col, val, shifts, rhs, proj_idx=None, proj
                                          ctypes.byref(info), _stream_ptr(stream))
     _check(code, "scocg_solve_csr_noalloc")
     return G_out, _info_dict(info, it, rs, 1, K, code)
+
+
+def scocg_solve_multi(handles, shifts, rhs, proj_idx=None, proj_vec=None, tol: float = 1e-10,
+                      use_graph: bool = False, G_out=None):
+    """scocg_solve_multi: independent systems in one launch.  handles, shifts,
+    rhs (CUDA complex128 [N_s]) and proj_idx (host [nproj]) or proj_vec (CUDA
+    complex128 [nproj][N_s]) are per-system lists.  Returns ([G_s], [info_s])."""
+    import torch
+    nsys = len(handles)
+    hs = (ctypes.c_void_p * nsys)(*[h.ptr for h in handles])
+    zs = [np.ascontiguousarray(np.asarray(z, dtype=np.complex128)) for z in shifts]
+    zp = (ctypes.c_void_p * nsys)(*[z.ctypes.data for z in zs])
+    ks = (ctypes.c_int * nsys)(*[z.size for z in zs])
+    rhs = [r.reshape(-1).contiguous() for r in rhs]
+    rp = (ctypes.c_void_p * nsys)(*[r.data_ptr() for r in rhs])
+    keep = []
+    if proj_idx is not None:
+        pis = [np.ascontiguousarray(np.asarray(p, dtype=np.int64).ravel()) for p in proj_idx]
+        keep.append(pis)
+        pip = (ctypes.c_void_p * nsys)(*[p.ctypes.data for p in pis])
+        pvp = None
+        ms = [p.size for p in pis]
+    else:
+        pvs = [(p if p.dim() == 2 else p.reshape(1, -1)).contiguous() for p in proj_vec]
+        keep.append(pvs)
+        pvp = (ctypes.c_void_p * nsys)(*[p.data_ptr() for p in pvs])
+        pip = None
+        ms = [p.shape[0] for p in pvs]
+    mp = (ctypes.c_int * nsys)(*ms)
+    if G_out is None:
+        G_out = [torch.zeros((m, z.size), dtype=torch.complex128, device=r.device) for m, z, r in zip(ms, zs, rhs)]
+    gp = (ctypes.c_void_p * nsys)(*[g.data_ptr() for g in G_out])
+    infos = (Info * nsys)()
+    arrays = []
+    for s in range(nsys):
+        it = np.zeros(zs[s].size, dtype=np.int32)
+        rs = np.zeros(zs[s].size, dtype=np.float64)
+        infos[s].freeze_iter = it.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        infos[s].resid = rs.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        arrays.append((it, rs))
+    code = lib().scocg_solve_multi(nsys, hs, zp, ks, rp, pip, pvp, mp, float(tol), gp, infos, int(bool(use_graph)))
+    _check(code, "scocg_solve_multi")
+    return G_out, [_info_dict(infos[s], arrays[s][0], arrays[s][1], 1, zs[s].size, code) for s in range(nsys)]
+
+
+def scocg_multi_release() -> None:
+    lib().scocg_multi_release()
