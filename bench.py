@@ -17,6 +17,18 @@ iteration count; it does not converge at this eta) are reported beside it.
 N > 1 GPUs run independent replicas (the path has no exchange step): value =
 all ranks' shift-iterations / max time.
 
+Two batched legs are timed once beside the headline (``--legs``):
+  batch  32^3 x 4 Anderson (131,072 rows), 256 unit right-hand sides e_j with
+         projection e_j (G_jj at 256 seeded sites) x 256 shifts over the
+         spectrum + 1e-2 i, tol 1e-6, in ONE persistent block launch whose
+         slots share every read of H (slot count and grid from the autotuner);
+         compensated FP32, complex64 and FP64, plus FP64 one right-hand side
+         at a time on a 16-rhs sample;
+  multi  32 independent Anderson clusters of seeded uneven edge 14..50
+         (13,500 to 500,000 rows, 5,118,460 in all), 128 shifts each over
+         [-6.5, 6.5] + 1e-2 i, b seeded unit complex, c = conj(b), tol 1e-6,
+         in one cooperative launch replayed from a CUDA graph.
+
 --impl reference times the CPU oracle (plain FP64 C) on a bounded sample of
 the same workload.
 """
@@ -44,6 +56,8 @@ TOL = 1e-6
 # Spectral bounds of the seed-2 64^3 x 4 Anderson matrix (ARPACK, tol 1e-4),
 # fixed here so every run uses the identical shift list.
 BOUNDS = (-6.086151226927176, 6.469558282777935)
+# The same for the seed-3 32^3 x 4 matrix of the batched leg.
+BATCH_BOUNDS = (-6.041048698881869, 5.997536652116761)
 
 # DRAM traffic per seed iteration of the persistent solve kernel, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum over a 60-iteration
@@ -202,6 +216,97 @@ def fp64_flops_per_iter(n: int, nnz: int, nproj_dense: int) -> float:
     return 4.0 * nnz + n * (8 + 8 + 8 + 8 + 8 + 4 + 8 * nproj_dense)
 
 
+def timed(stream, fn):
+    """(result, milliseconds) of fn() with CUDA events on the launching stream."""
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return out, e0.elapsed_time(e1)
+
+
+def leg_batch(scocg, dev, stream, hbm):
+    """256 right-hand sides x 256 shifts in one block launch per precision."""
+    import numpy as np
+    import torch
+    from paper_0802_0748_gb300 import inputs
+    wl = inputs.workload("batch", "full", bounds=BATCH_BOUNDS)
+    h = wl.csr
+    rp, col, val = (torch.from_numpy(a).to(dev) for a in (h.rowptr, h.col, h.val))
+    rhs = torch.from_numpy(wl.rhs).to(dev)
+    out = {}
+
+    def block(prec, max_iter=0):
+        hh = scocg.scocg_create_csr(rp, col, val, opts=scocg.SolveOptions(precision=prec, autotune=1,
+                                                                            max_iter=max_iter))
+        scocg.scocg_solve(hh, wl.shifts, rhs[:32], proj_idx=wl.proj_idx[:32], tol=wl.tol)   # autotune + warm-up
+        (G, info), ms = timed(stream, lambda: scocg.scocg_solve(hh, wl.shifts, rhs, proj_idx=wl.proj_idx,
+                                                                tol=wl.tol))
+        scocg.scocg_destroy(hh)
+        gbs = info["bytes_per_iter"] * info["iters"] / info["seconds"] / 1e9
+        return G.cpu().numpy(), info, {
+            "value": info["shift_iters"] / (ms * 1e-3), "unit": UNIT, "ms": ms, "status": info["status"],
+            "block_iters": info["iters"], "kernel_s": info["seconds"], "hbm_GBs_algorithmic": gbs,
+            "hbm_frac": gbs / hbm, "bytes_per_block_iter": info["bytes_per_iter"],
+            "max_iters_per_rhs": int(info["freeze_iter"].max())}
+
+    G_df, i_df, out["df"] = block(2)
+    # complex64 does not converge to 1e-6 at eta 1e-2: capped at the compensated
+    # mode's largest per-right-hand-side iteration count
+    G_mx, _, out["mixed"] = block(1, max_iter=out["df"]["max_iters_per_rhs"])
+    out["mixed"]["max_iter_cap"] = out["df"]["max_iters_per_rhs"]
+    # FP64, one right-hand side per launch, on a 16-rhs sample (a rate, so a sample suffices)
+    hh = scocg.scocg_create_csr(rp, col, val, opts=scocg.SolveOptions(precision=0, rhs_tile=1))
+    scocg.scocg_solve(hh, wl.shifts, rhs[:1], proj_idx=wl.proj_idx[:1], tol=wl.tol)
+    (G1, i1), ms1 = timed(stream, lambda: scocg.scocg_solve(hh, wl.shifts, rhs[:16], proj_idx=wl.proj_idx[:16],
+                                                            tol=wl.tol))
+    scocg.scocg_destroy(hh)
+    g64 = G1.cpu().numpy()
+    out["fp64_one_rhs_per_launch"] = {"value": i1["shift_iters"] / (ms1 * 1e-3), "unit": UNIT, "ms": ms1,
+                                      "sample": "first 16 of 256 right-hand sides"}
+    for name, G in (("df", G_df), ("mixed", G_mx)):
+        rel = np.abs(G[:16] - g64) / np.abs(g64)
+        out[name]["max_rel_G_diff_vs_fp64"] = float(rel.max())
+        out[name]["median_rel_G_diff_vs_fp64"] = float(np.median(rel))
+    out["speedup_df_block_vs_fp64_one_rhs"] = out["df"]["value"] / out["fp64_one_rhs_per_launch"]["value"]
+    out["workload"] = ("anderson-32^3x4 (131,072 rows, 3,670,016 nnz), 256 unit rhs (G_jj) x 256 shifts, "
+                       "eta 1e-2, tol 1e-6, one block launch")
+    return out
+
+
+def leg_multi(scocg, dev, stream):
+    """32 uneven clusters in one graph-replayed cooperative launch (compensated FP32)."""
+    import numpy as np
+    import torch
+    from paper_0802_0748_gb300 import inputs
+    Ls = inputs.cluster_sizes(32, 14, 50, seed=31)
+    hs = [inputs.anderson_csr(int(L), seed=3100 + i) for i, L in enumerate(Ls)]
+    shifts = [np.linspace(-6.5, 6.5, 128) + 1e-2j for _ in hs]
+    b = [torch.from_numpy(inputs.random_unit_complex(h.n, 3200 + i)).to(dev) for i, h in enumerate(hs)]
+    c = [torch.conj(x).resolve_conj().reshape(1, -1).contiguous() for x in b]
+    hh = [scocg.scocg_create_csr(h.rowptr, h.col, h.val, opts=scocg.SolveOptions(precision=2)) for h in hs]
+    G_out = [torch.zeros((1, 128), dtype=torch.complex128, device=dev) for _ in hs]
+    try:
+        scocg.scocg_solve_multi(hh, shifts, b, proj_vec=c, tol=TOL, use_graph=True, G_out=G_out)   # capture
+        (G, infos), ms = timed(stream, lambda: scocg.scocg_solve_multi(hh, shifts, b, proj_vec=c, tol=TOL,
+                                                                        use_graph=True, G_out=G_out))
+    finally:
+        scocg.scocg_multi_release()
+        for x in hh:
+            scocg.scocg_destroy(x)
+    siters = sum(i["shift_iters"] for i in infos)
+    bytes_all = sum(i["bytes_per_iter"] * i["iters"] for i in infos)
+    return {"value": siters / (ms * 1e-3), "unit": UNIT, "ms": ms, "precision": "df",
+            "status": max(i["status"] for i in infos), "iters_min": min(i["iters"] for i in infos),
+            "iters_max": max(i["iters"] for i in infos),
+            "hbm_GBs_algorithmic": bytes_all / (ms * 1e-3) / 1e9,
+            "workload": (f"32 Anderson clusters, edge 14..50 (seed 31), {sum(h.n for h in hs):,} rows in all, "
+                         "128 shifts each, eta 1e-2, tol 1e-6, one cooperative launch replayed from a CUDA graph")}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -212,6 +317,7 @@ def main():
     ap.add_argument("--compare", default="fp64,mixed", help="comma list of other precisions timed once beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--max-iter", type=int, default=0, help="cap on seed iterations (0 = to convergence)")
+    ap.add_argument("--legs", default="batch,multi", help="comma list of batched legs timed once beside it")
     args = ap.parse_args()
 
     from paper_0802_0748_gb300 import inputs
@@ -338,6 +444,13 @@ def main():
                         "max_iter_cap": mi, "speedup_vs_main_per_iter": us_per_iter / (io["seconds"] / io["iters"] * 1e6),
                         "max_rel_G_diff_vs_main": float(rel.max()), "median_rel_G_diff_vs_main": float(np.median(rel))}
 
+    legs = {}
+    leg_names = [x for x in args.legs.split(",") if x]
+    if "batch" in leg_names:
+        legs["batch"] = leg_batch(scocg, dev, stream, hbm)
+    if "multi" in leg_names:
+        legs["multi"] = leg_multi(scocg, dev, stream)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
@@ -364,6 +477,8 @@ def main():
                 "gpu_launches": args.steps * (5 + 1 + (1 if prec != scocg.FP64 else 0)),
                 "cpu_baseline": cpu}
         line.update(extra)
+        if legs:
+            line["legs"] = legs
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist

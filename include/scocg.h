@@ -97,6 +97,15 @@ typedef struct {
                                  (the solve must end with SCOCG_ERR_TIMEOUT)
                              2 = poison alpha with NaN at iteration 3 (the solve must
                                  end with SCOCG_ERR_BREAKDOWN)                        */
+    int rhs_tile;         /* right-hand sides solved together ("block" mode: one
+                             persistent launch in which T slots share every read of
+                             H, and a slot whose right-hand side has converged takes
+                             the next one).  Used by scocg_solve for CSR handles when
+                             nrhs > 1, projections are unit vectors (proj_idx,
+                             nproj <= 4) and MIXED residual replacement is off.
+                             0 = automatic (the autotuner's choice when autotune = 1,
+                             else 8, 16 or 32 by nrhs), 1 = one right-hand side at a
+                             time, 8 / 16 / 32 = that many slots                     */
 } scocg_opts;
 
 /* Per-solve report.  The two arrays are optional caller-owned HOST buffers of
@@ -179,6 +188,10 @@ int scocg_apply(scocg_handle h, scocg_c128 z, const void *x, void *y, int precis
  *   info                  optional report (may be NULL)
  * Returns SCOCG_OK, SCOCG_NOT_CONVERGED (outputs valid, per-shift residuals in
  * info) or an error.  1 <= nshift <= 4096, 1 <= nproj <= 32 (<= 4 when nrhs > 1).
+ * In block mode (see scocg_opts.rhs_tile) info->iters counts block iterations
+ * (each advances every occupied slot by one seed iteration), info->seed_final
+ * is the last right-hand side's final seed and info->bytes_per_iter is per
+ * block iteration; a right-hand side that breaks down does not stop the others.
  */
 int scocg_solve(scocg_handle h, const scocg_c128 *shifts, int nshift, const void *rhs, int nrhs,
                 const int64_t *proj_idx, const void *proj_vec, int nproj, double tol,

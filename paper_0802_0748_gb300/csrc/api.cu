@@ -61,6 +61,8 @@ void fill_opts(scocg_opts& o, const scocg_opts* in) {
     if (o.timeout_ms <= 0) o.timeout_ms = 10000.0;
     if (o.precision != SCOCG_FP64 && o.precision != SCOCG_MIXED && o.precision != SCOCG_MIXED_DF) o.precision = -1;
     if (o.layout != 0 && o.layout != 1) o.precision = -1;
+    if (o.rhs_tile != 0 && o.rhs_tile != 1 && o.rhs_tile != 8 && o.rhs_tile != 16 && o.rhs_tile != 32)
+        o.precision = -1;
 }
 
 // The seed rule (the method leaves the choice open): smallest Im z, then Re z
@@ -420,6 +422,21 @@ int scocg::solve_impl(scocg_ctx* h, const scocg_c128* shifts, int nshift, const 
     const bool mixed = prec == SCOCG_MIXED;
     const bool dfm = prec == SCOCG_MIXED_DF;
     if (dfm && h->kind == HandleKind::kHubbard) return SCOCG_ERR_INVALID;
+    // several right-hand sides with unit projections: the block kernel
+    if (!Xf && nrhs > 1 && proj_idx && h->kind == HandleKind::kCsr && nproj <= kMaxProjB &&
+        !(mixed && h->opts.replace_every > 0) && h->opts.rhs_tile != 1) {
+        int T = h->opts.rhs_tile, per_sm = 0;
+        if (T == 0) {
+            if (h->opts.autotune) {
+                const int st = block_autotune(h, shifts, nshift, rhs, nrhs, proj_idx, nproj, tol, G_out, prec, &T,
+                                              &per_sm);
+                if (st < 0) return st;
+            } else {
+                T = block_default_tile(nrhs);
+            }
+        }
+        return block_solve(h, shifts, nshift, rhs, nrhs, proj_idx, nproj, tol, G_out, info, prec, T, per_sm);
+    }
     const int64_t n = h->n;
     const int K = nshift, M = nproj;
     const int seed = (h->opts.seed >= 0 && h->opts.seed < K) ? h->opts.seed : default_seed(shifts, K);

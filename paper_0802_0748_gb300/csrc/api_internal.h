@@ -1,5 +1,6 @@
 // Handle structure and internal entry points shared by the C-ABI translation units.
 #pragma once
+#include <vector>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -59,6 +60,14 @@ struct Hubbard {
 
 }  // namespace scocg
 
+namespace scocg {
+// One autotuner decision for block (multi-right-hand-side) solves.
+struct TuneEntry {
+    int prec, K, M, nrhs;   // key: precision, shifts, projections, min(nrhs, 32)
+    int T, per_sm;          // slots per launch, CTAs per SM (0 = occupancy maximum)
+};
+}  // namespace scocg
+
 struct scocg_ctx {
     scocg::HandleKind kind = scocg::HandleKind::kCsr;
     int64_t n = 0, nnz = 0;
@@ -85,6 +94,7 @@ struct scocg_ctx {
     scocg::Ctrl* d_ctrl = nullptr;
     scocg::Workspace ws;
     unsigned long long ws_gen = 0;   // changes whenever ws is (re)allocated or the handle is new
+    std::vector<scocg::TuneEntry> tune;   // autotuner decisions of this handle
 
     void free_all();
     scocg::Layout layout(bool prefer_csr) const;
@@ -93,6 +103,13 @@ struct scocg_ctx {
 
 namespace scocg {
 int cuda_status(cudaError_t e);
+// multi-right-hand-side (block) solves (block.cu)
+int block_default_tile(int nrhs);
+int block_solve(scocg_ctx* h, const scocg_c128* shifts, int K, const void* rhs, int nrhs, const int64_t* proj_idx,
+                int M, double tol, scocg_c128* G_out, scocg_info* info, int prec, int T, int per_sm);
+int block_autotune(scocg_ctx* h, const scocg_c128* shifts, int K, const void* rhs, int nrhs,
+                   const int64_t* proj_idx, int M, double tol, scocg_c128* G_out, int prec, int* T_out,
+                   int* per_sm_out);
 unsigned long long next_generation();
 int init_ctx(scocg_ctx* h, const scocg_opts* opts, void* stream);
 void fill_opts(scocg_opts& o, const scocg_opts* in);

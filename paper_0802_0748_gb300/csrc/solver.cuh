@@ -27,6 +27,7 @@
 
 namespace scocg {
 
+constexpr int kMaxProjB = 4;   // unit projections per right-hand side of a block (multi-rhs) solve
 constexpr int kPartC = 10;   // active, best |pi|, arg, bad, pi_prev, pi_cur, alpha_k of arg
 
 struct ShiftState {          // device arrays, [K] or [K][M]

@@ -45,7 +45,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_iter", ctypes.c_int), ("replace_every", ctypes.c_int),
                 ("seed", ctypes.c_int), ("no_switch", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("timeout_ms", ctypes.c_double), ("layout", ctypes.c_int), ("grid", ctypes.c_int),
-                ("debug_inject", ctypes.c_int)]
+                ("debug_inject", ctypes.c_int), ("rhs_tile", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -67,10 +67,11 @@ class SolveOptions:
     layout: int = 0
     grid: int = 0
     debug_inject: int = 0
+    rhs_tile: int = 0
 
     def c(self) -> Opts:
         return Opts(self.precision, self.max_iter, self.replace_every, self.seed, self.no_switch,
-                    self.autotune, self.timeout_ms, self.layout, self.grid, self.debug_inject)
+                    self.autotune, self.timeout_ms, self.layout, self.grid, self.debug_inject, self.rhs_tile)
 
 
 _lib = None
