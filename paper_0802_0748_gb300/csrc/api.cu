@@ -364,9 +364,11 @@ static int solve_one_rhs(scocg_ctx* h, const double2* d_z, int K, int seed, cons
         double tot[8] = {0};
         for (int c = 0; c < grid; ++c)
             for (int k = 0; k < 8; ++k) tot[k] += (double)((volatile unsigned long long*)h_ns)[8 * c + k];
-        std::fprintf(stderr, "scocg phase ms (CTA average): A %.3f bar1 %.3f red1+B %.3f bar2 %.3f red2+C %.3f tail %.3f\n",
-                     tot[0] / grid * 1e-6, tot[1] / grid * 1e-6, tot[2] / grid * 1e-6, tot[3] / grid * 1e-6,
-                     tot[4] / grid * 1e-6, tot[7] / grid * 1e-6);
+        std::fprintf(stderr,
+                     "scocg phase ms (CTA average): A %.3f bar1 %.3f red1 %.3f B %.3f bar2 %.3f red2 %.3f C %.3f "
+                     "tail %.3f\n",
+                     tot[0] / grid * 1e-6, tot[1] / grid * 1e-6, tot[6] / grid * 1e-6, tot[2] / grid * 1e-6,
+                     tot[3] / grid * 1e-6, tot[5] / grid * 1e-6, tot[4] / grid * 1e-6, tot[7] / grid * 1e-6);
     }
 #endif
 #ifdef SCOCG_CHECKED

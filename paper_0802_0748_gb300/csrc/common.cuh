@@ -242,6 +242,30 @@ __device__ __forceinline__ void block_sum(const double* vals, int nval, double* 
 // j < nval: every CTA computes bit-identical sums (same data, same order).
 // The loads of a lane are issued together (up to 16 per lane, grids up to 512
 // CTAs in one round) so that the reduction costs one L2 round trip.
+// The same sum over value-major partials part[j * G + cta]: a warp's load of
+// 32 consecutive CTAs is one coalesced request, and the CTAs' reads after a
+// barrier touch G / 32 lines per value instead of G.  Same summation order.
+__device__ __forceinline__ void grid_sum_vm1(const double* part, int nval, double* out, int G) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = warp; j < nval; j += kWarps) {
+        const double* pj = part + (size_t)j * G;
+        double s = 0.0;
+        for (int c0 = 0; c0 < G; c0 += 32 * 16) {
+            double v[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int c = c0 + lane + 32 * u;
+                v[u] = c < G ? __ldcg(pj + c) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 16; ++u) s += v[u];
+        }
+        s = warp_sum(s);
+        if (lane == 0) out[j] = s;
+    }
+    __syncthreads();
+}
+
 __device__ __forceinline__ void grid_sum(const double* part, int stride, int nval, double* out, int G) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int j = warp; j < nval; j += kWarps) {

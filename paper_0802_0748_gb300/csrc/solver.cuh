@@ -226,8 +226,8 @@ struct SolveArgs {
     int max_iter;
     ShiftState S;
     // per-CTA partials
-    double* partA;             // [grid][4]
-    double* partB;             // [grid][strideB]
+    double* partA;             // value-major [4][grid]
+    double* partB;             // value-major [strideB][grid]
     double* partC;             // [grid][kPartC]
     int strideB;
     GridSync sync;
@@ -249,6 +249,8 @@ struct SeedScalars {
     double2 alpha, alpha_prev, beta_prev, rho, rho_prev, zs;
     double2 t2;                 // alpha_n beta_{n-1} / alpha_{n-1}
     double rnorm, bnorm, rn_b;  // rn_b = ||r_{n+1}|| / ||b||
+    double2 beta_next;          // rho_{n+1} / rho_n, before it becomes beta_prev
+    double rnorm_next;          // ||r_{n+1}||, before it becomes rnorm
     int seed, active, n;
     int replace_on, n_switch, n_replace;
     long long shift_iters;

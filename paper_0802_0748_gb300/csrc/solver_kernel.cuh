@@ -56,32 +56,33 @@ __device__ __forceinline__ void acc_r(typename Acc<R>::T (&acc)[5], typename Vec
     if (c0) acc_bil(acc[3], acc[4], *c0, ri);
 }
 
-// CTA sum of the accumulated partials into part[0..5); the extra dense
-// projections m >= 1 are summed in separate passes over r into part[3 + 2m].
+// CTA sum of the accumulated partials into values 0..4 of this CTA's column
+// of the value-major partials (value j at part[j * G]); the extra dense
+// projections m >= 1 are summed in separate passes over r into values 3 + 2m.
 template <typename R>
 __device__ __forceinline__ void finish_r_partials(const SolveArgs<R>& a, const typename Acc<R>::T (&acc)[5],
                                                   int64_t rbeg, int64_t rend, SeedScalars& s, double* s_part,
-                                                  double* part) {
+                                                  double* part, int G) {
     using AT = typename Acc<R>::T;
     const int tid = threadIdx.x;
     AT v[5] = {acc[0], acc[1], acc[2], acc[3], acc[4]};
     block_sum_n<5>(v, s.scratch, s_part);
-    if (tid < 5) part[tid] = s_part[tid];
+    if (tid < 5) part[(size_t)tid * G] = s_part[tid];
     for (int m = 1; m < a.nproj && a.cvec; ++m) {
         AT w2[2] = {};
         for (int64_t i = rbeg + tid; i < rend; i += kBlock) acc_bil(w2[0], w2[1], a.cvec[(size_t)m * a.n + i], a.r[i]);
         block_sum_n<2>(w2, s.scratch, s_part);
-        if (tid < 2) part[3 + 2 * m + tid] = s_part[tid];
+        if (tid < 2) part[(size_t)(3 + 2 * m + tid) * G] = s_part[tid];
     }
 }
 
 template <typename R>
 __device__ __forceinline__ void r_partials(const SolveArgs<R>& a, int64_t rbeg, int64_t rend,
-                                           SeedScalars& s, double* s_part, double* part) {
+                                           SeedScalars& s, double* s_part, double* part, int G) {
     typename Acc<R>::T acc[5] = {};
     for (int64_t i = rbeg + threadIdx.x; i < rend; i += kBlock)
         acc_r<R>(acc, a.r[i], a.cvec ? a.cvec + i : nullptr);
-    finish_r_partials(a, acc, rbeg, rend, s, s_part, part);
+    finish_r_partials(a, acc, rbeg, rend, s, s_part, part, G);
 }
 
 #ifdef SCOCG_CHECKED
@@ -113,6 +114,50 @@ __device__ __forceinline__ void r_partials(const SolveArgs<R>& a, int64_t rbeg, 
 #define SCOCG_MARK(k) do { } while (0)
 #endif
 
+// The inputs of one phase C (the per-shift update of seed iteration n): the
+// seed scalars alpha_n, beta_{n-1}, alpha_n beta_{n-1} / alpha_{n-1},
+// (||r_{n+1}|| / ||b||)^2 and c_m^T r_n.  Phase C can run one iteration late,
+// inside the next phase A, from this copy.
+struct ShiftInputs {
+    double2 alpha, beta_prev, t2;
+    double rn_b2;
+    int n;
+    double2 cr[kMaxProj];
+};
+
+// Phase C for shift k: the pi three-term recurrence, the projected p^k and
+// x^k, the residual estimate and freezing.  Sets bad for a zero or non-finite
+// pi, active when the shift stays unconverged.
+template <typename R>
+__device__ __forceinline__ void shift_update(const SolveArgs<R>& a, int k, const ShiftInputs& c, int M,
+                                             double tol2, int& active, int& bad) {
+    const double2 pp = a.S.pi_prev[k], pc = a.S.pi_cur[k], ic = a.S.inv_cur[k];
+    const double2 ratio = cmul(pp, ic);                        // pi_{n-1} / pi_n
+    const double2 beta_k = cmul(cmul(ratio, ratio), c.beta_prev);
+    const double2 pn = cadd(cmul(cadd(c2(1, 0), cmul(c.alpha, a.S.sigma[k])), pc), cmul(c.t2, csub(pc, pp)));
+    const double2 in = crecip(pn);
+    if (cabs2(pn) == 0.0 || !cfinite(pn) || !cfinite(in)) {
+        bad = 1;
+        return;
+    }
+    const double2 ak = cmul(cmul(pc, in), c.alpha);            // alpha^k_n
+    for (int m = 0; m < M; ++m) {
+        const size_t o = (size_t)k * M + m;
+        const double2 P = cadd(cmul(c.cr[m], ic), cmul(beta_k, a.S.P[o]));
+        a.S.P[o] = P;
+        a.S.X[o] = cadd(a.S.X[o], cmul(ak, P));
+    }
+    a.S.alpha_k[k] = ak;
+    a.S.pi_prev[k] = pc;
+    a.S.pi_cur[k] = pn;
+    a.S.inv_cur[k] = in;
+    const double res2 = c.rn_b2 * cabs2(in);
+    a.S.resid[k] = res2;
+    a.S.iters[k] = c.n + 1;
+    if (a.tol > 0.0 && res2 <= tol2) a.S.frozen[k] = 1;
+    else active = 1;
+}
+
 // Decision word of the per-iteration checks: kGoOn continues, any other value
 // ends the solve with that status (SCOCG_OK is 0, so 0 cannot mean "go on").
 constexpr int kGoOn = 0x7fffffff;
@@ -130,6 +175,7 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
     __shared__ int s_flag[4];
     __shared__ double s_min[kWarps];
     __shared__ int s_arg[kWarps];
+    __shared__ ShiftInputs s_c;          // inputs of a deferred phase C
     SCOCG_DYN_SHARED(double2, s_full);   // full-vector mode: per-shift scalars of the iteration
 
     const int tid = threadIdx.x;
@@ -145,10 +191,18 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
     const int M = a.nproj;
     const bool dense_proj = a.cvec != nullptr;
     const int nred = dense_proj ? 3 + 2 * M : 3;
-    double* myB = a.partB + (size_t)cta * a.strideB;
+    double* myB = a.partB + cta;              // value-major partials: value j at myB[j * G]
     unsigned long long epoch = 0;
     const int k_own = cta + tid * G;          // the shift this thread owns (if < K)
     const bool owns = k_own < a.K;
+    // Phase C may be deferred into the next phase A when every shift owner of
+    // every CTA is in warp 0 (K <= 32 G) and no per-shift vectors are formed:
+    // warp 0 then updates the shifts while the other warps apply H.  Seed
+    // switching needs the shifts of the same iteration, so an iteration whose
+    // seed has converged runs phase C in place.
+    bool defer_ok = a.K <= 32 * G;
+    if constexpr (kFull) defer_ok = defer_ok && a.Xf == nullptr;
+    bool pending = false;                     // a deferred phase C waits for the next phase A
     int status = SCOCG_NOT_CONVERGED;
     bool done = false;
 #ifdef SCOCG_PHASE_TIMERS
@@ -174,7 +228,7 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
         block_sum_n<1>(v1, s.scratch, s_part);
         if (tid == 0) a.partC[(size_t)cta * kPartC] = s_part[0];
         __syncthreads();
-        r_partials(a, rbeg, rend, s, s_part, myB);
+        r_partials(a, rbeg, rend, s, s_part, myB, G);
         if (owns) {
             const int k = k_own;
             a.S.pi_prev[k] = c2(1, 0); a.S.pi_cur[k] = c2(1, 0); a.S.inv_cur[k] = c2(1, 0);
@@ -185,7 +239,7 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
         }
         if (tid < 4) s_flag[tid] = 0;
         if (!grid_barrier(a.sync, epoch)) return;
-        grid_sum(a.partB, a.strideB, nred, s.red, G);
+        grid_sum_vm1(a.partB, nred, s.red, G);
         grid_sum(a.partC, kPartC, 1, s.red + nred, G);
         if (tid == 0) {
             s.rho = c2(s.red[0], s.red[1]);
@@ -217,11 +271,24 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
         SCOCG_TRACE(1);
         SCOCG_MARK(7);
         // ---- phase A: q_n = (z_s - H) r_n + beta_{n-1} q_{n-1}; partial r_n^T q_n
+        // (with a deferred phase C of iteration n-1 in warp 0)
         {
             const V zs = Vec<R>::make(s.zs);
             const V bp = Vec<R>::make(s.beta_prev);
             AT rq[2] = {};
-            for (int64_t u = u_first; u < u_end; u += u_step) {
+            const bool c_here = pending;           // uniform over the grid
+            if (c_here && warp == 0) {
+                int act = 0, bad = 0;
+                if (owns && !a.S.frozen[k_own]) shift_update(a, k_own, s_c, M, a.tol * a.tol, act, bad);
+                act = __popc(__ballot_sync(0xffffffffu, act));
+                bad = __any_sync(0xffffffffu, bad);
+                if (lane == 0) { s_flag[0] = act; s_flag[1] = bad; }
+            }
+            const int nw = c_here ? kWarps - 1 : kWarps;    // warps that apply H
+            const int wi = c_here ? warp - 1 : warp;
+            const int64_t a_first = Apply::kStrided ? (int64_t)cta + (int64_t)G * wi : ubeg + wi;
+            const int64_t a_step = Apply::kStrided ? (int64_t)G * nw : nw;
+            for (int64_t u = a_first; wi >= 0 && u < u_end; u += a_step) {
                 int64_t row;
                 V w;
                 if (ap(u, lane, zs, (const V*)a.r, row, w)) {
@@ -230,12 +297,13 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
                     acc_bil(rq[0], rq[1], a.r[row], qn);
                 }
             }
+            pending = false;
             block_sum_n<2>(rq, s.scratch, s_part);
             if (tid == 0) {
-                double* pa = a.partA + (size_t)cta * 4;
-                pa[0] = s_part[0]; pa[1] = s_part[1];
-                pa[2] = (double)s_flag[0];   // unconverged shifts of this CTA after the last phase C
-                pa[3] = (double)s_flag[1];   // a pi^k of this CTA became zero or non-finite
+                double* pa = a.partA + cta;            // value-major
+                pa[0] = s_part[0]; pa[G] = s_part[1];
+                pa[2 * G] = (double)s_flag[0];   // unconverged shifts of this CTA after the last phase C
+                pa[3 * G] = (double)s_flag[1];   // a pi^k of this CTA became zero or non-finite
             }
         }
         SCOCG_TRACE(2);
@@ -243,7 +311,7 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
         if (!grid_barrier(a.sync, epoch, a.debug_inject == 1 && cta == 0 && s.n == 3)) return;
         SCOCG_TRACE(3);
         SCOCG_MARK(1);
-        grid_sum(a.partA, 4, 4, s.red, G);
+        grid_sum_vm1(a.partA, 4, s.red, G);
         if (tid == 0) {
             const double2 rq = c2(s.red[0], s.red[1]);
             const int active = s.n == 0 ? a.K : (int)s.red[2];
@@ -262,6 +330,7 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
             s_flag[2] = st;
         }
         __syncthreads();
+        SCOCG_MARK(6);
         if (s_flag[2] != kGoOn) { status = s_flag[2]; break; }
 
         // ---- full-vector mode: this iteration's shift scalars for all shifts
@@ -336,72 +405,54 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
                 acc_r<R>(acc, rn, a.cvec ? a.cvec + i : nullptr);
             }
             __syncthreads();
-            finish_r_partials(a, acc, rbeg, rend, s, s_part, myB);
+            finish_r_partials(a, acc, rbeg, rend, s, s_part, myB, G);
         }
         SCOCG_TRACE(4);
         SCOCG_MARK(2);
         if (!grid_barrier(a.sync, epoch)) return;
         SCOCG_TRACE(5);
         SCOCG_MARK(3);
-        grid_sum(a.partB, a.strideB, nred, s.red, G);
+        grid_sum_vm1(a.partB, nred, s.red, G);
+        SCOCG_MARK(5);
+        // the scalars of this iteration: independent FP64 divisions and roots
+        // run in three warps at once
         if (tid < M) {
             s.cr_next[tid] = dense_proj ? c2(s.red[3 + 2 * tid], s.red[4 + 2 * tid])
                                         : (chk(a.dbg, 12, a.cidx[tid], a.n) ? Vec<R>::wide(__ldcg(a.r + a.cidx[tid])) : c2(0, 0));
+            s_c.cr[tid] = s.cr_cur[tid];
         }
         if (tid == 0) {
             s.t2 = cdiv(cmul(s.alpha, s.beta_prev), s.alpha_prev);
-            s.rn_b = sqrt(s.red[2]) / s.bnorm;
+            s_c.alpha = s.alpha; s_c.beta_prev = s.beta_prev; s_c.t2 = s.t2; s_c.n = s.n;
+        } else if (tid == 32) {
+            s.rnorm_next = sqrt(s.red[2]);
+            s.rn_b = s.rnorm_next / s.bnorm;
+            s_c.rn_b2 = s.rn_b * s.rn_b;
+        } else if (tid == 64) {
+            s.beta_next = cdiv(c2(s.red[0], s.red[1]), s.rho);
         }
         __syncthreads();
 
         // ---- phase C: per-shift scalar recurrences for this CTA's shifts
         // (one complex reciprocal per shift; 1/pi^k_n is carried between
-        // iterations and residuals are compared squared)
-        const double2 rho_new = c2(s.red[0], s.red[1]);
-        const double rnorm_new = sqrt(s.red[2]);
+        // iterations and residuals are compared squared), here or deferred
         const double tol2 = a.tol * a.tol;
-        const double rn_b2 = s.rn_b * s.rn_b;
-        const bool seed_conv = a.tol > 0.0 && rn_b2 <= tol2;   // the seed has pi = 1
-        int my_active = 0, my_bad = 0;
-        if (owns && !a.S.frozen[k_own]) {
-            const int k = k_own;
-            const double2 pp = a.S.pi_prev[k], pc = a.S.pi_cur[k], ic = a.S.inv_cur[k];
-            const double2 ratio = cmul(pp, ic);                        // pi_{n-1} / pi_n
-            const double2 beta_k = cmul(cmul(ratio, ratio), s.beta_prev);
-            const double2 pn = cadd(cmul(cadd(c2(1, 0), cmul(s.alpha, a.S.sigma[k])), pc),
-                                    cmul(s.t2, csub(pc, pp)));
-            const double2 in = crecip(pn);
-            if (cabs2(pn) == 0.0 || !cfinite(pn) || !cfinite(in)) {
-                my_bad = 1;
-            } else {
-                const double2 ak = cmul(cmul(pc, in), s.alpha);         // alpha^k_n
-                for (int m = 0; m < M; ++m) {
-                    const size_t o = (size_t)k * M + m;
-                    const double2 P = cadd(cmul(s.cr_cur[m], ic), cmul(beta_k, a.S.P[o]));
-                    a.S.P[o] = P;
-                    a.S.X[o] = cadd(a.S.X[o], cmul(ak, P));
-                }
-                a.S.alpha_k[k] = ak;
-                a.S.pi_prev[k] = pc;
-                a.S.pi_cur[k] = pn;
-                a.S.inv_cur[k] = in;
-                const double res2 = rn_b2 * cabs2(in);
-                a.S.resid[k] = res2;
-                a.S.iters[k] = s.n + 1;
-                if (a.tol > 0.0 && res2 <= tol2) a.S.frozen[k] = 1;
-                else my_active = 1;
-            }
+        const bool seed_conv = a.tol > 0.0 && s_c.rn_b2 <= tol2;   // the seed has pi = 1
+        const bool defer = defer_ok && !seed_conv;
+        if (!defer) {
+            int my_active = 0, my_bad = 0;
+            if (owns && !a.S.frozen[k_own]) shift_update(a, k_own, s_c, M, tol2, my_active, my_bad);
+            const int cnt_active = __syncthreads_count(my_active);
+            const int any_bad = __syncthreads_or(my_bad);
+            if (tid == 0) { s_flag[0] = cnt_active; s_flag[1] = any_bad; }
         }
-        const int cnt_active = __syncthreads_count(my_active);
-        const int any_bad = __syncthreads_or(my_bad);
+        pending = defer;
         if (tid == 0) {
-            s_flag[0] = cnt_active;
-            s_flag[1] = any_bad;
-            s.beta_prev = cdiv(rho_new, s.rho);
+            s.beta_prev = s.beta_next;
             s.alpha_prev = s.alpha;
             s.rho_prev = s.rho;
-            s.rho = rho_new;
-            s.rnorm = rnorm_new;
+            s.rho = c2(s.red[0], s.red[1]);
+            s.rnorm = s.rnorm_next;
             s.n += 1;
         }
         if (tid < M) s.cr_cur[tid] = s.cr_next[tid];
@@ -526,9 +577,9 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
                     }
                 }
                 if (!grid_barrier(a.sync, epoch)) return;
-                r_partials(a, rbeg, rend, s, s_part, myB);
+                r_partials(a, rbeg, rend, s, s_part, myB, G);
                 if (!grid_barrier(a.sync, epoch)) return;
-                grid_sum(a.partB, a.strideB, nred, s.red, G);
+                grid_sum_vm1(a.partB, nred, s.red, G);
                 if (tid == 0) {
                     s.rho = c2(s.red[0], s.red[1]);
                     s.beta_prev = cdiv(s.rho, s.rho_prev);
