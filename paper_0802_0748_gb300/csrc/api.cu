@@ -116,7 +116,7 @@ int scocg::init_ctx(scocg_ctx* h, const scocg_opts* opts, void* stream) {
 }
 
 void scocg_ctx::free_all() {
-    void* ptrs[] = {d_rowptr, d_col, d_val64, d_val32, d_unit_off, d_bcol, d_bval64, d_bval32, d_ctrl,
+    void* ptrs[] = {d_rowptr, d_col, d_val64, d_val32, d_unit_off, d_bcol, d_bval64, d_bval32, d_bval32c, d_ctrl,
                     hub.d_states, hub.d_hop_target, hub.d_hop_sign, hub.d_hop_packed};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -231,10 +231,12 @@ extern "C" int scocg_create_csr(scocg_handle* out, int64_t n, int64_t nnz, const
             if (e == cudaSuccess) e = cudaMalloc(&h->d_bcol, sizeof(int) * 8 * std::max<int64_t>(slots, 1));
             if (e == cudaSuccess) e = cudaMalloc(&h->d_bval64, sizeof(double) * 128 * std::max<int64_t>(slots, 1));
             if (e == cudaSuccess) e = cudaMalloc(&h->d_bval32, sizeof(float) * 128 * std::max<int64_t>(slots, 1));
+            if (e == cudaSuccess) e = cudaMalloc(&h->d_bval32c, sizeof(float) * 128 * std::max<int64_t>(slots, 1));
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(h->d_unit_off, uoff.data(), sizeof(int) * (nunits + 1), cudaMemcpyHostToDevice, s);
             if (e == cudaSuccess)
-                e = convert_bsr4(n, nunits, d_rp, d_c, d_v, h->d_unit_off, h->d_bcol, h->d_bval64, h->d_bval32, s);
+                e = convert_bsr4(n, nunits, d_rp, d_c, d_v, h->d_unit_off, h->d_bcol, h->d_bval64, h->d_bval32,
+                                 h->d_bval32c, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         }
         if (e != cudaSuccess) st = cuda_status(e);
@@ -261,7 +263,7 @@ Layout scocg_ctx::layout(bool prefer_csr) const {
     L.n = n; L.nnz = nnz;
     L.rowptr = d_rowptr; L.col = d_col; L.val64 = d_val64; L.val32 = d_val32;
     L.nunits_bsr = nunits_bsr; L.nslots = nslots;
-    L.unit_off = d_unit_off; L.bcol = d_bcol; L.bval64 = d_bval64; L.bval32 = d_bval32;
+    L.unit_off = d_unit_off; L.bcol = d_bcol; L.bval64 = d_bval64; L.bval32 = d_bval32; L.bval32c = d_bval32c;
     return L;
 }
 

@@ -86,6 +86,7 @@ struct scocg_ctx {
     int* d_bcol = nullptr;
     double* d_bval64 = nullptr;
     float* d_bval32 = nullptr;
+    float* d_bval32c = nullptr;      // the FP32 blocks column-major
     scocg::LayoutKind csr_kind = scocg::LayoutKind::kCsr1;
     int force_kind = -1;       // tuning override of the CSR lanes-per-row layout
     // Hubbard

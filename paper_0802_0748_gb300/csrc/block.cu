@@ -99,6 +99,21 @@ int run_block(scocg_ctx* h, const scocg_c128* shifts, int K, const void* rhs, in
     a.sync.nctas = grid;
     a.stats = &h->d_ctrl->stats;
     a.dbg = h->d_ctrl->dbg;
+    a.phase_ns = nullptr;
+#ifdef SCOCG_PHASE_TIMERS
+    static unsigned long long* h_ns = nullptr;
+    static int h_ns_n = 0;
+    if (h_ns_n < grid) {
+        if (h_ns) cudaFreeHost(h_ns);
+        h_ns = nullptr; h_ns_n = 0;
+        if (cudaHostAlloc((void**)&h_ns, sizeof(unsigned long long) * 8 * grid, cudaHostAllocMapped) == cudaSuccess)
+            h_ns_n = grid;
+    }
+    if (h_ns) {
+        std::memset(h_ns, 0, sizeof(unsigned long long) * 8 * grid);
+        cudaHostGetDevicePointer((void**)&a.phase_ns, h_ns, 0);
+    }
+#endif
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEventCreate(&ev0); cudaEventCreate(&ev1);
@@ -120,6 +135,18 @@ int run_block(scocg_ctx* h, const scocg_c128* shifts, int K, const void* rhs, in
     if (e == cudaSuccess) cudaEventElapsedTime(&ms, ev0, ev1);
     cudaEventDestroy(ev0); cudaEventDestroy(ev1);
     if (e != cudaSuccess) return cuda_status(e);
+#ifdef SCOCG_PHASE_TIMERS
+    if (h_ns) {
+        double tot[8] = {0};
+        for (int cc = 0; cc < grid; ++cc)
+            for (int k = 0; k < 8; ++k) tot[k] += (double)((volatile unsigned long long*)h_ns)[8 * cc + k];
+        std::fprintf(stderr,
+                     "scocg block T=%d grid %d phase ms (CTA average): A %.3f bar1 %.3f decide %.3f B %.3f bar2 %.3f "
+                     "red2 %.3f C %.3f switch+top %.3f\n", T, grid,
+                     tot[0] / grid * 1e-6, tot[1] / grid * 1e-6, tot[6] / grid * 1e-6, tot[2] / grid * 1e-6,
+                     tot[3] / grid * 1e-6, tot[5] / grid * 1e-6, tot[4] / grid * 1e-6, tot[7] / grid * 1e-6);
+    }
+#endif
     if (c.dbg[0]) {
         std::fprintf(stderr, "scocg checked build: out-of-range index at site %llu: %lld (limit %lld)\n", c.dbg[1],
                      (long long)c.dbg[2], (long long)c.dbg[3]);

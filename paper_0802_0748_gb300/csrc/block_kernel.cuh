@@ -72,6 +72,7 @@ struct BlockArgs {
     GridSync sync;
     SolveStats* stats;
     unsigned long long* dbg;
+    unsigned long long* phase_ns;   // phase-timer builds: [grid][8] accumulated ns
 };
 
 template <int T>
@@ -199,7 +200,11 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_block(BlockArgs<R> a) {
 
     bool first = true;
     int nblk = 0;                            // block iterations (every occupied slot advances once)
+#ifdef SCOCG_PHASE_TIMERS
+    uint64_t t_mark = globaltimer_ns();
+#endif
     while (true) {
+        SCOCG_MARK(7);
         if (!first) {
             // ---- phase A: q = (z_s - H) r + beta q per running slot; partial r^T q
             {
@@ -240,7 +245,9 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_block(BlockArgs<R> a) {
                     a.partA[(size_t)(tid * kNvA + 3) * G + cta] = (double)s.bad[tid];
                 }
             }
+            SCOCG_MARK(0);
             if (!grid_barrier(a.sync, epoch)) return;
+            SCOCG_MARK(1);
             grid_sum_vm(a.partA, G, kNvA * T, s.red);
 
             // ---- decide: alpha per running slot, or finish it
@@ -293,6 +300,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_block(BlockArgs<R> a) {
             __syncthreads();
             if (!s.any_live) break;
             ++nblk;
+            SCOCG_MARK(6);
         }
         first = false;
 
@@ -323,7 +331,9 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_block(BlockArgs<R> a) {
             block_cols<T, 3, kNvB>(acc, s.scratch, a.partB, G, cta);
             block_cols<T, 1, kNvB>(nb, s.scratch, a.partB, G, cta, 3);
         }
+        SCOCG_MARK(2);
         if (!grid_barrier(a.sync, epoch)) return;
+        SCOCG_MARK(3);
         grid_sum_vm(a.partB, G, kNvB * T, s.red);
         if (tid < T) {
             const int c = tid;
@@ -352,6 +362,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_block(BlockArgs<R> a) {
             s.cr_next[t] = chk(a.dbg, 24, idx, a.n) ? Vec<R>::wide(__ldcg(a.r + (size_t)idx * T + c)) : c2(0, 0);
         }
         __syncthreads();
+        SCOCG_MARK(5);
 
         // ---- phase C: per (slot, shift) pair
         for (int p = cta + G * tid; p < npairs; p += G * kBlock) {
@@ -413,6 +424,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_block(BlockArgs<R> a) {
             s.key[c] = 0ull; s.arg[c] = INT_MAX;
         }
         for (int t = tid; t < T * M; t += kBlock) s.cr_cur[t] = s.cr_next[t];
+        SCOCG_MARK(4);
 
         // ---- seed switching (Sec. III.C) for the slots whose seed converged
         if (__syncthreads_or(tid < T && s.sw[tid])) {

@@ -91,7 +91,7 @@ __global__ void k_hubbard_tables(int L, int k, int D, int ring, uint32_t* states
 template <typename R>
 struct ApplyHubbard {
     static constexpr int kRowsPerUnit = 32;
-    static constexpr bool kStrided = true;
+    static constexpr int kMap = kMapStrided;
     const uint32_t* st_up;
     const uint32_t* st_dn;
     const int32_t* hop_up;     // packed, [D_up][S]

@@ -95,7 +95,8 @@ __global__ void k_to_csr32(int64_t n, int64_t nnz, const int64_t* rowptr, const 
 // One thread per (block row, slot): slot t of block row B goes to
 // unit u = B / 8, position br = B % 8, slot index unit_off[u] + t.
 __global__ void k_to_bsr4(int64_t nbr, int64_t nunits, const int64_t* rowptr, const int32_t* col,
-                          const double* val, const int* unit_off, int* bcol, double* bv64, float* bv32) {
+                          const double* val, const int* unit_off, int* bcol, double* bv64, float* bv32,
+                          float* bv32c) {
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t u = tid / 8;
     if (u >= nunits) return;
@@ -113,10 +114,11 @@ __global__ void k_to_bsr4(int64_t nbr, int64_t nunits, const int64_t* rowptr, co
                     const double v = val[rowptr[4 * B + r] + 4 * t + c];
                     bv64[slot * 16 + r * 4 + c] = v;
                     bv32[slot * 16 + r * 4 + c] = (float)v;
+                    bv32c[slot * 16 + c * 4 + r] = (float)v;
                 }
         } else {
             bcol[slot] = -1;
-            for (int e = 0; e < 16; ++e) { bv64[slot * 16 + e] = 0.0; bv32[slot * 16 + e] = 0.f; }
+            for (int e = 0; e < 16; ++e) { bv64[slot * 16 + e] = 0.0; bv32[slot * 16 + e] = 0.f; bv32c[slot * 16 + e] = 0.f; }
         }
     }
 }
@@ -151,8 +153,9 @@ cudaError_t convert_csr32(int64_t n, int64_t nnz, const int64_t* rowptr, const i
 }
 
 cudaError_t convert_bsr4(int64_t n, int64_t nunits, const int64_t* rowptr, const int32_t* col, const double* val,
-                         const int* unit_off, int* bcol, double* bv64, float* bv32, cudaStream_t st) {
-    k_to_bsr4<<<grid1(nunits * 8, 256), 256, 0, st>>>(n / 4, nunits, rowptr, col, val, unit_off, bcol, bv64, bv32);
+                         const int* unit_off, int* bcol, double* bv64, float* bv32, float* bv32c, cudaStream_t st) {
+    k_to_bsr4<<<grid1(nunits * 8, 256), 256, 0, st>>>(n / 4, nunits, rowptr, col, val, unit_off, bcol, bv64, bv32,
+                                                      bv32c);
     return cudaGetLastError();
 }
 

@@ -20,6 +20,7 @@ cudaError_t validate_csr(int64_t n, int64_t nnz, const int64_t* d_rowptr, const 
 cudaError_t convert_csr32(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col, const double* val,
                           int* rp32, int* col32, double* v64, float* v32, cudaStream_t st);
 cudaError_t convert_bsr4(int64_t n, int64_t nunits, const int64_t* rowptr, const int32_t* col, const double* val,
-                         const int* unit_off, int* bcol, double* bv64, float* bv32, cudaStream_t st);
+                         const int* unit_off, int* bcol, double* bv64, float* bv32, float* bv32c,
+                         cudaStream_t st);
 
 }  // namespace scocg

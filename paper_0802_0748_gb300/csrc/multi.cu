@@ -32,6 +32,9 @@ template <typename W, class Apply> Apply make_apply(const Layout& L);
 template <> ApplyBSR4<double> make_apply<double, ApplyBSR4<double>>(const Layout& L) {
     return ApplyBSR4<double>{L.unit_off, L.bcol, L.bval64, L.n, L.nslots, nullptr};
 }
+template <> ApplyBSR4C<float> make_apply<float, ApplyBSR4C<float>>(const Layout& L) {
+    return ApplyBSR4C<float>{L.unit_off, L.bcol, L.bval32c, L.n, L.nslots, nullptr};
+}
 template <> ApplyBSR4<float> make_apply<float, ApplyBSR4<float>>(const Layout& L) {
     return ApplyBSR4<float>{L.unit_off, L.bcol, L.bval32, L.n, L.nslots, nullptr};
 }
@@ -343,8 +346,9 @@ int dispatch_layout(LayoutKind kind, int nsys, const scocg_handle* hs, const sco
     using W = typename ValT<R>::T;
     switch (kind) {
         case LayoutKind::kBsr4:
-            return run_multi<R, ApplyBSR4<W>>(nsys, hs, shifts, nshift, rhs, pvec, pidx, nproj, tol, G, info,
-                                              use_graph, prec, &make_apply<W, ApplyBSR4<W>>);
+            return run_multi<R, typename BsrApply<R>::T>(nsys, hs, shifts, nshift, rhs, pvec, pidx, nproj, tol, G,
+                                                         info, use_graph, prec,
+                                                         &make_apply<W, typename BsrApply<R>::T>);
         case LayoutKind::kCsr1:
             return run_multi<R, ApplyCSR<W, 1>>(nsys, hs, shifts, nshift, rhs, pvec, pidx, nproj, tol, G, info,
                                                 use_graph, prec, &make_csr<W, 1>);

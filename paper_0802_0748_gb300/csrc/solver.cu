@@ -1,5 +1,7 @@
 // Instantiations and launch of the persistent shifted-COCG kernel for every
 // (precision, H layout) pair, plus a one-shot apply kernel y = (z - H) x.
+#include <type_traits>
+
 #include "solver_kernel.cuh"
 #include "solver_launch.h"
 
@@ -27,11 +29,23 @@ static const W* pick(const Layout& h, const double* d, const float* f);
 template <> const double* pick<double>(const Layout&, const double* d, const float*) { return d; }
 template <> const float* pick<float>(const Layout&, const double*, const float* f) { return f; }
 
+// The blocked apply of vector precision R on layout h (row lanes on row-major
+// blocks, or column lanes on the column-major copy for complex64 vectors).
+template <typename R>
+static typename BsrApply<R>::T make_bsr(const Layout& h, unsigned long long* dbg) {
+    using W = typename ValT<R>::T;
+    return typename BsrApply<R>::T{h.unit_off, h.bcol, pick<W>(h, h.bval64, h.bval32), h.n, h.nslots, dbg};
+}
+template <>
+ApplyBSR4C<float> make_bsr<float>(const Layout& h, unsigned long long* dbg) {
+    return ApplyBSR4C<float>{h.unit_off, h.bcol, h.bval32c, h.n, h.nslots, dbg};
+}
+
 template <typename R>
 static int dispatch_occ(const Layout& h, size_t smem) {
     using W = typename ValT<R>::T;
     switch (h.kind) {
-        case LayoutKind::kBsr4: return occupancy_of<R, ApplyBSR4<W>>(smem);
+        case LayoutKind::kBsr4: return occupancy_of<R, typename BsrApply<R>::T>(smem);
         case LayoutKind::kCsr1: return occupancy_of<R, ApplyCSR<W, 1>>(smem);
         case LayoutKind::kCsr4: return occupancy_of<R, ApplyCSR<W, 4>>(smem);
         case LayoutKind::kCsr16: return occupancy_of<R, ApplyCSR<W, 16>>(smem);
@@ -59,10 +73,7 @@ template <typename R>
 cudaError_t launch_solve(const SolveArgs<R>& a, const Layout& h, int grid, cudaStream_t st) {
     using W = typename ValT<R>::T;
     switch (h.kind) {
-        case LayoutKind::kBsr4: {
-            ApplyBSR4<W> ap{h.unit_off, h.bcol, pick<W>(h, h.bval64, h.bval32), h.n, h.nslots, a.dbg};
-            return coop_launch(a, ap, grid, st);
-        }
+        case LayoutKind::kBsr4: return coop_launch(a, make_bsr<R>(h, a.dbg), grid, st);
         case LayoutKind::kCsr1: {
             ApplyCSR<W, 1> ap{h.rowptr, h.col, pick<W>(h, h.val64, h.val32), h.n, h.nnz, a.dbg};
             return coop_launch(a, ap, grid, st);
@@ -104,7 +115,10 @@ template <typename R, typename VV>
 static cudaError_t apply_dispatch(const Layout& h, int64_t nunits, VV zs, const VV* x, VV* y, cudaStream_t st) {
     switch (h.kind) {
         case LayoutKind::kBsr4:
-            return apply_one<R, VV>(ApplyBSR4<R>{h.unit_off, h.bcol, pick<R>(h, h.bval64, h.bval32), h.n, h.nslots, nullptr}, nunits, zs, x, y, st);
+            if constexpr (std::is_same<VV, float2>::value)   // complex64: column lanes
+                return apply_one<R, VV>(make_bsr<float>(h, nullptr), nunits, zs, x, y, st);
+            else
+                return apply_one<R, VV>(ApplyBSR4<R>{h.unit_off, h.bcol, pick<R>(h, h.bval64, h.bval32), h.n, h.nslots, nullptr}, nunits, zs, x, y, st);
         case LayoutKind::kCsr1:
             return apply_one<R, VV>(ApplyCSR<R, 1>{h.rowptr, h.col, pick<R>(h, h.val64, h.val32), h.n, h.nnz, nullptr}, nunits, zs, x, y, st);
         case LayoutKind::kCsr4:

@@ -54,6 +54,11 @@ struct SolveStats {          // device, written by CTA 0
 };
 
 // ---------------------------------------------------------------- applies
+// How the persistent kernel's phase A hands units to warps: a contiguous
+// range per CTA; unit cta + G * (warp + W * j) (all CTAs interleaved); or
+// blocks of W consecutive units per CTA, the grid sweeping the units together.
+enum : int { kMapContiguous = 0, kMapStrided = 1, kMapSweep = 2 };
+
 // Every apply maps (unit, lane) to at most one row and returns, on the lane
 // that owns the row, w = z_s x_row - (H x)_row.  The vector type VV sets the
 // arithmetic precision (float2: FP32, double2: FP64 with FP32 values promoted).
@@ -97,7 +102,7 @@ __device__ __forceinline__ void lane_add(float4& acc, int o) {   // compensated:
 template <typename R, int LPR>
 struct ApplyCSR {
     static constexpr int kRowsPerUnit = 32 / LPR;
-    static constexpr bool kStrided = false;
+    static constexpr int kMap = kMapContiguous;
     const int* rowptr;
     const int* col;
     const R* val;
@@ -136,7 +141,7 @@ struct ApplyCSR {
 template <typename R>
 struct ApplyBSR4 {
     static constexpr int kRowsPerUnit = 32;
-    static constexpr bool kStrided = false;
+    static constexpr int kMap = kMapContiguous;   // measured fastest for these lanes
     const int* unit_off;     // [nunits + 1] first slot of each unit
     const int* bcol;         // [slots][8]
     const R* bval;           // [slots][8][4][4]
@@ -197,6 +202,89 @@ struct ApplyBSR4 {
         return false;
     }
 };
+
+// Exchange of complex accumulators between lanes.
+__device__ __forceinline__ float2 shfl_xor_v(float2 v, int o) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+__device__ __forceinline__ double2 shfl_xor_v(double2 v, int o) {
+    return make_double2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+
+// The same 4x4-blocked sliced ELL with each 4x4 block stored column-major,
+// applied by column lanes (complex64 vectors): lane = 4 * block row + cc takes
+// column cc of each block and the single entry x[4 cb + cc], and accumulates
+// its contribution to all four rows of the block row.  The unit's column-block
+// indices are read first, then four slots of H and x at a time; a
+// reduce-scatter over the block row's four lanes leaves row 4 * block row + cc
+// in lane 4 * block row + cc.  Each x entry is read by one lane per slot
+// (instead of four), which shortens the gather; with compensated vectors the
+// four accumulators cost more than the gather saves, so those keep the row
+// lanes above.
+template <typename R>
+struct ApplyBSR4C {
+    static constexpr int kRowsPerUnit = 32;
+    static constexpr int kMap = kMapSweep;        // measured fastest for these lanes
+    static constexpr int kMaxSlots = 8;      // longer units take the loop below in chunks of 8
+    const int* unit_off;
+    const int* bcol;
+    const float* bvalc;      // [slots][8][4 columns][4 rows]
+    int64_t n;
+    int64_t nslots;
+    unsigned long long* dbg;
+
+    template <typename VV>   // float2, or double2 for the FP64 residual replacement
+    __device__ __forceinline__ bool operator()(int64_t unit, int lane, VV zs, const VV* x,
+                                               int64_t& row, VV& w) const {
+        const int br = lane >> 2, cc = lane & 3;
+        row = unit * 32 + lane;
+        int s0 = unit_off[unit], s1 = unit_off[unit + 1];
+        if (!chk(dbg, 4, s1, nslots + 1) || !chk(dbg, 4, s0, s1 + 1)) s0 = s1 = 0;
+        VV acc[4] = {vzero<VV>(), vzero<VV>(), vzero<VV>(), vzero<VV>()};
+        for (int c0 = s0; c0 < s1; c0 += kMaxSlots) {
+            const int ns = min(s1 - c0, kMaxSlots);
+            int cb[kMaxSlots];
+#pragma unroll
+            for (int j = 0; j < kMaxSlots; ++j) cb[j] = j < ns ? ld_stream(bcol + (size_t)(c0 + j) * 8 + br) : -1;
+#pragma unroll
+            for (int j0 = 0; j0 < kMaxSlots; j0 += 4) {
+                if (j0 >= ns) break;
+                float4 v[4];
+                VV xv[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    v[j] = j0 + j < ns ? ld_stream(reinterpret_cast<const float4*>(bvalc + ((size_t)(c0 + j0 + j) * 8 + br) * 16 + cc * 4))
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const int c = cb[j0 + j];
+                    xv[j] = (c >= 0 && chk(dbg, 5, (long long)c * 4 + 3, n)) ? x[(size_t)c * 4 + cc] : vzero<VV>();
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    cfma_r(acc[0], v[j].x, xv[j]); cfma_r(acc[1], v[j].y, xv[j]);
+                    cfma_r(acc[2], v[j].z, xv[j]); cfma_r(acc[3], v[j].w, xv[j]);
+                }
+            }
+        }
+        // reduce-scatter over the four lanes of the block row (xor 2, then xor 1)
+        const bool b1 = (cc >> 1) & 1, b0 = cc & 1;
+        VV k0 = b1 ? acc[2] : acc[0], k1 = b1 ? acc[3] : acc[1];
+        const VV t0 = shfl_xor_v(b1 ? acc[0] : acc[2], 2), t1 = shfl_xor_v(b1 ? acc[1] : acc[3], 2);
+        k0.x += t0.x; k0.y += t0.y; k1.x += t1.x; k1.y += t1.y;
+        const VV t = shfl_xor_v(b0 ? k0 : k1, 1);
+        VV mine = b0 ? k1 : k0;
+        mine.x += t.x; mine.y += t.y;
+        if (row < n) {
+            w = vsub(vcfma(zs, x[row], vzero<VV>()), mine);
+            return true;
+        }
+        return false;
+    }
+};
+
+// The blocked apply of each vector precision: column lanes for complex64,
+// row lanes otherwise.
+template <typename R> struct BsrApply { using T = ApplyBSR4<typename ValT<R>::T>; };
+template <> struct BsrApply<float> { using T = ApplyBSR4C<float>; };
 
 // ---------------------------------------------------------------- arguments
 template <typename R>

@@ -180,13 +180,14 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    // phase A visits units: a contiguous range per CTA, or (strided applies) the
-    // units cta + G * (warp + kWarps * j) so that all CTAs sweep the unit space
-    // together; the row-wise phases use a contiguous row range per CTA.
+    // phase A visits units in the apply's order (kMap); the row-wise phases
+    // use a contiguous row range per CTA.
     const int64_t ubeg = (int64_t)cta * a.nunits / G, uend = (int64_t)(cta + 1) * a.nunits / G;
-    const int64_t u_first = Apply::kStrided ? (int64_t)cta + (int64_t)G * warp : ubeg + warp;
-    const int64_t u_step = Apply::kStrided ? (int64_t)G * kWarps : kWarps;
-    const int64_t u_end = Apply::kStrided ? a.nunits : uend;
+    constexpr bool kWhole = Apply::kMap != kMapContiguous;   // every CTA visits the whole unit range
+    const int64_t u_first = Apply::kMap == kMapStrided ? (int64_t)cta + (int64_t)G * warp
+                          : Apply::kMap == kMapSweep ? (int64_t)cta * kWarps + warp : ubeg + warp;
+    const int64_t u_step = kWhole ? (int64_t)G * kWarps : kWarps;
+    const int64_t u_end = kWhole ? a.nunits : uend;
     const int64_t rbeg = (int64_t)cta * a.n / G, rend = (int64_t)(cta + 1) * a.n / G;
     const int M = a.nproj;
     const bool dense_proj = a.cvec != nullptr;
@@ -286,8 +287,9 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
             }
             const int nw = c_here ? kWarps - 1 : kWarps;    // warps that apply H
             const int wi = c_here ? warp - 1 : warp;
-            const int64_t a_first = Apply::kStrided ? (int64_t)cta + (int64_t)G * wi : ubeg + wi;
-            const int64_t a_step = Apply::kStrided ? (int64_t)G * nw : nw;
+            const int64_t a_first = Apply::kMap == kMapStrided ? (int64_t)cta + (int64_t)G * wi
+                                  : Apply::kMap == kMapSweep ? (int64_t)cta * nw + wi : ubeg + wi;
+            const int64_t a_step = kWhole ? (int64_t)G * nw : nw;
             for (int64_t u = a_first; wi >= 0 && u < u_end; u += a_step) {
                 int64_t row;
                 V w;

@@ -25,7 +25,8 @@ struct Layout {
     const int* unit_off;
     const int* bcol;
     const double* bval64;
-    const float* bval32;
+    const float* bval32;     // blocks row-major
+    const float* bval32c;    // the same blocks column-major (complex64 applies)
 };
 
 int rows_per_unit(LayoutKind k);
