@@ -17,7 +17,7 @@ iteration count; it does not converge at this eta) are reported beside it.
 N > 1 GPUs run independent replicas (the path has no exchange step): value =
 all ranks' shift-iterations / max time.
 
-Two batched legs are timed once beside the headline (``--legs``):
+Other workloads are timed once beside the headline (``--legs``):
   batch  32^3 x 4 Anderson (131,072 rows), 256 unit right-hand sides e_j with
          projection e_j (G_jj at 256 seeded sites) x 256 shifts over the
          spectrum + 1e-2 i, tol 1e-6, in ONE persistent block launch whose
@@ -27,7 +27,11 @@ Two batched legs are timed once beside the headline (``--legs``):
   multi  32 independent Anderson clusters of seeded uneven edge 14..50
          (13,500 to 500,000 rows, 5,118,460 in all), 128 shifts each over
          [-6.5, 6.5] + 1e-2 i, b seeded unit complex, c = conj(b), tol 1e-6,
-         in one cooperative launch replayed from a CUDA graph.
+         in one cooperative launch replayed from a CUDA graph;
+  chain  open chain of 4,096 sites, b = e_0, 64 shifts + 0.01i, FP64 to 1e-10;
+  adjoint  dL/dH of sum_k w_k Im G_00(z_k) on the 24^3 x 4 matrix, 128 shifts;
+  hubbard  matrix-free extended Hubbard ring, 14 sites, 7 up 7 down, 128
+         shifts + 0.05i, FP64 and complex64.
 
 --impl reference times the CPU oracle (plain FP64 C) on a bounded sample of
 the same workload.
@@ -307,6 +311,79 @@ def leg_multi(scocg, dev, stream):
                          "128 shifts each, eta 1e-2, tol 1e-6, one cooperative launch replayed from a CUDA graph")}
 
 
+def leg_chain(scocg, dev, stream):
+    """Open chain, 4,096 sites, 64 shifts + 0.01i, b = e_0, FP64 to 1e-10 (latency bound)."""
+    import torch
+    from paper_0802_0748_gb300 import inputs
+    wl = inputs.workload("chain", "full")
+    h = wl.csr
+    b = torch.from_numpy(wl.rhs[0]).to(dev)
+    hh = scocg.scocg_create_csr(h.rowptr, h.col, h.val)
+    scocg.scocg_solve(hh, wl.shifts, b, proj_idx=[0], tol=wl.tol)
+    (G, info), ms = timed(stream, lambda: scocg.scocg_solve(hh, wl.shifts, b, proj_idx=[0], tol=wl.tol))
+    scocg.scocg_destroy(hh)
+    return {"value": info["shift_iters"] / (ms * 1e-3), "unit": UNIT, "ms": ms, "status": info["status"],
+            "iters": info["iters"], "us_per_iter": info["seconds"] / info["iters"] * 1e6, "precision": "fp64",
+            "workload": "open chain L=4096, t=-1, b=e_0, 64 shifts linspace(-2.5,2.5)+0.01i, tol 1e-10"}
+
+
+def leg_adjoint(scocg, dev, stream):
+    """dL/dH for L = sum_k w_k Im G_00(z_k) on the 24^3 x 4 Anderson matrix (forward
+    solve, adjoint solves with full vectors, sampled products over the CSR pattern)."""
+    import numpy as np
+    import torch
+    from paper_0802_0748_gb300 import inputs
+    wl = inputs.workload("adjoint", "full", bounds=(-6.0, 6.4))
+    h = wl.csr
+    b = torch.from_numpy(wl.rhs[0]).to(dev)
+    gbar = torch.from_numpy((1j * wl.weights).astype(np.complex128)[None, :]).to(dev)
+    hh = scocg.scocg_create_csr(h.rowptr, h.col, h.val)
+    scocg.scocg_grad(hh, wl.shifts, b, gbar, proj_idx=[0], tol=wl.tol)
+    (g, info), ms = timed(stream, lambda: scocg.scocg_grad(hh, wl.shifts, b, gbar, proj_idx=[0], tol=wl.tol))
+    (G, i2), ms_f = timed(stream, lambda: scocg.scocg_solve(hh, wl.shifts, b, proj_idx=[0], tol=wl.tol))
+    scocg.scocg_destroy(hh)
+    return {"ms_per_gradient": ms, "ms_forward_solve": ms_f, "gradient_over_forward": ms / ms_f,
+            "status": info["status"], "nnz": h.nnz, "finite": bool(torch.isfinite(g).all().item()),
+            "workload": "anderson-24^3x4 (55,296 rows, 1,548,288 nnz), b=c=e_0, 128 shifts eta 0.02, tol 1e-10, "
+                        "dL/dval for all stored values (FP64)"}
+
+
+def leg_hubbard(scocg, dev, stream, hbm):
+    """Matrix-free extended Hubbard ring, 14 sites, 7 up 7 down (11,778,624 states),
+    128 shifts + 0.05i, b seeded unit complex, c = conj(b), tol 1e-6: FP64,
+    compensated FP32, and complex64 (capped at the FP64 iteration count)."""
+    import torch
+    from paper_0802_0748_gb300 import inputs
+    wl = inputs.workload("hubbard", "full")
+    p = wl.hubbard
+    b = torch.from_numpy(wl.rhs[0]).to(dev)
+    c = torch.from_numpy(wl.proj_vec).to(dev)
+    out = {"workload": "Hubbard ring L=14, 7 up 7 down (11,778,624 states), t=1 U=4 V=1 periodic, "
+                       "128 shifts linspace(-10,20)+0.05i, tol 1e-6"}
+    cap = 0
+    for name, prec in (("fp64", 0), ("df", 2), ("mixed", 1)):
+        hh = scocg.scocg_create_hubbard(p["L"], p["n_up"], p["n_dn"], p["t"], p["U"], p["V"], p["periodic"],
+                                        opts=scocg.SolveOptions(precision=prec, max_iter=cap if prec == 1 else 0))
+        (G, info), ms = timed(stream, lambda: scocg.scocg_solve(hh, wl.shifts, b, proj_vec=c, tol=wl.tol))
+        scocg.scocg_destroy(hh)
+        gbs = info["bytes_per_iter"] * info["iters"] / info["seconds"] / 1e9
+        out[name] = {"value": info["shift_iters"] / (ms * 1e-3), "unit": UNIT, "ms": ms, "status": info["status"],
+                     "iters": info["iters"], "us_per_iter": info["seconds"] / info["iters"] * 1e6,
+                     "hbm_GBs_algorithmic": gbs, "hbm_frac": gbs / hbm}
+        if name == "fp64":
+            cap = info["iters"]
+            g64 = G.cpu()
+            continue
+        rel = (G.cpu() - g64).abs() / g64.abs()
+        out[name]["max_rel_G_diff_vs_fp64"] = float(rel.max())
+        out[name]["median_rel_G_diff_vs_fp64"] = float(rel.median())
+        if name == "mixed":
+            out[name]["max_iter_cap"] = cap
+        else:
+            out[name]["speedup_vs_fp64"] = out[name]["value"] / out["fp64"]["value"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -317,7 +394,8 @@ def main():
     ap.add_argument("--compare", default="fp64,mixed", help="comma list of other precisions timed once beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--max-iter", type=int, default=0, help="cap on seed iterations (0 = to convergence)")
-    ap.add_argument("--legs", default="batch,multi", help="comma list of batched legs timed once beside it")
+    ap.add_argument("--legs", default="batch,multi,chain,adjoint,hubbard",
+                    help="comma list of the other workloads, each timed once beside the headline")
     args = ap.parse_args()
 
     from paper_0802_0748_gb300 import inputs
@@ -450,6 +528,12 @@ def main():
         legs["batch"] = leg_batch(scocg, dev, stream, hbm)
     if "multi" in leg_names:
         legs["multi"] = leg_multi(scocg, dev, stream)
+    if "chain" in leg_names:
+        legs["chain"] = leg_chain(scocg, dev, stream)
+    if "adjoint" in leg_names:
+        legs["adjoint"] = leg_adjoint(scocg, dev, stream)
+    if "hubbard" in leg_names:
+        legs["hubbard"] = leg_hubbard(scocg, dev, stream, hbm)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -67,7 +67,8 @@ typedef enum {
                            numbers (hi + lo, about 44 significant bits), FP32 H
                            values, every vector operation in FP32 arithmetic with
                            error-free transformations (TwoSum, FMA TwoProd); FP64
-                           seed scalars and shift recurrences.  CSR handles only. */
+                           seed scalars and shift recurrences.  For Hubbard
+                           handles t, U and V enter as float pairs.             */
 } scocg_precision;
 
 /* Options, fixed at create time (scocg_set_opts changes them later).

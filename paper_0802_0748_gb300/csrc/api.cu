@@ -273,8 +273,7 @@ extern "C" int scocg_apply(scocg_handle h, scocg_c128 z, const void* x, void* y,
         return SCOCG_ERR_INVALID;
     cudaError_t e;
     if (h->kind == HandleKind::kHubbard) {
-        if (precision == SCOCG_MIXED_DF) return SCOCG_ERR_INVALID;
-        e = hubbard_apply(h->hub, precision == SCOCG_MIXED, c2(z.re, z.im), x, y, h->stream);
+        e = hubbard_apply(h->hub, precision, c2(z.re, z.im), x, y, h->stream);
     } else {
         e = launch_apply(h->layout(false), precision, c2(z.re, z.im), x, y, h->stream);
     }
@@ -425,7 +424,6 @@ int scocg::solve_impl(scocg_ctx* h, const scocg_c128* shifts, int nshift, const 
     const size_t dyn_smem = Xf ? (size_t)nshift * kFullSmem : 0;
     const bool mixed = prec == SCOCG_MIXED;
     const bool dfm = prec == SCOCG_MIXED_DF;
-    if (dfm && h->kind == HandleKind::kHubbard) return SCOCG_ERR_INVALID;
     // several right-hand sides with unit projections: the block kernel
     if (!Xf && nrhs > 1 && proj_idx && h->kind == HandleKind::kCsr && nproj <= kMaxProjB &&
         !(mixed && h->opts.replace_every > 0) && h->opts.rhs_tile != 1) {
@@ -447,7 +445,7 @@ int scocg::solve_impl(scocg_ctx* h, const scocg_c128* shifts, int nshift, const 
     cudaStream_t s = h->stream;
 
     const Layout L = h->kind == HandleKind::kHubbard ? Layout{} : h->layout(false);
-    int maxco = h->kind == HandleKind::kHubbard ? hubbard_max_ctas(h->hub, mixed, h->num_sms, dyn_smem)
+    int maxco = h->kind == HandleKind::kHubbard ? hubbard_max_ctas(h->hub, prec, h->num_sms, dyn_smem)
                                                  : max_coresident_ctas(L, prec, h->num_sms, dyn_smem);
     if (maxco <= 0) return SCOCG_ERR_CUDA;
     const int rpu = h->kind == HandleKind::kHubbard ? 32 : rows_per_unit(L.kind);

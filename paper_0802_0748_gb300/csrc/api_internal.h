@@ -18,6 +18,7 @@ struct Ctrl {
     int pad;
     SolveStats stats;
     unsigned long long dbg[4];   // checked builds: (flag, site, index, limit)
+    unsigned long long rflag;    // last barrier epoch whose reduction has been published
 };
 
 // Sequential carving of a buffer into 256-byte aligned pieces; with a null
@@ -117,8 +118,8 @@ void fill_opts(scocg_opts& o, const scocg_opts* in);
 int default_seed(const scocg_c128* z, int K);
 
 // Hubbard (hubbard.cu)
-cudaError_t hubbard_apply(const Hubbard& hb, bool mixed, double2 z, const void* x, void* y, cudaStream_t st);
-int hubbard_max_ctas(const Hubbard& hb, bool mixed, int num_sms, size_t dyn_smem = 0);
+cudaError_t hubbard_apply(const Hubbard& hb, int prec, double2 z, const void* x, void* y, cudaStream_t st);
+int hubbard_max_ctas(const Hubbard& hb, int prec, int num_sms, size_t dyn_smem = 0);
 template <typename R>
 cudaError_t hubbard_launch_solve(const SolveArgs<R>& a, const Hubbard& hb, int grid, cudaStream_t st);
 

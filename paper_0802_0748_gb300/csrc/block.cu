@@ -62,6 +62,7 @@ int run_block(scocg_ctx* h, const scocg_c128* shifts, int K, const void* rhs, in
         a.partA = (double*)c.take(sizeof(double) * kNvA * T * grid);
         a.partB = (double*)c.take(sizeof(double) * kNvB * T * grid);
         a.partC = (double*)c.take(sizeof(double) * kNvC * T * grid);
+        a.res = (double*)c.take(sizeof(double) * (kNvA > kNvB ? kNvA : kNvB) * T);
     };
     Carver measure{nullptr, 0};
     carve(measure);
@@ -100,6 +101,7 @@ int run_block(scocg_ctx* h, const scocg_c128* shifts, int K, const void* rhs, in
     a.stats = &h->d_ctrl->stats;
     a.dbg = h->d_ctrl->dbg;
     a.phase_ns = nullptr;
+    a.rflag = &h->d_ctrl->rflag;
 #ifdef SCOCG_PHASE_TIMERS
     static unsigned long long* h_ns = nullptr;
     static int h_ns_n = 0;

@@ -73,6 +73,8 @@ struct BlockArgs {
     SolveStats* stats;
     unsigned long long* dbg;
     unsigned long long* phase_ns;   // phase-timer builds: [grid][8] accumulated ns
+    unsigned long long* rflag;      // published reduction epoch (grid_reduce)
+    double* res;                    // [max(kNvA, kNvB) * T] published sums
 };
 
 template <int T>
@@ -164,6 +166,63 @@ __device__ __forceinline__ void grid_sum_vm(const double* part, int G, int nval,
     __syncthreads();
 }
 
+// A grid barrier that also sums value-major partials part[v * G + cta]
+// (v < nval) into out[] (shared) in every CTA.  The CTA that arrives last
+// reads all partials once, writes the nval sums to res[] (global) and
+// publishes the barrier epoch in *flag; the other CTAs wait for the flag
+// (bounded, like grid_barrier) and read the nval sums.  The partials are thus
+// read by one CTA instead of all G, which matters when nval = 4T is large.
+// res[] can be reused by the next call: no CTA arrives there before it has
+// read the previous sums.
+__device__ __forceinline__ bool grid_reduce(const GridSync& g, unsigned long long& epoch,
+                                            unsigned long long* flag, const double* part, int G, int nval,
+                                            double* res, double* out) {
+    __shared__ int s_last, s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ++epoch;
+        __threadfence();                                  // release this CTA's partials
+        const unsigned long long old = atomicAdd(g.count, 1ull);
+        s_last = old + 1 == epoch * (unsigned long long)g.nctas;
+        __threadfence();                                  // acquire: the last arriver sees every partial
+        s_ok = 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        grid_sum_vm(part, G, nval, out);                  // ends with __syncthreads
+        for (int t = threadIdx.x; t < nval; t += kBlock) res[t] = out[t];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicMax(flag, epoch);                       // publish
+            if (ld_volatile_i32(g.status) < 0) s_ok = 0;
+        }
+        __syncthreads();
+        return s_ok != 0;
+    }
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const uint64_t t0 = globaltimer_ns();
+        while (ld_acquire_u64(flag) < epoch) {
+            if (ld_volatile_i32(g.status) < 0) { ok = 0; break; }
+            if (globaltimer_ns() - t0 > g.timeout_ns) {
+                atomicCAS(g.status, 0, (int)SCOCG_ERR_TIMEOUT);
+                atomicCAS(g.status, 1, (int)SCOCG_ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+        }
+        if (ok && ld_volatile_i32(g.status) < 0) ok = 0;
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) return false;
+    for (int t = threadIdx.x; t < nval; t += kBlock) out[t] = __ldcg(res + t);
+    __syncthreads();
+    return true;
+}
+
 // order-preserving bits of a non-negative double (for atomicMax)
 __device__ __forceinline__ unsigned long long key_bits(double v) {
     return (unsigned long long)__double_as_longlong(v);
@@ -246,9 +305,8 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_block(BlockArgs<R> a) {
                 }
             }
             SCOCG_MARK(0);
-            if (!grid_barrier(a.sync, epoch)) return;
+            if (!grid_reduce(a.sync, epoch, a.rflag, a.partA, G, kNvA * T, a.res, s.red)) return;
             SCOCG_MARK(1);
-            grid_sum_vm(a.partA, G, kNvA * T, s.red);
 
             // ---- decide: alpha per running slot, or finish it
             if (tid < T) {
@@ -332,9 +390,8 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_block(BlockArgs<R> a) {
             block_cols<T, 1, kNvB>(nb, s.scratch, a.partB, G, cta, 3);
         }
         SCOCG_MARK(2);
-        if (!grid_barrier(a.sync, epoch)) return;
+        if (!grid_reduce(a.sync, epoch, a.rflag, a.partB, G, kNvB * T, a.res, s.red)) return;
         SCOCG_MARK(3);
-        grid_sum_vm(a.partB, G, kNvB * T, s.red);
         if (tid < T) {
             const int c = tid;
             const double* rd = s.red + kNvB * c;

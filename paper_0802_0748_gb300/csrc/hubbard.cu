@@ -106,6 +106,48 @@ struct ApplyHubbard {
         return (x >> 1) | (ring ? ((x & 1u) << (L - 1)) : 0u);
     }
 
+    // Compensated vectors: the diagonal U n_up n_dn + V n_i n_j and the hop
+    // amplitude t are taken as float pairs (exact for values such as t = 1,
+    // U = 4, V = 1), products exact to the pair precision, sums with TwoSum.
+    __device__ __forceinline__ bool operator()(int64_t unit, int lane, float4 zs, const float4* x, int64_t& row,
+                                               float4& w) const {
+        const int u = (int)(unit % D_up);
+        const int d = (int)(unit / D_up) * 32 + lane;
+        if (d >= D_dn) return false;
+        row = (int64_t)u * D_dn + d;
+        const uint32_t su = st_up[u], sd = st_dn[d];
+        const uint32_t pu = partner(su), pd = partner(sd);
+        const int cu = __popc(su & sd);
+        const int cv = __popc(su & pu) + __popc(sd & pd) + __popc(su & pd) + __popc(sd & pu);
+        const float4 dg = df_from(c2(U * (double)cu + V * (double)cv, 0.0));
+        const dfs zr = df_add(cre(zs), df_neg(cre(dg)));
+        float4 acc = vcfma(cpack(zr, cim(zs)), x[row], vzero<float4>());   // (z_s - diag) x_row
+        dfs ar = cre(acc), ai = cim(acc);
+        const float4 tp = df_from(c2(t, 0.0));
+        const dfs tt = cre(tp), mt = df_neg(tt);
+        const float4* xrow = x + (size_t)u * D_dn;
+        for (int j = 0; j < S; ++j) {
+            const int e = hop_dn[(size_t)d * S + j];
+            if (e < 0) break;
+            if (!chk(dbg, 20, e >> 1, D_dn)) continue;
+            const float4 xv = xrow[e >> 1];
+            const dfs c = (e & 1) ? mt : tt;
+            df_acc_prod(ar, c, cre(xv));
+            df_acc_prod(ai, c, cim(xv));
+        }
+        for (int j = 0; j < S; ++j) {
+            const int e = hop_up[(size_t)u * S + j];
+            if (e < 0) break;
+            if (!chk(dbg, 21, e >> 1, D_up)) continue;
+            const float4 xv = x[(size_t)(e >> 1) * D_dn + d];
+            const dfs c = (e & 1) ? mt : tt;
+            df_acc_prod(ar, c, cre(xv));
+            df_acc_prod(ai, c, cim(xv));
+        }
+        w = cpack(df_norm(ar.hi, ar.lo), df_norm(ai.hi, ai.lo));
+        return true;
+    }
+
     template <typename VV>
     __device__ __forceinline__ bool operator()(int64_t unit, int lane, VV zs, const VV* x, int64_t& row,
                                                VV& w) const {
@@ -165,34 +207,34 @@ static ApplyHubbard<R> make_apply(const Hubbard& hb) {
     return ap;
 }
 
-int hubbard_max_ctas(const Hubbard& hb, bool mixed, int num_sms, size_t dyn_smem) {
+int hubbard_max_ctas(const Hubbard& hb, int prec, int num_sms, size_t dyn_smem) {
     int nb = 0;
-    cudaError_t e = mixed
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cocg_persistent<float, ApplyHubbard<float>>, kBlock,
-                                                        dyn_smem)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cocg_persistent<double, ApplyHubbard<double>>, kBlock,
-                                                        dyn_smem);
+    cudaError_t e =
+        prec == SCOCG_MIXED
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cocg_persistent<float, ApplyHubbard<float>>, kBlock,
+                                                            dyn_smem)
+        : prec == SCOCG_MIXED_DF
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cocg_persistent<DF, ApplyHubbard<float>>, kBlock,
+                                                            dyn_smem)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cocg_persistent<double, ApplyHubbard<double>>,
+                                                            kBlock, dyn_smem);
     (void)hb;
     return e == cudaSuccess ? nb * num_sms : 0;
 }
 
 template <typename R>
 cudaError_t hubbard_launch_solve(const SolveArgs<R>& a, const Hubbard& hb, int grid, cudaStream_t st) {
-    ApplyHubbard<R> ap = make_apply<R>(hb);
+    using W = typename ValT<R>::T;
+    ApplyHubbard<W> ap = make_apply<W>(hb);
     ap.dbg = a.dbg;
     void* args[] = {(void*)&a, (void*)&ap};
     const size_t smem = a.Xf ? (size_t)a.K * kFullSmem : 0;
-    return cudaLaunchCooperativeKernel((const void*)cocg_persistent<R, ApplyHubbard<R>>, dim3(grid), dim3(kBlock),
+    return cudaLaunchCooperativeKernel((const void*)cocg_persistent<R, ApplyHubbard<W>>, dim3(grid), dim3(kBlock),
                                        args, smem, st);
 }
 template cudaError_t hubbard_launch_solve<double>(const SolveArgs<double>&, const Hubbard&, int, cudaStream_t);
 template cudaError_t hubbard_launch_solve<float>(const SolveArgs<float>&, const Hubbard&, int, cudaStream_t);
-// the compensated FP32 mode is not built for the Hubbard apply (the C ABI
-// rejects it before launching)
-template <>
-cudaError_t hubbard_launch_solve<DF>(const SolveArgs<DF>&, const Hubbard&, int, cudaStream_t) {
-    return cudaErrorNotSupported;
-}
+template cudaError_t hubbard_launch_solve<DF>(const SolveArgs<DF>&, const Hubbard&, int, cudaStream_t);
 
 template <typename VV, class Apply>
 __global__ void __launch_bounds__(256) k_hub_apply(Apply ap, int64_t nunits, VV zs, const VV* x, VV* y) {
@@ -203,11 +245,14 @@ __global__ void __launch_bounds__(256) k_hub_apply(Apply ap, int64_t nunits, VV 
     if (ap(u, threadIdx.x & 31, zs, x, row, w)) y[row] = w;
 }
 
-cudaError_t hubbard_apply(const Hubbard& hb, bool mixed, double2 z, const void* x, void* y, cudaStream_t st) {
+cudaError_t hubbard_apply(const Hubbard& hb, int prec, double2 z, const void* x, void* y, cudaStream_t st) {
     const unsigned blocks = (unsigned)((hb.nunits * 32 + 255) / 256);
-    if (mixed)
+    if (prec == SCOCG_MIXED)
         k_hub_apply<float2><<<blocks, 256, 0, st>>>(make_apply<float>(hb), hb.nunits,
                                                     make_float2((float)z.x, (float)z.y), (const float2*)x, (float2*)y);
+    else if (prec == SCOCG_MIXED_DF)
+        k_hub_apply<float4><<<blocks, 256, 0, st>>>(make_apply<float>(hb), hb.nunits, df_from(z), (const float4*)x,
+                                                    (float4*)y);
     else
         k_hub_apply<double2><<<blocks, 256, 0, st>>>(make_apply<double>(hb), hb.nunits, z, (const double2*)x,
                                                      (double2*)y);

@@ -102,3 +102,46 @@ def test_solve_matches_oracle(S, oracle_mod):
     assert info2["status"] == 0
     assert np.max(np.abs(G2.cpu().numpy()[0] - ref2.G) / np.abs(ref2.G)) < 1e-9
     S.scocg_destroy(h)
+
+
+def to_df(x):
+    """complex128 -> float32 pairs {re.hi, im.hi, re.lo, im.lo} (value = hi + lo)."""
+    hi = x.astype(np.complex64)
+    lo = (x - hi.astype(np.complex128)).astype(np.complex64)
+    return np.stack([hi.real, hi.imag, lo.real, lo.imag], axis=-1).astype(np.float32)
+
+
+def from_df(v):
+    v = v.astype(np.float64)
+    return (v[..., 0] + v[..., 2]) + 1j * (v[..., 1] + v[..., 3])
+
+
+@pytest.mark.parametrize("t,U,V", [(1.0, 4.0, 1.0), (0.3, 4.1, 0.7)])
+def test_apply_df_matches_oracle(S, oracle_mod, t, U, V):
+    """Compensated FP32 apply: the amplitudes are split into float pairs (exact
+    for t=1, U=4, V=1; a rounding of ~2^-48 relative otherwise), products exact
+    to the pair precision, TwoSum accumulation: within 1e-12 of the FP64 apply."""
+    rp, c, v = oracle_mod.hubbard_csr(8, 4, 3, t, U, V, True)
+    n = rp.size - 1
+    x = inputs.random_unit_complex(n, 17)
+    z = 2.0 + 0.5j
+    ref = oracle_mod.apply_shifted(rp, c, v, z, x)
+    h = S.scocg_create_hubbard(8, 4, 3, t, U, V, True)
+    y = from_df(S.scocg_apply(h, z, cuda(to_df(x)), precision=S.MIXED_DF).cpu().numpy())
+    S.scocg_destroy(h)
+    assert np.max(np.abs(y - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_solve_df_matches_oracle(S, oracle_mod):
+    """8-site ring, 4 up 3 down: the compensated FP32 solve converged to 1e-12
+    gives the oracle's G within 1e-8 (the FP64 bound is 1e-9 at this tol)."""
+    rp, c, v = oracle_mod.hubbard_csr(8, 4, 3, 1.0, 4.0, 1.0, True)
+    n = rp.size - 1
+    b = inputs.random_unit_complex(n, 5)
+    shifts = np.linspace(-10, 20, 24) + 0.05j
+    h = S.scocg_create_hubbard(8, 4, 3, 1.0, 4.0, 1.0, True, opts=S.SolveOptions(precision=S.MIXED_DF))
+    G, info = S.scocg_solve(h, shifts, cuda(b), proj_vec=cuda(np.conj(b)[None, :]), tol=1e-12)
+    S.scocg_destroy(h)
+    ref = oracle_mod.shifted_cocg(rp, c, v, shifts, b, proj_vec=[np.conj(b)], tol=1e-12)
+    assert info["status"] == 0
+    assert np.max(np.abs(G.cpu().numpy()[0] - ref.G) / np.abs(ref.G)) < 1e-8
