@@ -143,24 +143,25 @@ def dist_env():
     return ws, rank, local
 
 
-def max_over_ranks(x: float, ws: int) -> float:
+def _reduce_over_ranks(x: float, ws: int, op: str) -> float:
+    """All-reduce of one float over the ranks (on the GPU under NCCL, on the
+    host under gloo)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    return _reduce_over_ranks(x, ws, "max")
 
 
 def sum_over_ranks(x: float, ws: int) -> float:
-    if ws == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce_over_ranks(x, ws, "sum")
 
 
 def barrier(ws: int):
