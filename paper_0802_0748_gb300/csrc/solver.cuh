@@ -141,7 +141,7 @@ struct ApplyCSR {
 template <typename R>
 struct ApplyBSR4 {
     static constexpr int kRowsPerUnit = 32;
-    static constexpr int kMap = kMapContiguous;   // measured fastest for these lanes
+    static constexpr int kMap = kMapContiguous;
     const int* unit_off;     // [nunits + 1] first slot of each unit
     const int* bcol;         // [slots][8]
     const R* bval;           // [slots][8][4][4]
@@ -224,7 +224,7 @@ __device__ __forceinline__ double2 shfl_xor_v(double2 v, int o) {
 template <typename R>
 struct ApplyBSR4C {
     static constexpr int kRowsPerUnit = 32;
-    static constexpr int kMap = kMapSweep;        // measured fastest for these lanes
+    static constexpr int kMap = kMapContiguous;
     static constexpr int kMaxSlots = 8;      // longer units take the loop below in chunks of 8
     const int* unit_off;
     const int* bcol;

@@ -204,6 +204,7 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
     bool defer_ok = a.K <= 32 * G;
     if constexpr (kFull) defer_ok = defer_ok && a.Xf == nullptr;
     bool pending = false;                     // a deferred phase C waits for the next phase A
+
     int status = SCOCG_NOT_CONVERGED;
     bool done = false;
 #ifdef SCOCG_PHASE_TIMERS
@@ -285,12 +286,13 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
                 bad = __any_sync(0xffffffffu, bad);
                 if (lane == 0) { s_flag[0] = act; s_flag[1] = bad; }
             }
-            const int nw = c_here ? kWarps - 1 : kWarps;    // warps that apply H
-            const int wi = c_here ? warp - 1 : warp;
+            // all warps apply H; with a deferred phase C the unit order is
+            // rotated so that warp 0 takes the last place in each round and,
+            // when the rounds do not come out even, one unit fewer
+            const int wi = c_here ? (warp + kWarps - 1) % kWarps : warp;
             const int64_t a_first = Apply::kMap == kMapStrided ? (int64_t)cta + (int64_t)G * wi
-                                  : Apply::kMap == kMapSweep ? (int64_t)cta * nw + wi : ubeg + wi;
-            const int64_t a_step = kWhole ? (int64_t)G * nw : nw;
-            for (int64_t u = a_first; wi >= 0 && u < u_end; u += a_step) {
+                                  : Apply::kMap == kMapSweep ? (int64_t)cta * kWarps + wi : ubeg + wi;
+            for (int64_t u = a_first; u < u_end; u += u_step) {
                 int64_t row;
                 V w;
                 if (ap(u, lane, zs, (const V*)a.r, row, w)) {
@@ -299,8 +301,8 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
                     acc_bil(rq[0], rq[1], a.r[row], qn);
                 }
             }
-            pending = false;
             block_sum_n<2>(rq, s.scratch, s_part);
+            pending = false;
             if (tid == 0) {
                 double* pa = a.partA + cta;            // value-major
                 pa[0] = s_part[0]; pa[G] = s_part[1];

