@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_block(BlockArgs<R> a) {
                 const size_t o = (size_t)i * T + cl;
                 V rn;
                 if (st == kSlotRun) {
-                    rn = vsub(a.r[o], vcfma(al, a.q[o], vzero<V>()));
+                    rn = r_update(a.r[o], al, a.q[o]);
                 } else {
                     const double2 bi = bj[i];
                     rn = Vec<R>::make(bi);
@@ -383,8 +383,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_block(BlockArgs<R> a) {
                     nb[0] = fma(bi.x, bi.x, fma(bi.y, bi.y, nb[0]));
                 }
                 a.r[o] = rn;
-                acc_bil(acc[0], acc[1], rn, rn);
-                acc_nrm(acc[2], rn);
+                acc_rr(acc[0], acc[1], acc[2], rn);
             }
             block_cols<T, 3, kNvB>(acc, s.scratch, a.partB, G, cta);
             block_cols<T, 1, kNvB>(nb, s.scratch, a.partB, G, cta, 3);

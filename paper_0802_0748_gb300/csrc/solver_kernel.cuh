@@ -47,13 +47,39 @@ __device__ __forceinline__ void acc_nrm(dfs& s, float4 u) {
     df_acc_prod(s, cim(u), cim(u));
 }
 
+// Per-thread accumulation of rho = r^T r (re, im) and ||r||^2.
+template <typename AT, typename V>
+__device__ __forceinline__ void acc_rr(AT& re, AT& im, AT& nrm, V ri) {
+    acc_bil(re, im, ri, ri);
+    acc_nrm(nrm, ri);
+}
+// Compensated vectors: rho = sum (x^2 - y^2) + 2i sum x y from three
+// pair-exact products (the doubling is exact), and ||r||^2 from the high
+// parts in FP32: it only feeds the convergence test, where a relative
+// accuracy of 1e-7 is ample.
+template <>
+__device__ __forceinline__ void acc_rr<dfs, float4>(dfs& re, dfs& im, dfs& nrm, float4 ri) {
+    const dfs x = cre(ri), y = cim(ri);
+    df_acc_prod(re, x, x);
+    df_acc_prod(re, df_neg(y), y);
+    df_acc_prod(im, dfs{2.f * x.hi, 2.f * x.lo}, y);
+    nrm.hi = fmaf(ri.x, ri.x, fmaf(ri.y, ri.y, nrm.hi));
+}
+
 // Per-thread accumulation of the r partials: rho = r^T r, ||r||^2, c_0^T r.
 template <typename R>
 __device__ __forceinline__ void acc_r(typename Acc<R>::T (&acc)[5], typename Vec<R>::T ri,
                                      const typename Vec<R>::T* c0) {
-    acc_bil(acc[0], acc[1], ri, ri);
-    acc_nrm(acc[2], ri);
+    acc_rr(acc[0], acc[1], acc[2], ri);
     if (c0) acc_bil(acc[3], acc[4], *c0, ri);
+}
+
+// r_{n+1} = r_n - alpha_n q_n (one fused multiply-add for compensated vectors)
+template <typename V>
+__device__ __forceinline__ V r_update(V r, V al, V q) { return vsub(r, vcfma(al, q, vzero<V>())); }
+template <>
+__device__ __forceinline__ float4 r_update<float4>(float4 r, float4 al, float4 q) {
+    return vcfma(make_float4(-al.x, -al.y, -al.z, -al.w), q, r);
 }
 
 // CTA sum of the accumulated partials into values 0..4 of this CTA's column
@@ -371,8 +397,26 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
             const V al = Vec<R>::make(s.alpha);
             const V bp = Vec<R>::make(s.beta_prev);
             const bool track_x = kMixed && s.replace_on;
+            bool plain = !track_x;
+            if constexpr (kFull) plain = plain && a.Xf == nullptr;
             AT acc[5] = {};
-            for (int64_t i = rbeg + tid; i < rend; i += kBlock) {
+            if (plain) {
+                // one row ahead: the next row's loads are in flight while this
+                // row is updated and stored (same rows, same order per thread)
+                int64_t i = rbeg + tid;
+                V ro = vzero<V>(), qo = vzero<V>(), co = vzero<V>();
+                if (i < rend) { ro = a.r[i]; qo = a.q[i]; if (a.cvec) co = a.cvec[i]; }
+                for (; i < rend; i += kBlock) {
+                    const int64_t inx = i + kBlock;
+                    V r1 = vzero<V>(), q1 = vzero<V>(), c1 = vzero<V>();
+                    if (inx < rend) { r1 = a.r[inx]; q1 = a.q[inx]; if (a.cvec) c1 = a.cvec[inx]; }
+                    const V rn = r_update(ro, al, qo);
+                    a.r[i] = rn;
+                    acc_r<R>(acc, rn, a.cvec ? &co : nullptr);
+                    ro = r1; qo = q1; co = c1;
+                }
+            }
+            for (int64_t i = rbeg + tid; !plain && i < rend; i += kBlock) {
                 const V ro = a.r[i];
                 if constexpr (kFull) {
                     if (a.Xf) {
@@ -404,7 +448,7 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
                         a.x_lo[i] = lo;
                     }
                 }
-                const V rn = vsub(ro, vcfma(al, a.q[i], vzero<V>()));
+                const V rn = r_update(ro, al, a.q[i]);
                 a.r[i] = rn;
                 acc_r<R>(acc, rn, a.cvec ? a.cvec + i : nullptr);
             }
