@@ -124,12 +124,12 @@ __device__ __forceinline__ void block_cols(AT (&acc)[NV], double* scratch, doubl
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
         const AT t = col_sum<T>(acc[j]);
-        if (lane < T) scratch[(warp * T + lane) * NV + j] = to_double(t);
+        if (lane < T) park(scratch + (warp * T + lane) * NV + j, t);
     }
     __syncthreads();
     for (int t = threadIdx.x; t < T * NV; t += kBlock) {
         double sum = 0.0;
-        for (int w = 0; w < kWarps; ++w) sum += scratch[w * T * NV + t];
+        for (int w = 0; w < kWarps; ++w) sum += unpark<AT>(scratch + w * T * NV + t);
         const int c = t / NV, j = t - c * NV;
         part[(size_t)(c * NVS + j_off + j) * G + cta] = sum;
     }
@@ -236,6 +236,9 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_block(BlockArgs<R> a) {
     constexpr int RPW = 32 / T;              // rows a warp covers per step
     constexpr unsigned kFull = 0xffffffffu;
     __shared__ BlockShared<T> s;
+    // per slot: z_s, beta_{n-1}, alpha_n in the vector type, converted by the
+    // slot's thread when they change rather than by every thread per phase
+    __shared__ V s_vz[T], s_vb[T], s_va[T];
 
     const int G = (int)gridDim.x, cta = (int)blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -253,6 +256,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_block(BlockArgs<R> a) {
         s.n[tid] = 0; s.nsw[tid] = 0; s.siters[tid] = 0; s.pend[tid] = kGoOn;
         s.cnt[tid] = 0; s.bad[tid] = 0; s.sw[tid] = 0;
         s.alpha[tid] = c2(0, 0);
+        s_vz[tid] = vzero<V>(); s_vb[tid] = vzero<V>(); s_va[tid] = vzero<V>();
     }
     if (tid == 0) s.next_rhs = a.nrhs < T ? a.nrhs : T;
     __syncthreads();
@@ -269,8 +273,8 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_block(BlockArgs<R> a) {
             {
                 AT acc[2] = {};
                 const bool run = s.state[cl] == kSlotRun;
-                const V zs = Vec<R>::make(s.zs[cl]);
-                const V bp = Vec<R>::make(s.beta_prev[cl]);
+                const V zs = s_vz[cl];
+                const V bp = s_vb[cl];
                 for (int64_t i0 = rbeg + warp * RPW; i0 < rend; i0 += kWarps * RPW) {
                     const int64_t i = i0 + sub;
                     const bool has = i < rend;
@@ -324,7 +328,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_block(BlockArgs<R> a) {
                     else {
                         const double2 al = cdiv(s.rho[c], rq);
                         if (!cfinite(al)) fin = SCOCG_ERR_BREAKDOWN;
-                        else { s.alpha[c] = al; s.siters[c] += active; }
+                        else { s.alpha[c] = al; s_va[c] = Vec<R>::make(al); s.siters[c] += active; }
                     }
                 }
                 s.fin[c] = fin;
@@ -367,7 +371,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_block(BlockArgs<R> a) {
             AT acc[3] = {};
             double nb[1] = {0.0};
             const int st = s.state[cl];
-            const V al = Vec<R>::make(s.alpha[cl]);
+            const V al = s_va[cl];
             const double2* bj = st == kSlotFresh ? a.b + (size_t)s.rhs[cl] * a.n : nullptr;
             for (int64_t i0 = rbeg + warp * RPW; i0 < rend; i0 += kWarps * RPW) {
                 const int64_t i = i0 + sub;
@@ -406,6 +410,8 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_block(BlockArgs<R> a) {
                 s.beta_prev[c] = c2(0, 0);
                 s.seed[c] = a.seed0;
                 s.zs[c] = a.z[a.seed0];
+                s_vz[c] = Vec<R>::make(s.zs[c]);
+                s_vb[c] = vzero<V>();
                 s.n[c] = 0; s.nsw[c] = 0; s.pend[c] = kGoOn;
             }
             s.cnt[c] = 0; s.bad[c] = 0;
@@ -469,6 +475,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_block(BlockArgs<R> a) {
             s.sw[c] = 0;
             if (s.state[c] == kSlotRun) {
                 s.beta_prev[c] = cdiv(s.rho_new[c], s.rho[c]);
+                s_vb[c] = Vec<R>::make(s.beta_prev[c]);
                 s.alpha_prev[c] = s.alpha[c];
                 s.rho[c] = s.rho_new[c];
                 s.n[c] += 1;
@@ -588,6 +595,8 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_block(BlockArgs<R> a) {
                     s.alpha_prev[c] = s.sw_alpha[c];
                     s.seed[c] = s.s2[c];
                     s.zs[c] = a.z[s.s2[c]];
+                    s_vz[c] = Vec<R>::make(s.zs[c]);
+                    s_vb[c] = Vec<R>::make(s.beta_prev[c]);
                     s.nsw[c] += 1;
                 }
                 if (!grid_barrier(a.sync, epoch)) return;

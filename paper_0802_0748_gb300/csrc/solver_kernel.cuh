@@ -7,6 +7,22 @@
 
 namespace scocg {
 
+// A warp sum parked in a double-sized scratch slot in its own type, so that
+// only the final sum over warps (NV threads of warp 0) uses the FP64 pipe:
+// on this GPU an FP64 instruction issued by every warp of an SM holds the
+// FP64 pipe for hundreds of cycles.
+__device__ __forceinline__ void park(double* slot, double v) { *slot = v; }
+__device__ __forceinline__ void park(double* slot, float v) { *reinterpret_cast<float*>(slot) = v; }
+__device__ __forceinline__ void park(double* slot, dfs v) { *reinterpret_cast<dfs*>(slot) = v; }
+template <typename T> __device__ __forceinline__ double unpark(const double* slot);
+template <> __device__ __forceinline__ double unpark<double>(const double* slot) { return *slot; }
+template <> __device__ __forceinline__ double unpark<float>(const double* slot) {
+    return (double)*reinterpret_cast<const float*>(slot);
+}
+template <> __device__ __forceinline__ double unpark<dfs>(const double* slot) {
+    return to_double(*reinterpret_cast<const dfs*>(slot));
+}
+
 // CTA sum of per-thread values: the warp-level part in the values' own type
 // (FP32 for complex64 vectors), the sum over warps in FP64.
 template <int NV, typename T>
@@ -15,12 +31,12 @@ __device__ __forceinline__ void block_sum_n(T (&v)[NV], double* scratch, double*
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
         const T t = warp_sum(v[j]);
-        if (lane == 0) scratch[warp * NV + j] = to_double(t);
+        if (lane == 0) park(scratch + warp * NV + j, t);
     }
     __syncthreads();
     if (threadIdx.x < NV) {
         double s = 0.0;
-        for (int w = 0; w < kWarps; ++w) s += scratch[w * NV + threadIdx.x];
+        for (int w = 0; w < kWarps; ++w) s += unpark<T>(scratch + w * NV + threadIdx.x);
         out[threadIdx.x] = s;
     }
     __syncthreads();
@@ -198,10 +214,14 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
     constexpr bool kFull = std::is_same<R, double>::value;   // full-vector mode compiled (FP64 only)
     __shared__ SeedScalars s;
     __shared__ double s_part[8];
-    __shared__ int s_flag[4];
+    __shared__ int s_flag[5];
     __shared__ double s_min[kWarps];
     __shared__ int s_arg[kWarps];
     __shared__ ShiftInputs s_c;          // inputs of a deferred phase C
+    // z_s, beta_{n-1}, alpha_n in the vector type, converted once by thread 0
+    // whenever they change (every thread converting them would queue all
+    // warps on the FP64 pipe at each phase start)
+    __shared__ V s_vs[3];
     SCOCG_DYN_SHARED(double2, s_full);   // full-vector mode: per-shift scalars of the iteration
 
     const int tid = threadIdx.x;
@@ -220,6 +240,7 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
     const int nred = dense_proj ? 3 + 2 * M : 3;
     double* myB = a.partB + cta;              // value-major partials: value j at myB[j * G]
     unsigned long long epoch = 0;
+    const double tol2 = a.tol * a.tol;
     const int k_own = cta + tid * G;          // the shift this thread owns (if < K)
     const bool owns = k_own < a.K;
     // Phase C may be deferred into the next phase A when every shift owner of
@@ -265,7 +286,7 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
             for (int m = 0; m < M; ++m) { a.S.P[(size_t)k * M + m] = c2(0, 0); a.S.X[(size_t)k * M + m] = c2(0, 0); }
             a.S.frozen[k] = 0; a.S.iters[k] = 0; a.S.resid[k] = 1.0;
         }
-        if (tid < 4) s_flag[tid] = 0;
+        if (tid < 5) s_flag[tid] = 0;
         if (!grid_barrier(a.sync, epoch)) return;
         grid_sum_vm1(a.partB, nred, s.red, G);
         grid_sum(a.partC, kPartC, 1, s.red + nred, G);
@@ -277,6 +298,8 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
             s.beta_prev = c2(0, 0);
             s.seed = a.seed;
             s.zs = a.z[a.seed];
+            s_vs[0] = Vec<R>::make(s.zs);
+            s_vs[1] = Vec<R>::make(s.beta_prev);
             s.n = 0;
             s.active = a.K;
             s.replace_on = kMixed && a.replace_every > 0;
@@ -301,13 +324,13 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
         // ---- phase A: q_n = (z_s - H) r_n + beta_{n-1} q_{n-1}; partial r_n^T q_n
         // (with a deferred phase C of iteration n-1 in warp 0)
         {
-            const V zs = Vec<R>::make(s.zs);
-            const V bp = Vec<R>::make(s.beta_prev);
+            const V zs = s_vs[0];
+            const V bp = s_vs[1];
             AT rq[2] = {};
             const bool c_here = pending;           // uniform over the grid
             if (c_here && warp == 0) {
                 int act = 0, bad = 0;
-                if (owns && !a.S.frozen[k_own]) shift_update(a, k_own, s_c, M, a.tol * a.tol, act, bad);
+                if (owns && !a.S.frozen[k_own]) shift_update(a, k_own, s_c, M, tol2, act, bad);
                 act = __popc(__ballot_sync(0xffffffffu, act));
                 bad = __any_sync(0xffffffffu, bad);
                 if (lane == 0) { s_flag[0] = act; s_flag[1] = bad; }
@@ -354,6 +377,7 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
                 s.alpha = cdiv(s.rho, rq);
                 if (a.debug_inject == 2 && s.n == 3) s.alpha = c2(__longlong_as_double(0x7ff8000000000000ll), 0);
                 if (!cfinite(s.alpha)) st = SCOCG_ERR_BREAKDOWN;
+                s_vs[2] = Vec<R>::make(s.alpha);
                 s.shift_iters += active;
             }
             s.active = active;
@@ -394,8 +418,8 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
 
         // ---- phase B: r_{n+1} = r_n - alpha_n q_n; partials rho, ||r||^2, c^T r
         {
-            const V al = Vec<R>::make(s.alpha);
-            const V bp = Vec<R>::make(s.beta_prev);
+            const V al = s_vs[2];
+            const V bp = s_vs[1];
             const bool track_x = kMixed && s.replace_on;
             bool plain = !track_x;
             if constexpr (kFull) plain = plain && a.Xf == nullptr;
@@ -476,6 +500,7 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
             s.rnorm_next = sqrt(s.red[2]);
             s.rn_b = s.rnorm_next / s.bnorm;
             s_c.rn_b2 = s.rn_b * s.rn_b;
+            s_flag[4] = a.tol > 0.0 && s_c.rn_b2 <= tol2;    // the seed (pi = 1) has converged
         } else if (tid == 64) {
             s.beta_next = cdiv(c2(s.red[0], s.red[1]), s.rho);
         }
@@ -484,8 +509,7 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
         // ---- phase C: per-shift scalar recurrences for this CTA's shifts
         // (one complex reciprocal per shift; 1/pi^k_n is carried between
         // iterations and residuals are compared squared), here or deferred
-        const double tol2 = a.tol * a.tol;
-        const bool seed_conv = a.tol > 0.0 && s_c.rn_b2 <= tol2;   // the seed has pi = 1
+        const bool seed_conv = s_flag[4] != 0;
         const bool defer = defer_ok && !seed_conv;
         if (!defer) {
             int my_active = 0, my_bad = 0;
@@ -497,6 +521,7 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
         pending = defer;
         if (tid == 0) {
             s.beta_prev = s.beta_next;
+            s_vs[1] = Vec<R>::make(s.beta_prev);
             s.alpha_prev = s.alpha;
             s.rho_prev = s.rho;
             s.rho = c2(s.red[0], s.red[1]);
@@ -598,6 +623,8 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
                 s.rnorm = s.rnorm / cabs_(pin1);
                 s.seed = s2;
                 s.zs = a.z[s2];
+                s_vs[0] = Vec<R>::make(s.zs);
+                s_vs[1] = Vec<R>::make(s.beta_prev);
                 s.n_switch += 1;
                 s.replace_on = 0;        // the new seed's full solution is not tracked
             }
@@ -631,6 +658,7 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
                 if (tid == 0) {
                     s.rho = c2(s.red[0], s.red[1]);
                     s.beta_prev = cdiv(s.rho, s.rho_prev);
+                    s_vs[1] = Vec<R>::make(s.beta_prev);
                     s.rnorm = sqrt(s.red[2]);
                     s.n_replace += 1;
                 }
@@ -660,8 +688,15 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
 }
 
 // One solve on the whole grid.
+// CTAs per SM the persistent kernel is compiled for: two (64 registers a
+// thread) hide the latency of the FP32-pipe modes; FP64 solves are bound by
+// the FP64 pipe, where one CTA per SM (128 registers, half the CTAs at every
+// grid barrier) measured faster.
+template <typename R> struct MinBlocks { static constexpr int value = 2; };
+template <> struct MinBlocks<double> { static constexpr int value = 1; };
+
 template <typename R, class Apply>
-__global__ void __launch_bounds__(kBlock, 2) cocg_persistent(SolveArgs<R> a, Apply ap) {
+__global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) cocg_persistent(SolveArgs<R> a, Apply ap) {
     cocg_body(a, ap, (int)gridDim.x, (int)blockIdx.x);
 }
 
