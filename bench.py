@@ -65,15 +65,21 @@ BATCH_BOUNDS = (-6.041048698881869, 5.997536652116761)
 
 # DRAM traffic per seed iteration of the persistent solve kernel, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum over a 60-iteration
-# launch on this workload, divided by 60); valid only for the kernel sources
-# with this digest.
+# launch on this workload, divided by 60; the command is in profiles/); valid
+# only for the kernel sources with this digest.
 TRAFFIC = {"digest": None, "mixed": None, "fp64": None}
+
+
+# The sources of the persistent solve kernel and its launch (the kernel the
+# roofline line describes); the traffic figure is valid only for this digest.
+KERNEL_SOURCES = ("common.cuh", "dfloat.cuh", "solver.cuh", "solver_kernel.cuh", "solver_launch.h", "solver.cu",
+                  "layout.cu")
 
 
 def kernel_digest() -> str:
     h = hashlib.sha256()
-    for f in sorted((ROOT / "paper_0802_0748_gb300" / "csrc").glob("*")):
-        h.update(f.read_bytes())
+    for name in KERNEL_SOURCES:
+        h.update((ROOT / "paper_0802_0748_gb300" / "csrc" / name).read_bytes())
     return h.hexdigest()[:16]
 
 
