@@ -31,7 +31,9 @@ Other workloads are timed once beside the headline (``--legs``):
   chain  open chain of 4,096 sites, b = e_0, 64 shifts + 0.01i, FP64 to 1e-10;
   adjoint  dL/dH of sum_k w_k Im G_00(z_k) on the 24^3 x 4 matrix, 128 shifts;
   hubbard  matrix-free extended Hubbard ring, 14 sites, 7 up 7 down, 128
-         shifts + 0.05i, FP64 and complex64.
+         shifts + 0.05i, FP64, compensated and complex64;
+  density  local densities by the Fermi integral at 64 sites of the 32^3 x 4
+         matrix (256 energies, compensated block solves).
 
 --impl reference times the CPU oracle (plain FP64 C) on a bounded sample of
 the same workload.
@@ -391,6 +393,31 @@ def leg_hubbard(scocg, dev, stream, hbm):
     return out
 
 
+def leg_density(scocg, dev, stream):
+    """Local densities rho_jj by the Fermi integral (Eq. densityM) at 64 seeded
+    sites of the 32^3 x 4 Anderson matrix: 256 grid energies over the spectrum
+    + 0.02 i, mu = 0, kT = 0.05, compensated block solves, tol 1e-8."""
+    import numpy as np
+    import torch
+    from paper_0802_0748_gb300 import inputs
+    wl = inputs.workload("batch", "full", bounds=BATCH_BOUNDS)
+    h = wl.csr
+    sites = wl.proj_idx[:64]
+    rhs = torch.from_numpy(wl.rhs[:64]).to(dev)
+    lo, hi = BATCH_BOUNDS
+    args = (0.0, 0.05, 0.02, lo - 0.5, hi + 0.5, 256)
+    hh = scocg.scocg_create_csr(h.rowptr, h.col, h.val, opts=scocg.SolveOptions(precision=2, autotune=1))
+    scocg.scocg_density(hh, *args, rhs[:32], proj_idx=sites[:32], tol=1e-8)    # autotune + warm-up
+    (rho, info), ms = timed(stream, lambda: scocg.scocg_density(hh, *args, rhs, proj_idx=sites, tol=1e-8))
+    scocg.scocg_destroy(hh)
+    r = rho.cpu().numpy()[:, 0]
+    return {"ms": ms, "sites_per_s": 64 / (ms * 1e-3), "shift_iter_per_s": info["shift_iters"] / (ms * 1e-3),
+            "status": info["status"], "rho_mean": float(r.mean()), "rho_min": float(r.min()),
+            "rho_max": float(r.max()),
+            "workload": "rho_jj at 64 sites of anderson-32^3x4, mu 0, kT 0.05, delta 0.02, 256 energies, "
+                        "compensated block solves, tol 1e-8"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -401,7 +428,7 @@ def main():
     ap.add_argument("--compare", default="fp64,mixed", help="comma list of other precisions timed once beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--max-iter", type=int, default=0, help="cap on seed iterations (0 = to convergence)")
-    ap.add_argument("--legs", default="batch,multi,chain,adjoint,hubbard",
+    ap.add_argument("--legs", default="batch,multi,chain,adjoint,hubbard,density",
                     help="comma list of the other workloads, each timed once beside the headline")
     args = ap.parse_args()
 
@@ -541,6 +568,8 @@ def main():
         legs["adjoint"] = leg_adjoint(scocg, dev, stream)
     if "hubbard" in leg_names:
         legs["hubbard"] = leg_hubbard(scocg, dev, stream, hbm)
+    if "density" in leg_names:
+        legs["density"] = leg_density(scocg, dev, stream)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -225,6 +225,28 @@ int scocg_grad(scocg_handle h, const scocg_c128 *shifts, int nshift, const void 
                const scocg_c128 *dL_dG, double *dL_dval, scocg_info *info);
 
 /*
+ * scocg_density -- density-matrix elements by the Fermi integral of Eq. densityM:
+ *   rho_m = -(1/pi) int de Im G_m(e + i delta) f((e - mu) / kT)
+ * taken on the uniform real-axis grid e_k = emin + k (emax - emin) / (nquad - 1),
+ * k < nquad, with trapezoid weights, where G_m(z) = c_m^T (z I - H)^{-1} b comes
+ * from one shifted-COCG solve on the shifts e_k + i delta (the block or the
+ * one-right-hand-side path of scocg_solve, same rhs / projection conventions).
+ * This is the projected density matrix c_m^T rho b when the eigenstate weights
+ * (c_m^T phi)(phi^T b) are real (unit vectors, or c = conj(b)); delta > 0
+ * broadens it by a Lorentzian (error O(delta / kT)), and the window should
+ * cover the spectrum with a margin of several delta.
+ *   mu, kT       chemical potential and k_B T (kT >= 0; kT = 0 is the step)
+ *   delta        broadening, > 0
+ *   emin < emax  energy window;  2 <= nquad <= 4096
+ *   rho_out      device double [nrhs][nproj], written
+ * Returns what the solve returns (SCOCG_NOT_CONVERGED leaves rho valid).
+ * Allocates a device buffer for the intermediate G.
+ */
+int scocg_density(scocg_handle h, double mu, double kT, double delta, double emin, double emax, int nquad,
+                  const void *rhs, int nrhs, const int64_t *proj_idx, const void *proj_vec, int nproj,
+                  double tol, double *rho_out, scocg_info *info);
+
+/*
  * scocg_solve_multi -- several independent solves (systems of different sizes,
  * one right-hand side each) in ONE cooperative launch: the GPU's co-resident
  * CTAs are split among the systems (at least enough for each system's shifts,

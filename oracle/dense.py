@@ -12,6 +12,10 @@ Each function is the plain definition it names, with a library routine
                       4^L Fock space from Jordan-Wigner Kronecker products, then
                       restricted to an (N_up, N_dn) sector.
 * ``grad_dense``      dG/dH_ab = (A^{-T} c)_a (A^{-1} b)_b from the dense inverse.
+* ``fermi``, ``density_exact``, ``density_quadrature``  the density matrix of
+                      Eqs. densityM-1 / densityM: the Fermi-weighted eigenstate
+                      sum (dense eigendecomposition) and the real-axis Fermi
+                      integral of given Green's functions on a uniform grid.
 """
 from __future__ import annotations
 
@@ -157,3 +161,32 @@ def grad_dense(H: np.ndarray, shifts, b, c, gbar) -> np.ndarray:
         y = np.linalg.solve(A.T, c)
         g += np.real(np.conj(gbar[k]) * np.outer(y, x))
     return g
+
+
+def fermi(e, mu: float, kT: float):
+    """Fermi-Dirac occupation f((e - mu)/kT) of Eq. densityM; kT = 0 is the
+    step function (1/2 at e = mu)."""
+    e = np.asarray(e, dtype=np.float64)
+    if kT <= 0.0:
+        return np.where(e < mu, 1.0, np.where(e > mu, 0.0, 0.5))
+    return 0.5 * (1.0 - np.tanh((e - mu) / (2.0 * kT)))
+
+
+def density_exact(H: np.ndarray, b, C, mu: float, kT: float) -> np.ndarray:
+    """rho_m = sum_alpha f(lambda_alpha) (C_m^T phi_alpha)(phi_alpha^T b): the
+    density matrix of Eq. densityM-1 (Fermi-weighted eigenstates, the
+    zero-broadening limit of Eq. densityM) projected on C_m and b, by a dense
+    symmetric eigendecomposition."""
+    lam, phi = np.linalg.eigh(H)
+    C = np.atleast_2d(np.asarray(C, dtype=np.complex128))
+    return ((C @ phi) * fermi(lam, mu, kT)) @ (phi.T @ np.asarray(b, dtype=np.complex128))
+
+
+def density_quadrature(G: np.ndarray, energies, mu: float, kT: float) -> np.ndarray:
+    """Eq. densityM on a uniform real-axis grid: rho_m = -(1/pi) sum_k w_k
+    f(e_k) Im G_m(e_k + i delta) with trapezoid weights w_k, given G[m, k]."""
+    e = np.asarray(energies, dtype=np.float64)
+    h = e[1] - e[0]
+    w = np.full(e.size, h)
+    w[0] = w[-1] = 0.5 * h
+    return -(np.asarray(G).imag * (w * fermi(e, mu, kT))).sum(axis=-1) / np.pi

@@ -28,6 +28,7 @@ EXPORTED = [
     "scocg_create_csr", "scocg_create_hubbard", "scocg_dim", "scocg_set_opts", "scocg_apply",
     "scocg_solve", "scocg_solve_full", "scocg_grad", "scocg_destroy", "scocg_strerror",
     "scocg_hubbard_tables", "scocg_solve_csr_noalloc", "scocg_solve_multi", "scocg_multi_release",
+    "scocg_density",
 ]
 
 
@@ -94,6 +95,7 @@ def lib() -> ctypes.CDLL:
         L.scocg_solve.argtypes = [P, P, I, P, I, P, P, I, D, P, ctypes.POINTER(Info)]
         L.scocg_solve_full.argtypes = [P, P, I, P, D, P, ctypes.POINTER(Info)]
         L.scocg_grad.argtypes = [P, P, I, P, I, P, P, I, D, P, P, ctypes.POINTER(Info)]
+        L.scocg_density.argtypes = [P, D, D, D, D, D, I, P, I, P, P, I, D, P, ctypes.POINTER(Info)]
         L.scocg_destroy.argtypes = [P]
         L.scocg_destroy.restype = None
         L.scocg_strerror.argtypes = [I]
@@ -271,6 +273,41 @@ def scocg_solve(h: Handle, shifts, rhs, proj_idx=None, proj_vec=None, tol: float
                              ctypes.byref(info))
     _check(code, "scocg_solve")
     return G, _info_dict(info, it, rs, nrhs, K, code)
+
+
+def scocg_density(h: Handle, mu: float, kT: float, delta: float, emin: float, emax: float, nquad: int, rhs,
+                  proj_idx=None, proj_vec=None, tol: float = 1e-10):
+    """scocg_density: returns (rho [nrhs][nproj] CUDA float64 tensor, info dict).
+
+    rhs / proj_idx / proj_vec as in scocg_solve; the shifts are the nquad grid
+    energies of [emin, emax] plus i delta."""
+    import torch
+    rhs = rhs if rhs.dim() == 2 else rhs.reshape(1, -1)
+    if rhs.dtype != torch.complex128 or not rhs.is_cuda:
+        raise TypeError("rhs must be a CUDA complex128 tensor")
+    rhs = rhs.contiguous()
+    nrhs = rhs.shape[0]
+    pidx_p = pvec_p = None
+    keep = None
+    if proj_idx is not None:
+        keep = np.ascontiguousarray(np.asarray(proj_idx, dtype=np.int64))
+        if keep.ndim == 1:
+            keep = np.ascontiguousarray(np.broadcast_to(keep, (nrhs, keep.size)))
+        M = keep.shape[1]
+        pidx_p = keep.ctypes.data
+    else:
+        pv = (proj_vec if proj_vec.dim() == 2 else proj_vec.reshape(1, -1)).contiguous()
+        if pv.dtype != torch.complex128 or not pv.is_cuda:
+            raise TypeError("proj_vec must be a CUDA complex128 tensor")
+        keep = pv
+        M = pv.shape[0]
+        pvec_p = _dev(pv)
+    rho = torch.zeros((nrhs, M), dtype=torch.float64, device=rhs.device)
+    info, it, rs = _info_struct(nrhs, int(nquad))
+    code = lib().scocg_density(h.ptr, float(mu), float(kT), float(delta), float(emin), float(emax), int(nquad),
+                               _dev(rhs), nrhs, pidx_p, pvec_p, M, float(tol), _dev(rho), ctypes.byref(info))
+    _check(code, "scocg_density")
+    return rho, _info_dict(info, it, rs, nrhs, int(nquad), code)
 
 
 def scocg_solve_full(h: Handle, shifts, rhs, tol: float = 1e-10):

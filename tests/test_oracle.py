@@ -315,3 +315,53 @@ def test_fixed_iterates_are_seed_independent_before_ritz_convergence(oracle_mod)
     c = oracle_mod.shifted_cocg(h.rowptr, h.col, h.val, shifts, b, proj_vec=[np.conj(b)], tol=0.0,
                                 max_iter=20, seed=8)
     assert relerr(a.G, c.G) < 1e-10
+
+
+# ------------------------------------------------------------------ density matrix (Eq. densityM)
+def test_density_half_filling_bipartite_is_one_half():
+    """Closed form: on a bipartite lattice with zero onsite energy the spectrum is
+    symmetric and every site holds exactly 1/2 at mu = 0, at any temperature
+    (an even chain: no zero mode on the step of the kT = 0 occupation)."""
+    from oracle import dense
+    L = 16
+    H = np.diag(-np.ones(L - 1), 1) + np.diag(-np.ones(L - 1), -1)
+    for kT in (0.0, 0.05, 0.7):
+        for j in (0, 5, 15):
+            e = np.zeros(L); e[j] = 1.0
+            assert abs(dense.density_exact(H, e, [e], 0.0, kT)[0] - 0.5) < 1e-13
+
+
+def test_density_limits_count_and_completeness():
+    """kT = 0: the trace is the number of eigenvalues below mu; mu far above the
+    spectrum: rho = c^T b (completeness of the eigenvectors)."""
+    from oracle import dense
+    rng = np.random.default_rng(5)
+    A = rng.normal(size=(12, 12)); H = (A + A.T) / 2
+    lam = np.linalg.eigvalsh(H)
+    mu = 0.5 * (lam[4] + lam[5])
+    I = np.eye(12)
+    tr = sum(dense.density_exact(H, I[j], [I[j]], mu, 0.0)[0] for j in range(12))
+    assert abs(tr - 5.0) < 1e-12
+    b = rng.normal(size=12) + 1j * rng.normal(size=12)
+    c = rng.normal(size=12)
+    assert abs(dense.density_exact(H, b, [c], 1e3, 0.1)[0] - c @ b) < 1e-12
+
+
+def test_density_quadrature_converges_to_eigenstate_sum():
+    """Eq. densityM on a broadened real-axis grid approaches the Fermi-weighted
+    eigenstate sum (Eq. densityM-1) as delta -> 0: the error of the Lorentzian
+    smoothing of f is O(delta / kT), so halving delta roughly halves it."""
+    from oracle import dense
+    rng = np.random.default_rng(9)
+    A = rng.normal(size=(16, 16)); H = (A + A.T) / 4
+    lo, hi = np.linalg.eigvalsh(H)[[0, -1]]
+    e0 = np.eye(16)[0]
+    mu, kT = 0.1, 0.2
+    exact = dense.density_exact(H, e0, [e0], mu, kT)[0]
+    errs = []
+    for delta in (0.04, 0.02, 0.01):
+        grid = np.linspace(lo - 4.0, hi + 4.0, int(round((hi - lo + 8.0) / (delta / 8))) + 1)
+        G = dense.green_dense(H, grid + 1j * delta, e0, [e0])
+        errs.append(abs(dense.density_quadrature(G, grid, mu, kT)[0] - exact))
+    assert errs[2] < 0.65 * errs[1] < 0.65 ** 2 * errs[0]
+    assert errs[2] < 1e-2
