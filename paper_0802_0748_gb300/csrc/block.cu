@@ -83,6 +83,14 @@ int run_block(scocg_ctx* h, const scocg_c128* shifts, int K, const void* rhs, in
     a.col = h->d_col;
     if constexpr (std::is_same<W, double>::value) a.val = h->d_val64;
     else a.val = h->d_val32;
+    // the 4x4-blocked layout, when the handle has it: each gathered row of x
+    // then serves the four rows of a block row
+    const bool blocked = h->bsr_ok && h->d_unit_off && h->n % 4 == 0;
+    a.unit_off = blocked ? h->d_unit_off : nullptr;
+    a.bcol = blocked ? h->d_bcol : nullptr;
+    if constexpr (std::is_same<W, double>::value) a.bval = blocked ? h->d_bval64 : nullptr;
+    else a.bval = blocked ? h->d_bval32 : nullptr;
+    a.nslots = blocked ? h->nslots : 0;
     a.b = static_cast<const double2*>(rhs);
     a.nrhs = nrhs;
     a.cidx = d_cidx;
@@ -172,9 +180,11 @@ int run_block(scocg_ctx* h, const scocg_c128* shifts, int K, const void* rhs, in
         info->n_replace = 0;
         info->shift_iters = c.stats.shift_iters;
         info->seconds = ms * 1e-3;
-        // one block iteration: H once, six passes over the [n][T] vectors
+        // one block iteration: H once in the layout used, six passes over the [n][T] vectors
         const double vb = prec == SCOCG_MIXED ? 8.0 : 16.0;
-        info->bytes_per_iter = (double)h->nnz * (4.0 + sizeof(W)) + 4.0 * (n + 1) + 6.0 * vb * (double)n * T;
+        const double hb = blocked ? (double)h->nslots * 8 * (4.0 + 16.0 * sizeof(W)) + 4.0 * (h->nunits_bsr + 1)
+                                  : (double)h->nnz * (4.0 + sizeof(W)) + 4.0 * (n + 1);
+        info->bytes_per_iter = hb + 6.0 * vb * (double)n * T;
     }
     return worst;
 }

@@ -72,6 +72,11 @@ struct BlockArgs {
     GridSync sync;
     SolveStats* stats;
     unsigned long long* dbg;
+    // 4x4-blocked sliced ELL of H (unit_off null: the CSR apply above)
+    const int* unit_off;
+    const int* bcol;
+    const W* bval;                  // row-major 4x4 blocks
+    int64_t nslots;
     unsigned long long* phase_ns;   // phase-timer builds: [grid][8] accumulated ns
     unsigned long long* rflag;      // published reduction epoch (grid_reduce)
     double* res;                    // [max(kNvA, kNvB) * T] published sums
@@ -223,6 +228,17 @@ __device__ __forceinline__ bool grid_reduce(const GridSync& g, unsigned long lon
     return true;
 }
 
+// Four consecutive values of a 4x4 block row (16- or 32-byte aligned).
+__device__ __forceinline__ void block_row4(const float* p, float (&v)[4]) {
+    const float4 t = ld_stream(reinterpret_cast<const float4*>(p));
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void block_row4(const double* p, double (&v)[4]) {
+    const double2 a = ld_stream(reinterpret_cast<const double2*>(p));
+    const double2 b = ld_stream(reinterpret_cast<const double2*>(p) + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
 // order-preserving bits of a non-negative double (for atomicMax)
 __device__ __forceinline__ unsigned long long key_bits(double v) {
     return (unsigned long long)__double_as_longlong(v);
@@ -275,7 +291,47 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_block(BlockArgs<R> a) {
                 const bool run = s.state[cl] == kSlotRun;
                 const V zs = s_vz[cl];
                 const V bp = s_vb[cl];
-                for (int64_t i0 = rbeg + warp * RPW; i0 < rend; i0 += kWarps * RPW) {
+                if (a.unit_off) {
+                    // block rows: lane group `sub` takes block row B (rows 4B..4B+3);
+                    // per column block its lane of slot cl reads the four x entries
+                    // once and applies all sixteen block values, so each gathered
+                    // x row of T entries serves four rows
+                    const int64_t nbr = a.n / 4;
+                    const int64_t bbeg = (int64_t)cta * nbr / G, bend = (int64_t)(cta + 1) * nbr / G;
+                    for (int64_t b0 = bbeg + warp * RPW; b0 < bend; b0 += kWarps * RPW) {
+                        const int64_t B = b0 + sub;
+                        if (B >= bend || !run) continue;
+                        V rowacc[4] = {vzero<V>(), vzero<V>(), vzero<V>(), vzero<V>()};
+                        const int64_t u = B >> 3;
+                        const int br = (int)(B & 7);
+                        int s0 = a.unit_off[u], s1 = a.unit_off[u + 1];
+                        if (!chk(a.dbg, 26, s1, a.nslots + 1) || !chk(a.dbg, 26, s0, s1 + 1)) s0 = s1 = 0;
+                        for (int sl = s0; sl < s1; ++sl) {
+                            const int cb = ld_stream(a.bcol + (size_t)sl * 8 + br);
+                            if (cb < 0 || !chk(a.dbg, 27, (long long)cb * 4 + 3, a.n)) continue;
+                            V xv[4];
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) xv[j] = a.r[((size_t)cb * 4 + j) * T + cl];
+                            const W* hb = a.bval + ((size_t)sl * 8 + br) * 16;
+#pragma unroll
+                            for (int rr = 0; rr < 4; ++rr) {
+                                W hv[4];
+                                block_row4(hb + rr * 4, hv);
+#pragma unroll
+                                for (int j = 0; j < 4; ++j) cfma_r(rowacc[rr], hv[j], xv[j]);
+                            }
+                        }
+#pragma unroll
+                        for (int rr = 0; rr < 4; ++rr) {
+                            const size_t o = ((size_t)B * 4 + rr) * T + cl;
+                            const V ri = a.r[o];
+                            const V qn = vcfma(bp, a.q[o], vsub(vcfma(zs, ri, vzero<V>()), rowacc[rr]));
+                            a.q[o] = qn;
+                            acc_bil(acc[0], acc[1], ri, qn);
+                        }
+                    }
+                }
+                for (int64_t i0 = rbeg + warp * RPW; !a.unit_off && i0 < rend; i0 += kWarps * RPW) {
                     const int64_t i = i0 + sub;
                     const bool has = i < rend;
                     int e0 = 0, e1 = 0;
