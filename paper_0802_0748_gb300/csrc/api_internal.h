@@ -18,7 +18,6 @@ struct Ctrl {
     int pad;
     SolveStats stats;
     unsigned long long dbg[4];   // checked builds: (flag, site, index, limit)
-    unsigned long long rflag;    // last barrier epoch whose reduction has been published
 };
 
 // Sequential carving of a buffer into 256-byte aligned pieces; with a null

@@ -109,7 +109,6 @@ int run_block(scocg_ctx* h, const scocg_c128* shifts, int K, const void* rhs, in
     a.stats = &h->d_ctrl->stats;
     a.dbg = h->d_ctrl->dbg;
     a.phase_ns = nullptr;
-    a.rflag = &h->d_ctrl->rflag;
 #ifdef SCOCG_PHASE_TIMERS
     static unsigned long long* h_ns = nullptr;
     static int h_ns_n = 0;

@@ -78,8 +78,7 @@ struct BlockArgs {
     const W* bval;                  // row-major 4x4 blocks
     int64_t nslots;
     unsigned long long* phase_ns;   // phase-timer builds: [grid][8] accumulated ns
-    unsigned long long* rflag;      // published reduction epoch (grid_reduce)
-    double* res;                    // [max(kNvA, kNvB) * T] published sums
+    double* res;                    // [max(kNvA, kNvB) * T] sums published by grid_reduce
 };
 
 template <int T>
@@ -172,57 +171,24 @@ __device__ __forceinline__ void grid_sum_vm(const double* part, int G, int nval,
 }
 
 // A grid barrier that also sums value-major partials part[v * G + cta]
-// (v < nval) into out[] (shared) in every CTA.  The CTA that arrives last
-// reads all partials once, writes the nval sums to res[] (global) and
-// publishes the barrier epoch in *flag; the other CTAs wait for the flag
-// (bounded, like grid_barrier) and read the nval sums.  The partials are thus
-// read by one CTA instead of all G, which matters when nval = 4T is large.
-// res[] can be reused by the next call: no CTA arrives there before it has
-// read the previous sums.
-__device__ __forceinline__ bool grid_reduce(const GridSync& g, unsigned long long& epoch,
-                                            unsigned long long* flag, const double* part, int G, int nval,
-                                            double* res, double* out) {
-    __shared__ int s_last, s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ++epoch;
-        __threadfence();                                  // release this CTA's partials
-        const unsigned long long old = atomicAdd(g.count, 1ull);
-        s_last = old + 1 == epoch * (unsigned long long)g.nctas;
-        __threadfence();                                  // acquire: the last arriver sees every partial
-        s_ok = 1;
+// (v < nval) into out[] (shared) in every CTA: after the barrier CTA c sums
+// the values v = c, c + G, ... (one warp each, the CTAs in a fixed order) and
+// writes them to res[] (global); a second barrier; then every CTA reads the
+// nval sums.  The partials are read once in all, spread over the CTAs, and
+// every CTA gets bit-identical sums.  res[] can be reused by the next call: no
+// CTA passes that call's first barrier before all have read these sums.
+__device__ __forceinline__ bool grid_reduce(const GridSync& g, unsigned long long& epoch, const double* part,
+                                            int G, int nval, double* res, double* out) {
+    if (!grid_barrier(g, epoch)) return false;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int v = (int)blockIdx.x % G + G * warp; v < nval; v += G * kWarps) {
+        const double* pv = part + (size_t)v * G;
+        double sum = 0.0;
+        for (int c = lane; c < G; c += 32) sum += __ldcg(pv + c);
+        sum = warp_sum(sum);
+        if (lane == 0) res[v] = sum;
     }
-    __syncthreads();
-    if (s_last) {
-        grid_sum_vm(part, G, nval, out);                  // ends with __syncthreads
-        for (int t = threadIdx.x; t < nval; t += kBlock) res[t] = out[t];
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            atomicMax(flag, epoch);                       // publish
-            if (ld_volatile_i32(g.status) < 0) s_ok = 0;
-        }
-        __syncthreads();
-        return s_ok != 0;
-    }
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        const uint64_t t0 = globaltimer_ns();
-        while (ld_acquire_u64(flag) < epoch) {
-            if (ld_volatile_i32(g.status) < 0) { ok = 0; break; }
-            if (globaltimer_ns() - t0 > g.timeout_ns) {
-                atomicCAS(g.status, 0, (int)SCOCG_ERR_TIMEOUT);
-                atomicCAS(g.status, 1, (int)SCOCG_ERR_TIMEOUT);
-                ok = 0;
-                break;
-            }
-        }
-        if (ok && ld_volatile_i32(g.status) < 0) ok = 0;
-        __threadfence();
-        s_ok = ok;
-    }
-    __syncthreads();
-    if (!s_ok) return false;
+    if (!grid_barrier(g, epoch)) return false;
     for (int t = threadIdx.x; t < nval; t += kBlock) out[t] = __ldcg(res + t);
     __syncthreads();
     return true;
@@ -365,7 +331,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_block(BlockArgs<R> a) {
                 }
             }
             SCOCG_MARK(0);
-            if (!grid_reduce(a.sync, epoch, a.rflag, a.partA, G, kNvA * T, a.res, s.red)) return;
+            if (!grid_reduce(a.sync, epoch, a.partA, G, kNvA * T, a.res, s.red)) return;
             SCOCG_MARK(1);
 
             // ---- decide: alpha per running slot, or finish it
@@ -449,7 +415,7 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_block(BlockArgs<R> a) {
             block_cols<T, 1, kNvB>(nb, s.scratch, a.partB, G, cta, 3);
         }
         SCOCG_MARK(2);
-        if (!grid_reduce(a.sync, epoch, a.rflag, a.partB, G, kNvB * T, a.res, s.red)) return;
+        if (!grid_reduce(a.sync, epoch, a.partB, G, kNvB * T, a.res, s.red)) return;
         SCOCG_MARK(3);
         if (tid < T) {
             const int c = tid;
