@@ -450,7 +450,11 @@ int scocg::solve_impl(scocg_ctx* h, const scocg_c128* shifts, int nshift, const 
     if (maxco <= 0) return SCOCG_ERR_CUDA;
     const int rpu = h->kind == HandleKind::kHubbard ? 32 : rows_per_unit(L.kind);
     const int64_t nunits = h->kind == HandleKind::kHubbard ? h->hub.nunits : (n + rpu - 1) / rpu;
+    // one warp per unit of rows and one thread per shift at least; small
+    // problems are latency bound and still gain from up to 32 CTAs (4,096-row
+    // chain: 24.4 us per iteration at 8 CTAs, 21.1 at 32)
     int64_t want = std::max<int64_t>((nunits + kWarps - 1) / kWarps, (K + kBlock - 1) / kBlock);
+    want = std::max<int64_t>(want, std::min<int64_t>(32, nunits));
     if (h->opts.grid > 0) want = h->opts.grid;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, maxco));
     if ((int64_t)grid * kBlock < K) return SCOCG_ERR_INVALID;

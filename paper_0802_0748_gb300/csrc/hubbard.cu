@@ -229,6 +229,9 @@ cudaError_t hubbard_launch_solve(const SolveArgs<R>& a, const Hubbard& hb, int g
     ap.dbg = a.dbg;
     void* args[] = {(void*)&a, (void*)&ap};
     const size_t smem = a.Xf ? (size_t)a.K * kFullSmem : 0;
+    if (smem > 0)   // above the 48 KB default together with the static part
+        cudaFuncSetAttribute((const void*)cocg_persistent<R, ApplyHubbard<W>>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return cudaLaunchCooperativeKernel((const void*)cocg_persistent<R, ApplyHubbard<W>>, dim3(grid), dim3(kBlock),
                                        args, smem, st);
 }

@@ -7,16 +7,28 @@
 
 namespace scocg {
 
+// Dynamic shared memory above the 48 KB default (with the static part) needs
+// the kernel's opt-in; the full-vector mode asks for up to kMaxFullShifts x
+// kFullSmem bytes.
+template <typename R, class Apply>
+static void allow_dyn_smem(size_t smem) {
+    if (smem > 0)
+        cudaFuncSetAttribute((const void*)cocg_persistent<R, Apply>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+}
+
 template <typename R, class Apply>
 static cudaError_t coop_launch(const SolveArgs<R>& a, const Apply& ap, int grid, cudaStream_t st) {
     void* args[] = {(void*)&a, (void*)&ap};
     const size_t smem = a.Xf ? (size_t)a.K * kFullSmem : 0;
+    allow_dyn_smem<R, Apply>(smem);
     return cudaLaunchCooperativeKernel((const void*)cocg_persistent<R, Apply>, dim3(grid), dim3(kBlock), args, smem,
                                        st);
 }
 
 template <typename R, class Apply>
 static int occupancy_of(size_t smem) {
+    allow_dyn_smem<R, Apply>(smem);
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cocg_persistent<R, Apply>, kBlock, smem) != cudaSuccess)
         return 0;

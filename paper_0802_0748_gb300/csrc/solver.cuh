@@ -333,6 +333,11 @@ struct SolveArgs {
 constexpr int kFullSmem = 3 * 16 + 4;   // per shift: 1/pi_n, beta^k, alpha^k, active flag
 
 // Shared per-CTA copy of the seed scalars; every CTA holds identical values.
+// CTA scratch of the block sums: per warp 3 + 2 kMaxProj values, or (FP64
+// block sums) kScratchNV values per thread
+constexpr int kScratchNV = 5;
+constexpr int kScratch = kWarps * (3 + 2 * kMaxProj) > kScratchNV * kBlock ? kWarps * (3 + 2 * kMaxProj)
+                                                                          : kScratchNV * kBlock;
 struct SeedScalars {
     double2 alpha, alpha_prev, beta_prev, rho, rho_prev, zs;
     double2 t2;                 // alpha_n beta_{n-1} / alpha_{n-1}
@@ -345,7 +350,7 @@ struct SeedScalars {
     double2 cr_cur[kMaxProj];   // c_m^T r_n
     double2 cr_next[kMaxProj];  // c_m^T r_{n+1}
     double red[4 + 2 * kMaxProj + 4];
-    double scratch[kWarps * (3 + 2 * kMaxProj)];
+    double scratch[kScratch];
 };
 
 // residual estimate of a shift from the seed residual norm and its pi

@@ -28,6 +28,24 @@ template <> __device__ __forceinline__ double unpark<dfs>(const double* slot) {
 template <int NV, typename T>
 __device__ __forceinline__ void block_sum_n(T (&v)[NV], double* scratch, double* out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if constexpr (std::is_same<T, double>::value) {
+        // FP64 values: every thread parks its values (scratch holds NV *
+        // kBlock doubles) and NV warps sum them, instead of NV five-step FP64
+        // warp sums in all kWarps warps (an FP64 instruction of a whole warp
+        // occupies the FP64 pipe ~16 cycles)
+        static_assert(NV <= kScratchNV, "scratch too small");
+#pragma unroll
+        for (int j = 0; j < NV; ++j) scratch[j * kBlock + threadIdx.x] = v[j];
+        __syncthreads();
+        if (warp < NV) {
+            double acc = 0.0;
+            for (int t = lane; t < kBlock; t += 32) acc += scratch[warp * kBlock + t];
+            acc = warp_sum(acc);
+            if (lane == 0) out[warp] = acc;
+        }
+        __syncthreads();
+        return;
+    }
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
         const T t = warp_sum(v[j]);
