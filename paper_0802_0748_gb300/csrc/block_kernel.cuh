@@ -395,19 +395,31 @@ __global__ void __launch_bounds__(kBlock, 2) cocg_block(BlockArgs<R> a) {
             const int st = s.state[cl];
             const V al = s_va[cl];
             const double2* bj = st == kSlotFresh ? a.b + (size_t)s.rhs[cl] * a.n : nullptr;
-            for (int64_t i0 = rbeg + warp * RPW; i0 < rend; i0 += kWarps * RPW) {
-                const int64_t i = i0 + sub;
-                if (i >= rend || st == kSlotEmpty) continue;
-                const size_t o = (size_t)i * T + cl;
-                V rn;
-                if (st == kSlotRun) {
-                    rn = r_update(a.r[o], al, a.q[o]);
-                } else {
-                    const double2 bi = bj[i];
-                    rn = Vec<R>::make(bi);
-                    a.q[o] = vzero<V>();
-                    nb[0] = fma(bi.x, bi.x, fma(bi.y, bi.y, nb[0]));
+            constexpr int64_t kStep = (int64_t)kWarps * RPW;
+            if (st == kSlotRun) {
+                // one row ahead: the next row's r and q are in flight while this
+                // row is updated and stored (same rows, same order per lane)
+                int64_t i = rbeg + warp * RPW + sub;
+                V r0 = vzero<V>(), q0 = vzero<V>();
+                if (i < rend) { r0 = a.r[(size_t)i * T + cl]; q0 = a.q[(size_t)i * T + cl]; }
+                for (; i < rend; i += kStep) {
+                    const int64_t inx = i + kStep;
+                    V r1 = vzero<V>(), q1 = vzero<V>();
+                    if (inx < rend) { r1 = a.r[(size_t)inx * T + cl]; q1 = a.q[(size_t)inx * T + cl]; }
+                    const V rn = r_update(r0, al, q0);
+                    a.r[(size_t)i * T + cl] = rn;
+                    acc_rr(acc[0], acc[1], acc[2], rn);
+                    r0 = r1; q0 = q1;
                 }
+            }
+            for (int64_t i0 = rbeg + warp * RPW; st == kSlotFresh && i0 < rend; i0 += kStep) {
+                const int64_t i = i0 + sub;
+                if (i >= rend) continue;
+                const size_t o = (size_t)i * T + cl;
+                const double2 bi = bj[i];
+                const V rn = Vec<R>::make(bi);
+                a.q[o] = vzero<V>();
+                nb[0] = fma(bi.x, bi.x, fma(bi.y, bi.y, nb[0]));
                 a.r[o] = rn;
                 acc_rr(acc[0], acc[1], acc[2], rn);
             }
