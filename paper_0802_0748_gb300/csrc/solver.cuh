@@ -55,9 +55,10 @@ struct SolveStats {          // device, written by CTA 0
 
 // ---------------------------------------------------------------- applies
 // How the persistent kernel's phase A hands units to warps: a contiguous
-// range per CTA; unit cta + G * (warp + W * j) (all CTAs interleaved); or
-// blocks of W consecutive units per CTA, the grid sweeping the units together.
-enum : int { kMapContiguous = 0, kMapStrided = 1, kMapSweep = 2 };
+// range per CTA (the blocked and CSR applies: measured fastest), or unit
+// cta + G * (warp + W * j), all CTAs interleaved (the Hubbard apply, whose
+// units are up-spin blocks of very different cost).
+enum : int { kMapContiguous = 0, kMapStrided = 1 };
 
 // Every apply maps (unit, lane) to at most one row and returns, on the lane
 // that owns the row, w = z_s x_row - (H x)_row.  The vector type VV sets the

@@ -44,20 +44,20 @@ __device__ __forceinline__ void block_sum_n(T (&v)[NV], double* scratch, double*
             if (lane == 0) out[warp] = acc;
         }
         __syncthreads();
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int j = 0; j < NV; ++j) {
-        const T t = warp_sum(v[j]);
-        if (lane == 0) park(scratch + warp * NV + j, t);
+        for (int j = 0; j < NV; ++j) {
+            const T t = warp_sum(v[j]);
+            if (lane == 0) park(scratch + warp * NV + j, t);
+        }
+        __syncthreads();
+        if (threadIdx.x < NV) {
+            double s = 0.0;
+            for (int w = 0; w < kWarps; ++w) s += unpark<T>(scratch + w * NV + threadIdx.x);
+            out[threadIdx.x] = s;
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    if (threadIdx.x < NV) {
-        double s = 0.0;
-        for (int w = 0; w < kWarps; ++w) s += unpark<T>(scratch + w * NV + threadIdx.x);
-        out[threadIdx.x] = s;
-    }
-    __syncthreads();
 }
 
 // per-thread accumulation of u^T v (bilinear) in the vector precision
@@ -248,8 +248,7 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
     // use a contiguous row range per CTA.
     const int64_t ubeg = (int64_t)cta * a.nunits / G, uend = (int64_t)(cta + 1) * a.nunits / G;
     constexpr bool kWhole = Apply::kMap != kMapContiguous;   // every CTA visits the whole unit range
-    const int64_t u_first = Apply::kMap == kMapStrided ? (int64_t)cta + (int64_t)G * warp
-                          : Apply::kMap == kMapSweep ? (int64_t)cta * kWarps + warp : ubeg + warp;
+    const int64_t u_first = Apply::kMap == kMapStrided ? (int64_t)cta + (int64_t)G * warp : ubeg + warp;
     const int64_t u_step = kWhole ? (int64_t)G * kWarps : kWarps;
     const int64_t u_end = kWhole ? a.nunits : uend;
     const int64_t rbeg = (int64_t)cta * a.n / G, rend = (int64_t)(cta + 1) * a.n / G;
@@ -357,8 +356,7 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
             // rotated so that warp 0 takes the last place in each round and,
             // when the rounds do not come out even, one unit fewer
             const int wi = c_here ? (warp + kWarps - 1) % kWarps : warp;
-            const int64_t a_first = Apply::kMap == kMapStrided ? (int64_t)cta + (int64_t)G * wi
-                                  : Apply::kMap == kMapSweep ? (int64_t)cta * kWarps + wi : ubeg + wi;
+            const int64_t a_first = Apply::kMap == kMapStrided ? (int64_t)cta + (int64_t)G * wi : ubeg + wi;
             for (int64_t u = a_first; u < u_end; u += u_step) {
                 int64_t row;
                 V w;
