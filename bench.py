@@ -69,7 +69,7 @@ BATCH_BOUNDS = (-6.041048698881869, 5.997536652116761)
 # capture (dram__bytes_read.sum + dram__bytes_write.sum over a 60-iteration
 # launch on this workload, divided by 60; the command is in profiles/); valid
 # only for the kernel sources with this digest.
-TRAFFIC = {"digest": "9e9409ee13a2b780", "df": (7.620042e9 + 47.796736e6) / 60}
+TRAFFIC = {"digest": "af586c71491254fd", "df": (7.622577e9 + 33.650688e6) / 60}
 
 
 # The sources of the persistent solve kernel and its launch (the kernel the
