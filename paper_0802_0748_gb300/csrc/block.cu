@@ -154,6 +154,16 @@ int run_block(scocg_ctx* h, const scocg_c128* shifts, int K, const void* rhs, in
                      "red2 %.3f C %.3f switch+top %.3f\n", T, grid,
                      tot[0] / grid * 1e-6, tot[1] / grid * 1e-6, tot[6] / grid * 1e-6, tot[2] / grid * 1e-6,
                      tot[3] / grid * 1e-6, tot[5] / grid * 1e-6, tot[4] / grid * 1e-6, tot[7] / grid * 1e-6);
+        // spread of the apply time over the CTAs (first and last CTA ids of the extremes)
+        double mn = 1e300, mx = 0.0;
+        int cmn = 0, cmx = 0;
+        for (int cc = 0; cc < grid; ++cc) {
+            const double v = (double)((volatile unsigned long long*)h_ns)[8 * cc];
+            if (v < mn) { mn = v; cmn = cc; }
+            if (v > mx) { mx = v; cmx = cc; }
+        }
+        std::fprintf(stderr, "scocg block apply per CTA ms: min %.3f (cta %d) max %.3f (cta %d)\n", mn * 1e-6, cmn,
+                     mx * 1e-6, cmx);
     }
 #endif
     if (c.dbg[0]) {
