@@ -15,6 +15,9 @@ Contents (each function cites the passage of arXiv:0802.0748 it follows):
                          Jordan-Wigner definition (Sec. IV.D).
 * ``dense``              dense LU Green's functions, closed forms, Fock-space
                          exact diagonalisation, dense gradients.
+* ``ground``             Lanczos / CG-inverse-iteration ground state and the
+                         one-particle operators c, c+ between sectors
+                         (Sec. II.C, Sec. IV.D).
 """
 from __future__ import annotations
 

@@ -151,6 +151,13 @@ def random_unit_complex(n: int, seed: int) -> np.ndarray:
     return v / np.linalg.norm(v)
 
 
+def random_unit_real(n: int, seed: int) -> np.ndarray:
+    """Seeded real vector with N(0,1) entries, normalised to 1 (a start vector)."""
+    rng = np.random.default_rng(seed)
+    v = rng.normal(size=n)
+    return v / np.linalg.norm(v)
+
+
 def cluster_sizes(nsys: int = 32, lmin: int = 14, lmax: int = 50, seed: int = 31) -> np.ndarray:
     """Edge lengths of the uneven Anderson clusters of the multi-system batch."""
     rng = np.random.default_rng(seed)
