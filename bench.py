@@ -33,7 +33,10 @@ Other workloads are timed once beside the headline (``--legs``):
   hubbard  matrix-free extended Hubbard ring, 14 sites, 7 up 7 down, 128
          shifts + 0.05i, FP64, compensated and complex64;
   density  local densities by the Fermi integral at 64 sites of the 32^3 x 4
-         matrix (256 energies, compensated block solves).
+         matrix (256 energies, compensated block solves);
+  ground  ground state of the 14-site ring by Lanczos (80 steps per cycle) and
+         CG inverse iteration (40 steps), tol 1e-8, FP64; then c_{0 up}|psi_0>
+         and the ionization spectrum (128 shifts, compensated solve).
 
 --impl reference times the CPU oracle (plain FP64 C) on a bounded sample of
 the same workload.
@@ -418,6 +421,42 @@ def leg_density(scocg, dev, stream):
                         "compensated block solves, tol 1e-8"}
 
 
+def leg_ground(scocg, dev, stream, hbm):
+    """Ground state of the 14-site ring (11,778,624 states, t=1 U=4 V=1,
+    periodic) from a seeded start vector: Lanczos (m = 80 per cycle) and CG
+    inverse iteration (40 steps), tol 1e-8, FP64; then b = c_{0 up}|psi_0> into
+    the 6-up sector and G(z) = b^T (z - H)^{-1} b on 128 ionization shifts
+    z = E_0 - w - 0.05 i, w in [-5, 20], compensated, tol 1e-6."""
+    import numpy as np
+    import torch
+    from paper_0802_0748_gb300 import inputs
+    wl = inputs.workload("hubbard", "full")
+    p = wl.hubbard
+    n = wl.n
+    h = scocg.scocg_create_hubbard(p["L"], p["n_up"], p["n_dn"], p["t"], p["U"], p["V"], p["periodic"])
+    h1 = scocg.scocg_create_hubbard(p["L"], p["n_up"] - 1, p["n_dn"], p["t"], p["U"], p["V"], p["periodic"],
+                                    opts=scocg.SolveOptions(precision=2))
+    v0 = torch.from_numpy(inputs.random_unit_real(n, 8)).to(dev)
+    (E, psi, info), ms = timed(stream, lambda: scocg.scocg_ground_state(h, v0, m=80, cg_steps=40, max_cycles=30,
+                                                                          tol=1e-8))
+    steps = info["lanczos_steps"] + info["cg_steps"]
+    gbs = info["bytes_per_step"] * steps / info["seconds"] / 1e9
+    b, ms_x = timed(stream, lambda: scocg.scocg_excite(h, h1, 0, 0, False, psi))
+    z = E - np.linspace(-5.0, 20.0, 128) - 0.05j
+    (G, sinfo), ms_s = timed(stream, lambda: scocg.scocg_solve(h1, z, b, proj_vec=b, tol=1e-6))
+    scocg.scocg_destroy(h)
+    scocg.scocg_destroy(h1)
+    return {"workload": "ground state of the Hubbard ring L=14, 7 up 7 down (11,778,624 states), t=1 U=4 V=1, "
+                        "Lanczos m=80 + CG 40 per cycle, tol 1e-8, FP64; c_{0 up}|psi_0> (6 up, 10,306,296 "
+                        "states) and 128 ionization shifts, compensated, tol 1e-6",
+            "ground_ms": ms, "status": info["status"], "energy": E, "residual": info["residual"],
+            "cycles": info["cycles"], "lanczos_steps": info["lanczos_steps"], "cg_steps": info["cg_steps"],
+            "us_per_apply_step": info["seconds"] / steps * 1e6, "hbm_GBs_algorithmic": gbs, "hbm_frac": gbs / hbm,
+            "excite_ms": ms_x, "norm2_c_psi": float((b.real * b.real).sum()),
+            "spectrum_ms": ms_s, "spectrum_status": sinfo["status"], "spectrum_iters": sinfo["iters"],
+            "spectrum_shift_iter_per_s": sinfo["shift_iters"] / (ms_s * 1e-3)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -428,7 +467,7 @@ def main():
     ap.add_argument("--compare", default="fp64,mixed", help="comma list of other precisions timed once beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--max-iter", type=int, default=0, help="cap on seed iterations (0 = to convergence)")
-    ap.add_argument("--legs", default="batch,multi,chain,adjoint,hubbard,density",
+    ap.add_argument("--legs", default="batch,multi,chain,adjoint,hubbard,density,ground",
                     help="comma list of the other workloads, each timed once beside the headline")
     args = ap.parse_args()
 
@@ -570,6 +609,8 @@ def main():
         legs["hubbard"] = leg_hubbard(scocg, dev, stream, hbm)
     if "density" in leg_names:
         legs["density"] = leg_density(scocg, dev, stream)
+    if "ground" in leg_names:
+        legs["ground"] = leg_ground(scocg, dev, stream, hbm)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

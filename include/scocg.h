@@ -308,6 +308,67 @@ int scocg_solve_csr_noalloc(int64_t n, int64_t nnz, const int32_t *rowptr, const
                             const int64_t *proj_idx, const void *proj_vec, int nproj, double tol,
                             int max_iter, scocg_c128 *G_out, scocg_info *info, void *cuda_stream);
 
+/*
+ * scocg_ground_state -- lowest eigenvalue E and unit eigenvector psi of the
+ * real symmetric H of a CSR or Hubbard handle, by the cycle of Sec. II.C: the
+ * Lanczos method (its basis loses orthogonality; it is not reorthogonalized),
+ * then the conjugate-gradient method used as inverse iteration, repeated until
+ * the residual norm is small enough.  One cycle:
+ *   m Lanczos steps from psi (fewer when beta_j vanishes), kept in device
+ *   memory as V[m][N]; (theta, s) = lowest eigenpair of the tridiagonal T;
+ *   psi = V s / ||V s||; E = psi^T H psi; res = ||H psi - E psi||_2;
+ *   done when res <= tol; else (not in the last cycle) CG on
+ *   (H - sigma) y = psi, sigma = E - res, from y = 0 for at most cg_steps
+ *   steps (ended earlier at a relative residual of 1e-10 or when
+ *   p^T (H - sigma) p <= 0), and psi = y / ||y|| (kept if y = 0).
+ * FP64 arithmetic regardless of the handle's precision option.
+ *   v0           device double [N], start vector (not zero; caller-owned)
+ *   psi          device double [N], written: the eigenvector (sign arbitrary)
+ *   m            Lanczos steps per cycle, 2..1024 (clamped to N); the basis
+ *                needs (m + 5) N doubles of device memory, allocated per call
+ *   cg_steps     CG steps per inverse iteration, >= 0 (0: restart from the
+ *                Ritz vector alone)
+ *   max_cycles   >= 1
+ *   tol          residual bound, >= 0
+ *   energy       host double, written: E = psi^T H psi of the returned psi
+ *   info         optional, written
+ * Returns SCOCG_OK, SCOCG_NOT_CONVERGED (psi, E and info->residual are those
+ * of the last cycle), SCOCG_ERR_BREAKDOWN (a non-finite E or residual),
+ * SCOCG_ERR_INVALID, SCOCG_ERR_OOM or SCOCG_ERR_CUDA.
+ */
+typedef struct {
+    int cycles;               /* Lanczos / inverse-iteration cycles run               */
+    long long lanczos_steps;  /* Lanczos steps over all cycles (one H apply each)     */
+    long long cg_steps;       /* CG steps over all inverse iterations (one apply each) */
+    double residual;          /* ||H psi - E psi||_2 of the returned psi              */
+    double seconds;           /* device time from the first to the last kernel        */
+    double bytes_per_step;    /* algorithmic bytes of one Lanczos step: H once in its
+                                 device layout plus 8 FP64 vector passes              */
+} scocg_ground_info;
+
+int scocg_ground_state(scocg_handle h, const double *v0, double *psi, int m, int cg_steps, int max_cycles,
+                       double tol, double *energy, scocg_ground_info *info);
+
+/*
+ * scocg_excite -- one-particle excitation vector between Hubbard sectors
+ * (Sec. IV.D: the ionization and affinity spectra are G(z) = b^T (z - H)^{-1} b
+ * for b = c_{i s}|psi_0> and b = c+_{i s}|psi_0>):
+ *   out = c_{site,spin} psi   (create = 0; to = sector with one spin-s electron less)
+ *   out = c+_{site,spin} psi  (create = 1; to = sector with one spin-s electron more)
+ * with modes ordered all up sites then all down sites (the Jordan-Wigner
+ * convention of the Hubbard handles' hopping signs).  from / to: Hubbard
+ * handles with the same L whose sectors differ by exactly that electron
+ * (else SCOCG_ERR_INVALID); spin 0 = up, 1 = down; 0 <= site < L.
+ *   psi   device double [N_from]
+ *   out   device complex128 [N_to], written (imaginary parts 0), ready as the
+ *         right-hand side of scocg_solve (spectrum: proj_vec = out, since
+ *         conj(b) = b)
+ * Runs on to's stream (after from's stream has finished, if they differ) and
+ * synchronises it.
+ */
+int scocg_excite(scocg_handle from, scocg_handle to, int site, int spin, int create, const double *psi,
+                 void *out);
+
 /* Free the handle and everything it owns (NULL is ignored). */
 void scocg_destroy(scocg_handle h);
 

@@ -18,6 +18,8 @@ scipy.sparse matrix).
 * ``fermion_op``            c_{i s} or c+_{i s} between particle-number sectors,
                             from the Jordan-Wigner definition acting on
                             occupation patterns (Sec. IV.D's model)
+* ``fermion_op_at``         selected entries of the same, one by one
+* ``hubbard_rows_apply``    (H psi) on selected rows, from the operators
 * ``excitation_green``      <b|(z - H)^{-1}|b> by dense solves (Eq. gf)
 * ``lehmann_green``         the same from the eigen-decomposition of H
 
@@ -29,7 +31,9 @@ shift is sigma = theta - ||r|| (theta the Rayleigh quotient, r = H psi -
 theta psi), which lies below the lowest eigenvalue once psi is close to
 the ground state, so that H - sigma is positive definite; the CG solve of
 (H - sigma) y = psi starts from y = 0 and stops after ``cg_steps`` steps, at
-a relative residual of 1e-10, or when p^T (H - sigma) p <= 0.
+a relative residual of 1e-10, or when p^T (H - sigma) p <= 0; the last
+cycle runs no inverse iteration, so that the returned vector is the one whose
+energy and residual are reported.
 """
 from __future__ import annotations
 
@@ -118,7 +122,7 @@ def lanczos_ground_state(H, v0, m=60, cg_steps=0, max_cycles=50, tol=1e-10):
         res = float(np.linalg.norm(Hpsi - E * psi))
         if res <= tol:
             return GroundState(E, psi, res, 0, nl, ncg, cycle)
-        if cg_steps > 0:
+        if cg_steps > 0 and cycle < max_cycles:
             y = _cg_inverse_step(H, psi, E - res, cg_steps)
             ncg += cg_steps
             ny = float(np.linalg.norm(y))
@@ -169,6 +173,80 @@ def fermion_op(L, n_up, n_dn, site, spin, create, psi):
     return out
 
 
+def _flip(occ, m, create):
+    """c_m (create=False) or c+_m on an occupation tuple: (sign, new tuple), or
+    None when the mode is already empty (full).  Sign (-1)^(occupied modes
+    before m), the Jordan-Wigner string."""
+    if occ[m] == (1 if create else 0):
+        return None
+    sign = -1.0 if sum(occ[:m]) % 2 else 1.0
+    new = list(occ)
+    new[m] ^= 1
+    return sign, tuple(new)
+
+
+def fermion_op_at(L, n_up, n_dn, site, spin, create, psi, targets):
+    """Entries ``targets`` of fermion_op(...): for each target basis state, the
+    source state is the target with the mode flipped back, and the entry is the
+    operator's sign on the source pattern times psi[source] (0 if the target
+    has the mode in the wrong state).  For checks at sizes where the whole
+    vector is out of reach."""
+    d = 1 if create else -1
+    tu, td = (n_up + d, n_dn) if spin == 0 else (n_up, n_dn + d)
+    ups, dns = _sector(L, n_up), _sector(L, n_dn)
+    tups, tdns = _sector(L, tu), _sector(L, td)
+    pos_u = {s: i for i, s in enumerate(ups)}
+    pos_d = {s: i for i, s in enumerate(dns)}
+    m = site + spin * L
+    out = np.zeros(len(targets), dtype=np.float64)
+    for k, t in enumerate(targets):
+        u, dd = tups[int(t) // len(tdns)], tdns[int(t) % len(tdns)]
+        occ = tuple([(u >> i) & 1 for i in range(L)] + [(dd >> i) & 1 for i in range(L)])
+        back = _flip(occ, m, not create)           # the source pattern
+        if back is None:
+            continue
+        src = back[1]
+        sign = _flip(src, m, create)[0]
+        nu = sum(src[i] << i for i in range(L))
+        nd = sum(src[L + i] << i for i in range(L))
+        out[k] = sign * psi[pos_u[nu] * len(dns) + pos_d[nd]]
+    return out
+
+
+def hubbard_rows_apply(L, n_up, n_dn, t, U, V, periodic, psi, rows):
+    """(H psi)[rows] for the extended Hubbard ring of Sec. IV.D,
+    H = -t sum_{<ij>,s} (c+_is c_js + h.c.) + U sum_i n_iu n_id + V sum_<ij> n_i n_j,
+    each row from the operators acting on that basis pattern (H is real
+    symmetric, so row s is H|s> read in the basis).  Bonds (i, i+1), and
+    (L-1, 0) on a ring of L >= 3."""
+    ups, dns = _sector(L, n_up), _sector(L, n_dn)
+    pos_u = {s: i for i, s in enumerate(ups)}
+    pos_d = {s: i for i, s in enumerate(dns)}
+    bonds = [(i, i + 1) for i in range(L - 1)] + ([(L - 1, 0)] if periodic and L >= 3 else [])
+    out = np.zeros(len(rows), dtype=np.float64)
+    for k, r in enumerate(rows):
+        u, dd = ups[int(r) // len(dns)], dns[int(r) % len(dns)]
+        occ = tuple([(u >> i) & 1 for i in range(L)] + [(dd >> i) & 1 for i in range(L)])
+        nsite = [occ[i] + occ[L + i] for i in range(L)]
+        acc = (U * sum(occ[i] * occ[L + i] for i in range(L)) + V * sum(nsite[i] * nsite[j] for i, j in bonds)) \
+            * psi[int(r)]
+        for i, j in bonds:
+            for sp in range(2):
+                for a, b in ((i + sp * L, j + sp * L), (j + sp * L, i + sp * L)):
+                    s1 = _flip(occ, b, False)              # c_b
+                    if s1 is None:
+                        continue
+                    s2 = _flip(s1[1], a, True)             # c+_a
+                    if s2 is None:
+                        continue
+                    o = s2[1]
+                    nu = sum(o[x] << x for x in range(L))
+                    nd = sum(o[L + x] << x for x in range(L))
+                    acc += -t * s1[0] * s2[0] * psi[pos_u[nu] * len(dns) + pos_d[nd]]
+        out[k] = acc
+    return out
+
+
 def excitation_green(H, b, shifts):
     """G(z_k) = b^T (z_k - H)^{-1} b by dense solves (Eq. gf with c = b real)."""
     H = np.asarray(H.todense() if hasattr(H, "todense") else H, dtype=np.float64)
@@ -209,5 +287,5 @@ def occupations(L, n_up, n_dn, psi):
     return out
 
 
-__all__ = ["lanczos_ground_state", "fermion_op", "excitation_green", "lehmann_green",
+__all__ = ["lanczos_ground_state", "fermion_op", "fermion_op_at", "hubbard_rows_apply", "excitation_green", "lehmann_green",
            "free_fermion_ground_energy", "occupations", "GroundState", "CG_RTOL"]

@@ -119,6 +119,9 @@ int default_seed(const scocg_c128* z, int K);
 // Hubbard (hubbard.cu)
 cudaError_t hubbard_apply(const Hubbard& hb, int prec, double2 z, const void* x, void* y, cudaStream_t st);
 int hubbard_max_ctas(const Hubbard& hb, int prec, int num_sms, size_t dyn_smem = 0);
+// real FP64 y = (H - sigma) x - beta x_prev with per-block partials of x^T y (ground state)
+cudaError_t hubbard_hx(const Hubbard& hb, const double* x, double* y, const double* xprev, const double* beta,
+                       double sigma, const int* skip, double* part, int grid, cudaStream_t st);
 template <typename R>
 cudaError_t hubbard_launch_solve(const SolveArgs<R>& a, const Hubbard& hb, int grid, cudaStream_t st);
 

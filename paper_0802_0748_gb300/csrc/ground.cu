@@ -1,0 +1,499 @@
+// Ground state of a real symmetric H by the Lanczos method followed by the
+// conjugate-gradient method used as inverse iteration, the two repeated until
+// the residual norm is small enough (Sec. II.C).  The vector it returns is the
+// starting point of the excitation spectra: c|psi_0> and c+|psi_0>
+// (scocg_excite, hubbard.cu) are right-hand sides of the shifted solve.
+//
+// One cycle:
+//   Lanczos, m steps from psi (no reorthogonalization):
+//     w = H v_j - beta_{j-1} v_{j-1};  alpha_j = v_j^T w;  w -= alpha_j v_j;
+//     beta_j = ||w||;  v_{j+1} = w / beta_j  (stop when beta_j vanishes)
+//   lowest eigenpair (theta, s) of T = tridiag(beta, alpha, beta): Sturm
+//     bisection, then inverse iteration with a pivoted tridiagonal LU
+//   psi = V s / ||V s||;  E = psi^T H psi;  res = ||H psi - E psi||
+//   stop if res <= tol; else CG on (H - sigma) y = psi, sigma = E - res
+//     (below the lowest eigenvalue once psi is close to it, so H - sigma is
+//     positive definite), y = 0 first, at most cg_steps steps, stopped at a
+//     relative residual of 1e-10 or when p^T (H - sigma) p <= 0; psi = y / ||y||.
+//
+// GPU layout: the Lanczos basis V[m][N] (FP64) stays in HBM during the cycle,
+// so the Ritz vector is one pass over it instead of a second Lanczos run; all
+// scalars stay on the device.  Each reduction is written as per-block partials
+// that every consuming block adds in the same order, and every flag a kernel
+// decides is stored per step, so no launch reads a value that it also writes
+// and the host synchronises once per cycle to read E and res.
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "api_internal.h"
+#include "common.cuh"
+#include "vector_ops.cuh"
+
+namespace scocg {
+namespace {
+
+constexpr double kCgRtol = 1e-10;
+constexpr int kMaxLanczos = 1024;
+
+// y = (H - sigma) x - beta x_prev on the int32 CSR with FP64 values, 8 lanes
+// per row (the 4 row groups of a warp take consecutive rows, so every lane of
+// a warp runs the same number of outer steps); partial of x^T y per block.
+__global__ void __launch_bounds__(kVecBlock) k_csr_hx(int64_t n, const int* rowptr, const int* col,
+                                                      const double* val, const double* x, double* y,
+                                                      const double* xprev, const double* beta, double sigma,
+                                                      const int* skip, double* part) {
+    if (skip && *skip) return;
+    const int lane = threadIdx.x & 31, sub = lane & 7;
+    const int64_t gw = ((blockIdx.x * (int64_t)kVecBlock + threadIdx.x) >> 5) * 4;   // first row group of the warp
+    const int64_t ng = ((int64_t)gridDim.x * kVecBlock) >> 3;
+    const double bp = (xprev && beta) ? *beta : 0.0;
+    double acc = 0.0;
+    for (int64_t base = gw; base < n; base += ng) {
+        const int64_t i = base + (lane >> 3);
+        double s = 0.0;
+        if (i < n)
+            for (int k = rowptr[i] + sub; k < rowptr[i + 1]; k += 8) s = fma(val[k], x[col[k]], s);
+        s += __shfl_xor_sync(0xffffffffu, s, 4);
+        s += __shfl_xor_sync(0xffffffffu, s, 2);
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+        if (i < n && sub == 0) {
+            const double xi = x[i];
+            double yi = fma(-sigma, xi, s);
+            if (xprev) yi = fma(-bp, xprev[i], yi);
+            y[i] = yi;
+            acc = fma(xi, yi, acc);
+        }
+    }
+    block_partial(acc, part);
+}
+
+__device__ __forceinline__ bool lead() { return blockIdx.x == 0 && threadIdx.x == 0; }
+
+#define GRID_STRIDE(i, n) \
+    for (int64_t i = blockIdx.x * (int64_t)kVecBlock + threadIdx.x; i < (n); i += (int64_t)gridDim.x * kVecBlock)
+
+// partial of x^T x
+__global__ void __launch_bounds__(kVecBlock) k_norm_part(int64_t n, const double* x, double* part) {
+    double acc = 0.0;
+    GRID_STRIDE(i, n) { const double v = x[i]; acc = fma(v, v, acc); }
+    block_partial(acc, part);
+}
+
+// dst = src / sqrt(sum of the partials); dst left as it is when that sum is
+// zero or not finite (*ok = 0, written by the lead thread)
+__global__ void __launch_bounds__(kVecBlock) k_scale_to(int64_t n, const double* src, double* dst,
+                                                        const double* part, int G, int* ok) {
+    const double s = sum_partials(part, G);
+    const bool good = s > 0.0 && isfinite(s);
+    if (lead() && ok) *ok = good;
+    if (!good) return;
+    const double inv = 1.0 / sqrt(s);
+    GRID_STRIDE(i, n) dst[i] = src[i] * inv;
+}
+
+// alpha_j = sum(part); w -= alpha_j v_j; partial of w^T w
+__global__ void __launch_bounds__(kVecBlock) k_lz_ortho(int64_t n, int j, const double* v, double* w,
+                                                        const double* part, int G, const int* stop, double* alpha,
+                                                        double* part2) {
+    if (stop[j]) return;
+    const double a = sum_partials(part, G);
+    if (lead()) alpha[j] = a;
+    double acc = 0.0;
+    GRID_STRIDE(i, n) {
+        const double wi = fma(-a, v[i], w[i]);
+        w[i] = wi;
+        acc = fma(wi, wi, acc);
+    }
+    block_partial(acc, part2);
+}
+
+// beta_j = sqrt(sum(part2)); the recursion ends after step j when j + 1 = m or
+// beta_j <= 1e-12 * max_i (|alpha_i| + beta_i + beta_{i-1}) (an invariant
+// subspace, or a non-finite value); else v_{j+1} = w / beta_j.
+__global__ void __launch_bounds__(kVecBlock) k_lz_next(int64_t n, int j, int m, const double* w, double* vnext,
+                                                       const double* part2, int G, const double* alpha, double* beta,
+                                                       double* tnorm, int* stop, int* kdim) {
+    if (stop[j]) {
+        if (lead()) stop[j + 1] = 1;
+        return;
+    }
+    const double b = sqrt(sum_partials(part2, G));
+    const double tn = fmax(j ? tnorm[j - 1] : 0.0, fabs(alpha[j]) + b + (j ? beta[j - 1] : 0.0));
+    const bool end = (j + 1 == m) || !(b > 1e-12 * tn);
+    if (lead()) {
+        beta[j] = b;
+        tnorm[j] = tn;
+        stop[j + 1] = end;
+        if (end) *kdim = j + 1;
+    }
+    if (end) return;
+    const double inv = 1.0 / b;
+    GRID_STRIDE(i, n) vnext[i] = w[i] * inv;
+}
+
+// Lowest eigenpair of the k x k tridiagonal T (alpha on the diagonal, beta
+// off it), one warp: multisection on the Sturm count (negative pivots of the
+// LDL^T factorisation of T - x) inside the Gershgorin interval, 32 points per
+// round, each lane counting at one point; then, in lane 0, three steps of
+// inverse iteration with T - theta factorised by Gaussian elimination with
+// partial pivoting (U with two superdiagonals).
+__global__ void k_tri_lowest(const int* kdim, const double* alpha, const double* beta, double* s, double* work,
+                             double* theta_out) {
+    if (blockIdx.x != 0) return;
+    const int lane = threadIdx.x & 31;
+    const int k = *kdim;
+    const double* a = alpha;
+    const double* b = beta;
+    double lo = INFINITY, hi = -INFINITY;
+    for (int i = 0; i < k; ++i) {
+        const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < k ? fabs(b[i]) : 0.0);
+        lo = fmin(lo, a[i] - r);
+        hi = fmax(hi, a[i] + r);
+    }
+    const double scale = fmax(fmax(fabs(lo), fabs(hi)), 1e-300);
+    const double eps = 2.220446049250313e-16;
+    const double pivmin = eps * scale * 1e-3 + 1e-300;
+    lo -= 2.0 * eps * scale + pivmin;
+    hi += 2.0 * eps * scale + pivmin;
+    auto count_below = [&](double x) {
+        int c = 0;
+        double d = 1.0;
+        for (int i = 0; i < k; ++i) {
+            d = (a[i] - x) - (i > 0 ? b[i - 1] * (b[i - 1] / d) : 0.0);
+            if (fabs(d) < pivmin) d = -pivmin;
+            if (d < 0.0) ++c;
+        }
+        return c;
+    };
+    // invariant: no eigenvalue below lo, at least one below hi (the same on every lane)
+    for (int it = 0; it < 64 && hi - lo > 2.0 * eps * fmax(fabs(lo), fabs(hi)) + pivmin; ++it) {
+        const double x = lo + (hi - lo) * ((double)(lane + 1) / 33.0);
+        const unsigned above = __ballot_sync(0xffffffffu, count_below(x) >= 1);
+        const int f = above ? __ffs(above) - 1 : 32;    // first point with an eigenvalue below it
+        const double xf = __shfl_sync(0xffffffffu, x, f < 32 ? f : 31);
+        const double xp = __shfl_sync(0xffffffffu, x, f > 0 ? f - 1 : 0);
+        if (f == 32) lo = xf;
+        else { hi = xf; if (f > 0) lo = xp; }
+    }
+    if (lane != 0) return;
+    const double th = 0.5 * (lo + hi);
+    *theta_out = th;
+    // LU of T - th with row interchanges: U0 diagonal, U1, U2 superdiagonals,
+    // l multipliers, sw = 1 where rows i and i + 1 were exchanged
+    double* U0 = work;
+    double* U1 = work + k;
+    double* U2 = work + 2 * k;
+    double* l = work + 3 * k;
+    double* sw = work + 4 * k;
+    const double tiny = eps * scale + 1e-280;
+    double r0 = a[0] - th, r1 = k > 1 ? b[0] : 0.0, r2 = 0.0;
+    for (int i = 0; i + 1 < k; ++i) {
+        const double c = b[i];                       // row i+1: (b_i, a_{i+1} - th, b_{i+1})
+        const double d1 = a[i + 1] - th, d2 = i + 2 < k ? b[i + 1] : 0.0;
+        if (fabs(r0) >= fabs(c)) {
+            const double m = r0 != 0.0 ? c / r0 : 0.0;
+            U0[i] = r0; U1[i] = r1; U2[i] = r2; l[i] = m; sw[i] = 0.0;
+            r0 = d1 - m * r1; r1 = d2 - m * r2; r2 = 0.0;
+        } else {
+            const double m = r0 / c;
+            U0[i] = c; U1[i] = d1; U2[i] = d2; l[i] = m; sw[i] = 1.0;
+            const double n0 = r1 - m * d1, n1 = r2 - m * d2;
+            r0 = n0; r1 = n1; r2 = 0.0;
+        }
+        if (fabs(U0[i]) < tiny) U0[i] = U0[i] < 0.0 ? -tiny : tiny;
+    }
+    U0[k - 1] = fabs(r0) < tiny ? (r0 < 0.0 ? -tiny : tiny) : r0;
+    for (int i = 0; i < k; ++i) s[i] = 1.0 + (double)((i * 7919) % 13) / 13.0;
+    for (int rep = 0; rep < 3; ++rep) {
+        for (int i = 0; i + 1 < k; ++i) {
+            if (sw[i] != 0.0) { const double t = s[i]; s[i] = s[i + 1]; s[i + 1] = t; }
+            s[i + 1] -= l[i] * s[i];
+        }
+        for (int i = k - 1; i >= 0; --i) {
+            double v = s[i];
+            if (i + 1 < k) v -= U1[i] * s[i + 1];
+            if (i + 2 < k) v -= U2[i] * s[i + 2];
+            s[i] = v / U0[i];
+        }
+        double mx = 0.0;
+        for (int i = 0; i < k; ++i) mx = fmax(mx, fabs(s[i]));
+        if (!(mx > 0.0) || !isfinite(mx)) break;
+        double nr = 0.0;
+        for (int i = 0; i < k; ++i) { s[i] /= mx; nr += s[i] * s[i]; }
+        nr = sqrt(nr);
+        for (int i = 0; i < k; ++i) s[i] /= nr;
+    }
+}
+
+// psi = sum_{j < k} s_j v_j; partial of psi^T psi
+__global__ void __launch_bounds__(kVecBlock) k_ritz(int64_t n, const int* kdim, const double* s, const double* V,
+                                                    double* psi, double* part) {
+    __shared__ double s_s[kMaxLanczos];
+    const int k = *kdim;
+    for (int j = threadIdx.x; j < k; j += kVecBlock) s_s[j] = s[j];
+    __syncthreads();
+    double acc = 0.0;
+    GRID_STRIDE(i, n) {
+        double v = 0.0;
+        for (int j = 0; j < k; ++j) v = fma(s_s[j], V[(size_t)j * n + i], v);
+        psi[i] = v;
+        acc = fma(v, v, acc);
+    }
+    block_partial(acc, part);
+}
+
+// E = sum(part) (= psi^T H psi with h = H psi); partial of ||h - E psi||^2
+__global__ void __launch_bounds__(kVecBlock) k_resid(int64_t n, const double* psi, const double* h,
+                                                     const double* part, int G, double* part2, double* E_out) {
+    const double E = sum_partials(part, G);
+    if (lead()) *E_out = E;
+    double acc = 0.0;
+    GRID_STRIDE(i, n) {
+        const double r = fma(-E, psi[i], h[i]);
+        acc = fma(r, r, acc);
+    }
+    block_partial(acc, part2);
+}
+
+// *out = sqrt(sum(part)) (one block) or the plain sum
+__global__ void __launch_bounds__(kVecBlock) k_sum_store(const double* part, int G, double* out, int take_sqrt) {
+    const double s = sum_partials(part, G);
+    if (threadIdx.x == 0) *out = take_sqrt ? sqrt(s) : s;
+}
+
+// y = 0; r = p = psi; partial of r^T r
+__global__ void __launch_bounds__(kVecBlock) k_cg_init(int64_t n, const double* psi, double* y, double* r, double* p,
+                                                       double* part) {
+    double acc = 0.0;
+    GRID_STRIDE(i, n) {
+        const double v = psi[i];
+        y[i] = 0.0; r[i] = v; p[i] = v;
+        acc = fma(v, v, acc);
+    }
+    block_partial(acc, part);
+}
+
+// step s: pq = p^T q (q = (H - sigma) p); breakdown when pq <= 0 or not finite;
+// else gamma = rr_s / pq, y += gamma p, r -= gamma q, partial of r^T r
+__global__ void __launch_bounds__(kVecBlock) k_cg_xr(int64_t n, int s, double* y, double* r, const double* p,
+                                                     const double* q, const double* part, int G, const double* rr,
+                                                     const int* cgstop, int* cgbrk, double* part2) {
+    if (cgstop[s]) return;
+    const double pq = sum_partials(part, G);
+    const bool brk = !(pq > 0.0) || !isfinite(pq);
+    if (lead()) cgbrk[s] = brk;
+    if (brk) return;
+    const double g = rr[s] / pq;
+    double acc = 0.0;
+    GRID_STRIDE(i, n) {
+        y[i] = fma(g, p[i], y[i]);
+        const double ri = fma(-g, q[i], r[i]);
+        r[i] = ri;
+        acc = fma(ri, ri, acc);
+    }
+    block_partial(acc, part2);
+}
+
+// rr_{s+1} = sum(part2); p = r + (rr_{s+1} / rr_s) p; the solve ends after
+// step s on a breakdown or when rr_{s+1} <= (1e-10)^2 rr_0
+__global__ void __launch_bounds__(kVecBlock) k_cg_p(int64_t n, int s, const double* r, double* p, const double* part2,
+                                                    int G, double* rr, int* cgstop, const int* cgbrk) {
+    if (cgstop[s] || cgbrk[s]) {
+        if (lead()) cgstop[s + 1] = 1;
+        return;
+    }
+    const double rn = sum_partials(part2, G);
+    if (lead()) {
+        rr[s + 1] = rn;
+        cgstop[s + 1] = !(rn > kCgRtol * kCgRtol * rr[0]);
+    }
+    const double be = rn / rr[s];
+    GRID_STRIDE(i, n) p[i] = fma(be, p[i], r[i]);
+}
+
+#undef GRID_STRIDE
+
+// Device scalars of one call, carved from one allocation.
+struct GroundScalars {
+    double* alpha;    // [m]
+    double* beta;     // [m]
+    double* tnorm;    // [m]
+    double* s;        // [m]  eigenvector of T
+    double* work;     // [5 m]
+    double* scal;     // [4]: theta of T, E, res, spare
+    double* part;     // [G]
+    double* part2;    // [G]
+    double* rr;       // [cg + 1]
+    int* stop;        // [m + 1]
+    int* kdim;        // [1]
+    int* ok;          // [1]
+    int* cgstop;      // [cg + 1]
+    int* cgbrk;       // [cg]
+};
+
+}  // namespace
+
+// Real FP64 operator of the handle: y = (H - sigma) x - beta x_prev, partial of x^T y.
+static cudaError_t hx(scocg_ctx* h, const double* x, double* y, const double* xprev, const double* beta,
+                      double sigma, const int* skip, double* part, int G) {
+    if (h->kind == HandleKind::kHubbard) return hubbard_hx(h->hub, x, y, xprev, beta, sigma, skip, part, G, h->stream);
+    k_csr_hx<<<G, kVecBlock, 0, h->stream>>>(h->n, h->d_rowptr, h->d_col, h->d_val64, x, y, xprev, beta, sigma, skip,
+                                              part);
+    return cudaGetLastError();
+}
+
+// Algorithmic bytes of one Lanczos step: H once (CSR: int32 index + FP64 value
+// per entry and the row pointers; Hubbard: the hop tables) plus the vector
+// passes: apply (read v_j, v_{j-1}, write w, gather v_j), ortho (read v_j, w,
+// write w), next (read w, write v_{j+1}) = 8 passes of 8 bytes.
+static double lanczos_step_bytes(const scocg_ctx* h) {
+    const double hb = h->kind == HandleKind::kHubbard ? h->hub.table_bytes
+                                                      : 12.0 * (double)h->nnz + 4.0 * (double)(h->n + 1);
+    return hb + 8.0 * 8.0 * (double)h->n;
+}
+
+}  // namespace scocg
+
+using namespace scocg;
+
+extern "C" int scocg_ground_state(scocg_handle h, const double* v0, double* psi_out, int m, int cg_steps,
+                                  int max_cycles, double tol, double* energy, scocg_ground_info* info) {
+    if (!h || !v0 || !psi_out || !energy || m < 2 || m > kMaxLanczos || cg_steps < 0 || cg_steps > 1000000 ||
+        max_cycles < 1 || !(tol >= 0.0) || !std::isfinite(tol))
+        return SCOCG_ERR_INVALID;
+    if (h->kind == HandleKind::kCsr && !h->d_val64) return SCOCG_ERR_INVALID;
+    const int64_t n = h->n;
+    if (n < 1) return SCOCG_ERR_INVALID;
+    const int G = (int)std::max<int64_t>(1, std::min<int64_t>((n + kVecBlock - 1) / kVecBlock, 8LL * h->num_sms));
+    const int mm = (int)std::min<int64_t>(m, n);   // at most n Lanczos vectors are independent
+    // device memory: V[mm][n], w, psi, y, r, p and the scalars
+    Carver cv{nullptr, 0};
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+            void* base = nullptr;
+            if (cudaMalloc(&base, cv.off) != cudaSuccess) { cudaGetLastError(); return SCOCG_ERR_OOM; }
+            cv = Carver{static_cast<char*>(base), 0};
+        }
+        cv.take(sizeof(double) * (size_t)mm * n);
+        for (int v = 0; v < 5; ++v) cv.take(sizeof(double) * n);
+        cv.take(sizeof(double) * (9 * (size_t)mm + 4 + 2 * (size_t)G + cg_steps + 1));
+        cv.take(sizeof(int) * ((size_t)mm + 3 + 2 * (size_t)cg_steps + 1));
+    }
+    char* base = cv.base;
+    cv.off = 0;
+    double* V = (double*)cv.take(sizeof(double) * (size_t)mm * n);
+    double* w = (double*)cv.take(sizeof(double) * n);
+    double* psi = (double*)cv.take(sizeof(double) * n);
+    double* y = (double*)cv.take(sizeof(double) * n);
+    double* r = (double*)cv.take(sizeof(double) * n);
+    double* p = (double*)cv.take(sizeof(double) * n);
+    GroundScalars S;
+    {
+        double* d = (double*)cv.take(sizeof(double) * (9 * (size_t)mm + 4 + 2 * (size_t)G + cg_steps + 1));
+        S.alpha = d; S.beta = d + mm; S.tnorm = d + 2 * mm; S.s = d + 3 * mm; S.work = d + 4 * mm;
+        S.scal = d + 9 * mm; S.part = S.scal + 4; S.part2 = S.part + G; S.rr = S.part2 + G;
+        int* q = (int*)cv.take(sizeof(int) * ((size_t)mm + 3 + 2 * (size_t)cg_steps + 1));
+        S.stop = q; S.kdim = q + mm + 1; S.ok = S.kdim + 1; S.cgstop = S.ok + 1; S.cgbrk = S.cgstop + cg_steps + 1;
+    }
+    cudaStream_t st = h->stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(psi, v0, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    int status = SCOCG_NOT_CONVERGED;
+    long long lanczos_total = 0, cg_total = 0;
+    int cycles = 0;
+    double E = NAN, res = NAN;
+    std::vector<int> host_stop(cg_steps + 1);
+    for (int cyc = 0; cyc < max_cycles && e == cudaSuccess; ++cyc) {
+        ++cycles;
+        // v_0 = psi / ||psi||
+        k_norm_part<<<G, kVecBlock, 0, st>>>(n, psi, S.part);
+        k_scale_to<<<G, kVecBlock, 0, st>>>(n, psi, V, S.part, G, S.ok);
+        if (cyc == 0) {   // a zero or non-finite start vector is an invalid argument
+            int ok = 0;
+            e = cudaMemcpyAsync(&ok, S.ok, sizeof(int), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e == cudaSuccess && !ok) { status = SCOCG_ERR_INVALID; break; }
+            if (e != cudaSuccess) break;
+        }
+        e = cudaMemsetAsync(S.stop, 0, sizeof(int) * (mm + 1), st);
+        const int mm_v = mm;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(S.kdim, &mm_v, sizeof(int), cudaMemcpyHostToDevice, st);
+        for (int j = 0; j < mm && e == cudaSuccess; ++j) {
+            const double* vj = V + (size_t)j * n;
+            e = hx(h, vj, w, j ? vj - n : nullptr, j ? S.beta + j - 1 : nullptr, 0.0, S.stop + j, S.part, G);
+            if (e != cudaSuccess) break;
+            k_lz_ortho<<<G, kVecBlock, 0, st>>>(n, j, vj, w, S.part, G, S.stop, S.alpha, S.part2);
+            k_lz_next<<<G, kVecBlock, 0, st>>>(n, j, mm, w, j + 1 < mm ? V + (size_t)(j + 1) * n : w, S.part2, G,
+                                               S.alpha, S.beta, S.tnorm, S.stop, S.kdim);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) break;
+        k_tri_lowest<<<1, 32, 0, st>>>(S.kdim, S.alpha, S.beta, S.s, S.work, S.scal);
+        k_ritz<<<G, kVecBlock, 0, st>>>(n, S.kdim, S.s, V, w, S.part);
+        k_scale_to<<<G, kVecBlock, 0, st>>>(n, w, psi, S.part, G, S.ok);
+        e = hx(h, psi, w, nullptr, nullptr, 0.0, nullptr, S.part, G);
+        if (e != cudaSuccess) break;
+        k_resid<<<G, kVecBlock, 0, st>>>(n, psi, w, S.part, G, S.part2, S.scal + 1);
+        k_sum_store<<<1, kVecBlock, 0, st>>>(S.part2, G, S.scal + 2, 1);
+        double sc[3];
+        int kd = 0;
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(sc, S.scal, sizeof(sc), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&kd, S.kdim, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) break;
+        lanczos_total += kd;
+        E = sc[1];
+        res = sc[2];
+        if (!std::isfinite(E) || !std::isfinite(res)) { status = SCOCG_ERR_BREAKDOWN; break; }
+        if (res <= tol) { status = SCOCG_OK; break; }
+        if (cg_steps == 0 || cyc + 1 == max_cycles) continue;
+        // inverse iteration: CG on (H - sigma) y = psi
+        const double sigma = E - res;
+        k_cg_init<<<G, kVecBlock, 0, st>>>(n, psi, y, r, p, S.part);
+        k_sum_store<<<1, kVecBlock, 0, st>>>(S.part, G, S.rr, 0);
+        e = cudaMemsetAsync(S.cgstop, 0, sizeof(int) * (2 * (size_t)cg_steps + 1), st);
+        for (int s = 0; s < cg_steps && e == cudaSuccess; ++s) {
+            e = hx(h, p, w, nullptr, nullptr, sigma, S.cgstop + s, S.part, G);
+            if (e != cudaSuccess) break;
+            k_cg_xr<<<G, kVecBlock, 0, st>>>(n, s, y, r, p, w, S.part, G, S.rr, S.cgstop, S.cgbrk, S.part2);
+            k_cg_p<<<G, kVecBlock, 0, st>>>(n, s, r, p, S.part2, G, S.rr, S.cgstop, S.cgbrk);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) break;
+        k_norm_part<<<G, kVecBlock, 0, st>>>(n, y, S.part);
+        k_scale_to<<<G, kVecBlock, 0, st>>>(n, y, psi, S.part, G, S.ok);   // psi kept if y = 0
+        e = cudaMemcpyAsync(host_stop.data(), S.cgstop, sizeof(int) * (cg_steps + 1), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) {
+            int taken = 0;
+            while (taken < cg_steps && !host_stop[taken]) ++taken;
+            cg_total += taken;
+        }
+    }
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(psi_out, psi, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(base);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (status == SCOCG_ERR_INVALID) return status;
+    *energy = E;
+    if (info) {
+        info->cycles = cycles;
+        info->lanczos_steps = lanczos_total;
+        info->cg_steps = cg_total;
+        info->residual = res;
+        info->seconds = ms * 1e-3;
+        info->bytes_per_step = lanczos_step_bytes(h);
+    }
+    return status;
+}

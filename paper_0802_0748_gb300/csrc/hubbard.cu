@@ -22,6 +22,7 @@
 
 #include "api_internal.h"
 #include "solver_kernel.cuh"
+#include "vector_ops.cuh"
 
 namespace scocg {
 
@@ -262,6 +263,84 @@ cudaError_t hubbard_apply(const Hubbard& hb, int prec, double2 z, const void* x,
     return cudaGetLastError();
 }
 
+// Real FP64 operator of the ground-state iteration: y = (H - sigma) x - beta x_prev
+// (x_prev and beta optional), same unit order as the solver's apply, and the
+// block's partial of x^T y in part[blockIdx.x].  A launch whose *skip is set
+// does nothing.
+__global__ void __launch_bounds__(kVecBlock) k_hub_hx(ApplyHubbard<double> ap, int64_t nunits, const double* x,
+                                                      double* y, const double* xprev, const double* beta,
+                                                      double sigma, const int* skip, double* part) {
+    if (skip && *skip) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)kVecBlock + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * kVecBlock) >> 5;
+    const double bp = (xprev && beta) ? *beta : 0.0;
+    double acc = 0.0;
+    for (int64_t unit = w0; unit < nunits; unit += nw) {
+        const int u = (int)(unit % ap.D_up);
+        const int d = (int)(unit / ap.D_up) * 32 + lane;
+        if (d >= ap.D_dn) continue;
+        const int64_t row = (int64_t)u * ap.D_dn + d;
+        const uint32_t su = ap.st_up[u], sd = ap.st_dn[d];
+        const uint32_t pu = ap.partner(su), pd = ap.partner(sd);
+        const int cu = __popc(su & sd);
+        const int cv = __popc(su & pu) + __popc(sd & pd) + __popc(su & pd) + __popc(sd & pu);
+        const double xi = x[row];
+        double hop = 0.0;   // sum of sign * x over the hops; H's hopping part is -t times it
+        const double* xrow = x + (size_t)u * ap.D_dn;
+        for (int j = 0; j < ap.S; ++j) {
+            const int e = ap.hop_dn[(size_t)d * ap.S + j];
+            if (e < 0) break;
+            const double xv = xrow[e >> 1];
+            hop += (e & 1) ? -xv : xv;
+        }
+        for (int j = 0; j < ap.S; ++j) {
+            const int e = ap.hop_up[(size_t)u * ap.S + j];
+            if (e < 0) break;
+            const double xv = x[(size_t)(e >> 1) * ap.D_dn + d];
+            hop += (e & 1) ? -xv : xv;
+        }
+        const double diag = ap.U * (double)cu + ap.V * (double)cv;
+        double yi = fma(diag - sigma, xi, -ap.t * hop);
+        if (xprev) yi = fma(-bp, xprev[row], yi);
+        y[row] = yi;
+        acc = fma(xi, yi, acc);
+    }
+    block_partial(acc, part);
+}
+
+cudaError_t hubbard_hx(const Hubbard& hb, const double* x, double* y, const double* xprev, const double* beta,
+                       double sigma, const int* skip, double* part, int grid, cudaStream_t st) {
+    k_hub_hx<<<grid, kVecBlock, 0, st>>>(make_apply<double>(hb), hb.nunits, x, y, xprev, beta, sigma, skip, part);
+    return cudaGetLastError();
+}
+
+// c_{site,spin} or c+_{site,spin} from the sector of `src` into the sector of
+// this handle: one thread per target basis state.  The source state is the
+// target with mode (site, spin) flipped back; with modes ordered all up sites
+// then all down sites, the Jordan-Wigner sign is (-1)^(occupied modes before
+// the flipped one) in the source state.  Output complex128 with zero imaginary
+// part (a right-hand side of the shifted solve).
+__global__ void k_excite(int site, int spin, int create, int n_up_src, int D_dn_src, const uint32_t* st_up_t,
+                         const uint32_t* st_dn_t, int D_up_t, int D_dn_t, const double* psi, double2* out) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)D_up_t * D_dn_t) return;
+    const int ut = (int)(t / D_dn_t), dt = (int)(t % D_dn_t);
+    uint32_t su = st_up_t[ut], sd = st_dn_t[dt];
+    const uint32_t bit = 1u << site;
+    const uint32_t s_t = spin ? sd : su;
+    double v = 0.0;
+    if (((s_t & bit) != 0u) == (create != 0)) {
+        if (spin) sd ^= bit; else su ^= bit;
+        const uint32_t s_src = spin ? sd : su;
+        const int before = __popc(s_src & (bit - 1u)) + (spin ? n_up_src : 0);
+        const int64_t src = spin ? (int64_t)ut * D_dn_src + rank_of(sd) : rank_of(su) * D_dn_src + dt;
+        const double p = psi[src];
+        v = (before & 1) ? -p : p;
+    }
+    out[t] = make_double2(v, 0.0);
+}
+
 }  // namespace scocg
 
 using namespace scocg;
@@ -321,5 +400,30 @@ extern "C" int scocg_hubbard_tables(scocg_handle h, int spin, int32_t* dim, uint
         e = cudaMemcpy(hop_target, hb.d_hop_target + spin * tab, sizeof(int32_t) * D * S, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && hop_sign)
         e = cudaMemcpy(hop_sign, hb.d_hop_sign + spin * tab, sizeof(int8_t) * D * S, cudaMemcpyDeviceToHost);
+    return cuda_status(e);
+}
+
+extern "C" int scocg_excite(scocg_handle from, scocg_handle to, int site, int spin, int create, const double* psi,
+                            void* out) {
+    if (!from || !to || !psi || !out || from->kind != HandleKind::kHubbard || to->kind != HandleKind::kHubbard)
+        return SCOCG_ERR_INVALID;
+    const Hubbard& a = from->hub;
+    const Hubbard& b = to->hub;
+    const int d = create ? 1 : -1;
+    if (a.L != b.L || site < 0 || site >= a.L || (spin != 0 && spin != 1) || (create != 0 && create != 1))
+        return SCOCG_ERR_INVALID;
+    const int tu = a.n_up + (spin == 0 ? d : 0), td = a.n_dn + (spin == 1 ? d : 0);
+    if (b.n_up != tu || b.n_dn != td) return SCOCG_ERR_INVALID;
+    const int64_t n_t = (int64_t)b.D_up * b.D_dn;
+    if (n_t == 0) return SCOCG_OK;
+    if (from->stream != to->stream) {   // psi may still be written on the source handle's stream
+        cudaError_t e = cudaStreamSynchronize(from->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    k_excite<<<(unsigned)((n_t + 255) / 256), 256, 0, to->stream>>>(site, spin, create, a.n_up, a.D_dn,
+                                                                     b.d_states, b.d_states + b.Dmax, b.D_up, b.D_dn,
+                                                                     psi, (double2*)out);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(to->stream);
     return cuda_status(e);
 }

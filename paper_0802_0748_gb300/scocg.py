@@ -28,7 +28,7 @@ EXPORTED = [
     "scocg_create_csr", "scocg_create_hubbard", "scocg_dim", "scocg_set_opts", "scocg_apply",
     "scocg_solve", "scocg_solve_full", "scocg_grad", "scocg_destroy", "scocg_strerror",
     "scocg_hubbard_tables", "scocg_solve_csr_noalloc", "scocg_solve_multi", "scocg_multi_release",
-    "scocg_density",
+    "scocg_density", "scocg_ground_state", "scocg_excite",
 ]
 
 
@@ -47,6 +47,11 @@ class Opts(ctypes.Structure):
                 ("seed", ctypes.c_int), ("no_switch", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("timeout_ms", ctypes.c_double), ("layout", ctypes.c_int), ("grid", ctypes.c_int),
                 ("debug_inject", ctypes.c_int), ("rhs_tile", ctypes.c_int)]
+
+
+class GroundInfo(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("lanczos_steps", ctypes.c_longlong), ("cg_steps", ctypes.c_longlong),
+                ("residual", ctypes.c_double), ("seconds", ctypes.c_double), ("bytes_per_step", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -96,6 +101,8 @@ def lib() -> ctypes.CDLL:
         L.scocg_solve_full.argtypes = [P, P, I, P, D, P, ctypes.POINTER(Info)]
         L.scocg_grad.argtypes = [P, P, I, P, I, P, P, I, D, P, P, ctypes.POINTER(Info)]
         L.scocg_density.argtypes = [P, D, D, D, D, D, I, P, I, P, P, I, D, P, ctypes.POINTER(Info)]
+        L.scocg_ground_state.argtypes = [P, P, P, I, I, I, D, ctypes.POINTER(D), ctypes.POINTER(GroundInfo)]
+        L.scocg_excite.argtypes = [P, P, I, I, I, P, P]
         L.scocg_destroy.argtypes = [P]
         L.scocg_destroy.restype = None
         L.scocg_strerror.argtypes = [I]
@@ -191,6 +198,7 @@ def scocg_create_hubbard(L, n_up, n_dn, t, U, V, periodic=True, opts: SolveOptio
     _check(code, "scocg_create_hubbard")
     h = Handle(out, stream)
     h.L = L
+    h.sector = (int(n_up), int(n_dn))
     return h
 
 
@@ -353,6 +361,41 @@ def scocg_destroy(h: Handle) -> None:
 
 def scocg_strerror(code: int) -> str:
     return strerror(code)
+
+
+def scocg_ground_state(h: Handle, v0, m: int = 60, cg_steps: int = 0, max_cycles: int = 50, tol: float = 1e-10):
+    """scocg_ground_state: returns (E, psi CUDA float64 [N], info dict).
+
+    v0: CUDA float64 [N] start vector.  Lanczos / CG-inverse-iteration cycles
+    (Sec. II.C) until ||H psi - E psi|| <= tol."""
+    import torch
+    if v0.dtype != torch.float64 or not v0.is_cuda:
+        raise TypeError("v0 must be a CUDA float64 tensor")
+    v0 = v0.reshape(-1).contiguous()
+    psi = torch.empty_like(v0)
+    E = ctypes.c_double()
+    info = GroundInfo()
+    code = lib().scocg_ground_state(h.ptr, _dev(v0), _dev(psi), int(m), int(cg_steps), int(max_cycles), float(tol),
+                                    ctypes.byref(E), ctypes.byref(info))
+    _check(code, "scocg_ground_state")
+    return E.value, psi, {"status": code, "cycles": info.cycles, "lanczos_steps": int(info.lanczos_steps),
+                          "cg_steps": int(info.cg_steps), "residual": info.residual, "seconds": info.seconds,
+                          "bytes_per_step": info.bytes_per_step}
+
+
+def scocg_excite(h_from: Handle, h_to: Handle, site: int, spin: int, create: bool, psi):
+    """scocg_excite: c_{site,spin} psi (create=False) or c+_{site,spin} psi as a
+    CUDA complex128 vector of h_to's sector."""
+    import torch
+    if psi.dtype != torch.float64 or not psi.is_cuda:
+        raise TypeError("psi must be a CUDA float64 tensor")
+    n = ctypes.c_int64()
+    _check(lib().scocg_dim(h_to.ptr, ctypes.byref(n)), "scocg_dim")
+    out = torch.empty(n.value, dtype=torch.complex128, device=psi.device)
+    psi = psi.reshape(-1).contiguous()
+    _check(lib().scocg_excite(h_from.ptr, h_to.ptr, int(site), int(spin), int(bool(create)), _dev(psi), _dev(out)),
+           "scocg_excite")
+    return out
 
 
 def scocg_hubbard_tables(h: Handle, spin: int):

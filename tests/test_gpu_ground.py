@@ -1,0 +1,225 @@
+"""Ground state by Lanczos + CG inverse iteration (Sec. II.C) and the
+one-particle excitation vectors c|psi_0>, c+|psi_0> (Sec. IV.D) through the C
+ABI, against the oracle: the dense eigenpair (the definition), closed forms,
+the Jordan-Wigner operators bit for bit, the ionization spectrum end to end,
+and at the 14-site size sampled rows of H psi - E psi and sampled entries of
+c psi computed one by one.
+
+The eigenvector is unique up to sign (each case has a gap checked first), so
+it is compared through |<psi, u_0>|; G = b^T (z - H)^{-1} b is quadratic in b
+and does not depend on that sign.
+"""
+import itertools
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from paper_0802_0748_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def S():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0802_0748_gb300 import scocg
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return scocg
+
+
+def hub_csr(oracle_mod, L, nu, nd, t=1.0, U=4.0, V=1.0, periodic=True):
+    rowptr, col, val = oracle_mod.hubbard_csr(L, nu, nd, t, U, V, periodic)
+    n = rowptr.size - 1
+    return sp.csr_matrix((val, col, rowptr), shape=(n, n))
+
+
+def start(n, seed):
+    return torch.from_numpy(inputs.random_unit_real(n, seed)).cuda()
+
+
+@pytest.mark.parametrize("m,cg", [(20, 0), (20, 30), (50, 0)])
+def test_hubbard_ground_state_matches_dense(S, oracle_mod, m, cg):
+    """Ring L=8, 3 up 3 down (3,136 states: 13 vector blocks, a ragged down
+    tile): E to 1e-11, psi to 1e-12 in overlap, residual <= tol."""
+    from oracle import ground
+    H = hub_csr(oracle_mod, 8, 3, 3)
+    E, U = np.linalg.eigh(H.toarray())
+    assert E[1] - E[0] > 1e-2
+    h = S.scocg_create_hubbard(8, 3, 3, 1.0, 4.0, 1.0, True)
+    try:
+        e0, psi, info = S.scocg_ground_state(h, start(H.shape[0], 1), m=m, cg_steps=cg, tol=1e-10)
+    finally:
+        S.scocg_destroy(h)
+    assert info["status"] == 0 and info["residual"] <= 1e-10
+    p = psi.cpu().numpy()
+    assert abs(e0 - E[0]) < 1e-11
+    assert abs(abs(p @ U[:, 0]) - 1.0) < 1e-12
+    assert abs(np.linalg.norm(p) - 1.0) < 1e-13
+    if cg:
+        assert info["cg_steps"] > 0
+    # the oracle's own cycle reaches the same pair
+    ref = ground.lanczos_ground_state(H, inputs.random_unit_real(H.shape[0], 1), m=m, cg_steps=cg, tol=1e-10)
+    assert abs(ref.energy - e0) < 1e-11
+
+
+def test_csr_ground_state_matches_dense(S):
+    """CSR handle (FP64 values): the 4^3 x 4 Anderson matrix (256 rows)."""
+    h_csr = inputs.anderson_csr(4, seed=5)
+    E, U = np.linalg.eigh(h_csr.dense())
+    assert E[1] - E[0] > 1e-3
+    h = S.scocg_create_csr(h_csr.rowptr, h_csr.col, h_csr.val)
+    try:
+        e0, psi, info = S.scocg_ground_state(h, start(h_csr.n, 2), m=60, cg_steps=20, tol=1e-10, max_cycles=200)
+    finally:
+        S.scocg_destroy(h)
+    assert info["status"] == 0
+    assert abs(e0 - E[0]) < 1e-10
+    assert abs(abs(psi.cpu().numpy() @ U[:, 0]) - 1.0) < 1e-11
+
+
+def test_free_fermions_closed_form(S):
+    """U = V = 0, ring L=10, 5 up 5 down (63,504 states, 249 vector blocks):
+    E_0 = the sum of the lowest -2 t cos(2 pi m / L)."""
+    from oracle import ground
+    h = S.scocg_create_hubbard(10, 5, 5, 1.0, 0.0, 0.0, True)
+    try:
+        e0, psi, info = S.scocg_ground_state(h, start(252 * 252, 3), m=80, tol=1e-9)
+    finally:
+        S.scocg_destroy(h)
+    assert info["status"] == 0
+    assert abs(e0 - ground.free_fermion_ground_energy(10, 5, 5, 1.0)) < 1e-10
+
+
+def test_two_sites_early_stop(S):
+    """4 states, m = 10: the recursion ends at the invariant subspace (at most
+    4 steps) and E_0 = (U+V)/2 - sqrt(((U-V)/2)^2 + 4 t^2)."""
+    from oracle import dense
+    h = S.scocg_create_hubbard(2, 1, 1, 1.0, 3.0, 0.5, False)
+    try:
+        e0, psi, info = S.scocg_ground_state(h, start(4, 3), m=10, tol=1e-12)
+    finally:
+        S.scocg_destroy(h)
+    assert info["status"] == 0 and info["lanczos_steps"] <= 4 * info["cycles"]
+    assert abs(e0 - dense.two_site_spectrum(1.0, 3.0, 0.5)[0]) < 1e-13
+
+
+def test_not_converged_and_invalid(S):
+    """max_cycles = 1 with a tiny tolerance: NOT_CONVERGED with a valid pair;
+    bad arguments and a zero start vector are rejected."""
+    h = S.scocg_create_hubbard(6, 3, 3, 1.0, 4.0, 1.0, True)
+    try:
+        e0, psi, info = S.scocg_ground_state(h, start(400, 4), m=5, max_cycles=1, tol=1e-14)
+        assert info["status"] == 1 and info["cycles"] == 1 and np.isfinite(e0)
+        assert abs(np.linalg.norm(psi.cpu().numpy()) - 1.0) < 1e-13
+        for kw in ({"m": 1}, {"m": 2000}, {"cg_steps": -1}, {"max_cycles": 0}, {"tol": -1.0}):
+            with pytest.raises(S.ScocgError):
+                S.scocg_ground_state(h, start(400, 4), **kw)
+        with pytest.raises(S.ScocgError):
+            S.scocg_ground_state(h, torch.zeros(400, dtype=torch.float64, device="cuda"))
+    finally:
+        S.scocg_destroy(h)
+
+
+def test_excite_bit_exact(S):
+    """c and c+ for every site and spin from the L=6, 3 up 2 down sector equal
+    the oracle's Jordan-Wigner operator bit for bit (a sign and a copy)."""
+    from oracle import ground
+    L, nu, nd = 6, 3, 2
+    src = S.scocg_create_hubbard(L, nu, nd, 1.0, 4.0, 1.0, True)
+    psi_np = inputs.random_unit_real(20 * 15, 6)
+    psi = torch.from_numpy(psi_np).cuda()
+    try:
+        for spin, create in itertools.product(range(2), (False, True)):
+            d = 1 if create else -1
+            tu, td = (nu + d, nd) if spin == 0 else (nu, nd + d)
+            dst = S.scocg_create_hubbard(L, tu, td, 1.0, 4.0, 1.0, True)
+            try:
+                for site in range(L):
+                    out = S.scocg_excite(src, dst, site, spin, create, psi).cpu().numpy()
+                    ref = ground.fermion_op(L, nu, nd, site, spin, create, psi_np)
+                    assert np.all(out.imag == 0)
+                    assert np.array_equal(out.real, ref), (site, spin, create)
+            finally:
+                S.scocg_destroy(dst)
+        bad = S.scocg_create_hubbard(L, nu - 1, nd - 1, 1.0, 4.0, 1.0, True)
+        try:
+            with pytest.raises(S.ScocgError):
+                S.scocg_excite(src, bad, 0, 0, False, psi)
+            with pytest.raises(S.ScocgError):
+                S.scocg_excite(src, bad, L, 0, False, psi)
+        finally:
+            S.scocg_destroy(bad)
+    finally:
+        S.scocg_destroy(src)
+
+
+def test_ionization_and_affinity_spectra_end_to_end(S, oracle_mod):
+    """GPU ground state -> c_{0 up}|psi_0> and c+_{0 up}|psi_0> -> shifted
+    solve, against the oracle's ground state, operator and Lehmann sum.
+    Ionization: G^-(w) = b^T (w + i eta + H - E_0)^{-1} b = -b^T (z - H)^{-1} b
+    at z = E_0 - w - i eta; affinity: z = E_0 + w + i eta.  Sum rules
+    ||c psi_0||^2 = <n_0up> = 3/8 and ||c+ psi_0||^2 = 5/8."""
+    from oracle import ground
+    L, nu, nd = 8, 3, 3
+    H = hub_csr(oracle_mod, L, nu, nd)
+    E, U = np.linalg.eigh(H.toarray())
+    u0 = U[:, 0]
+    h0 = S.scocg_create_hubbard(L, nu, nd, 1.0, 4.0, 1.0, True)
+    w = np.linspace(-3.0, 12.0, 24)
+    eta = 0.1
+    try:
+        e0, psi, info = S.scocg_ground_state(h0, start(H.shape[0], 7), m=50, tol=1e-11)
+        assert info["status"] == 0
+        for create, occ in ((False, 3 / 8), (True, 5 / 8)):
+            tu = nu + (1 if create else -1)
+            h1 = S.scocg_create_hubbard(L, tu, nd, 1.0, 4.0, 1.0, True)
+            try:
+                b = S.scocg_excite(h0, h1, 0, 0, create, psi)
+                z = (e0 + w + 1j * eta) if create else (e0 - w - 1j * eta)
+                G, sinfo = S.scocg_solve(h1, z, b, proj_vec=b, tol=1e-12)
+                assert sinfo["status"] == 0
+            finally:
+                S.scocg_destroy(h1)
+            g = G.cpu().numpy()[0, 0]
+            bn = b.cpu().numpy().real
+            assert abs(bn @ bn - occ) < 1e-10
+            bref = ground.fermion_op(L, nu, nd, 0, 0, create, u0)
+            zref = (E[0] + w + 1j * eta) if create else (E[0] - w - 1j * eta)
+            ref = ground.lehmann_green(hub_csr(oracle_mod, L, tu, nd), bref, zref)
+            assert np.max(np.abs(g - ref)) / np.max(np.abs(ref)) < 1e-8
+    finally:
+        S.scocg_destroy(h0)
+
+
+def test_full_size_ring_sampled(S):
+    """14 sites, 7 up 7 down (11,778,624 states, the size of the Hubbard
+    shifted-solve workload): after the ground-state cycles, 256 sampled rows of
+    H psi - E psi computed one by one by the oracle are each below the reported
+    residual, psi has unit norm, and 512 sampled entries of c_{3 dn} psi equal
+    the oracle's one-by-one operator bit for bit."""
+    from oracle import ground
+    L, nu, nd = 14, 7, 7
+    n = 3432 * 3432
+    h = S.scocg_create_hubbard(L, nu, nd, 1.0, 4.0, 1.0, True)
+    h1 = S.scocg_create_hubbard(L, nu, nd - 1, 1.0, 4.0, 1.0, True)
+    try:
+        e0, psi, info = S.scocg_ground_state(h, start(n, 8), m=80, cg_steps=40, max_cycles=6, tol=1e-8)
+        assert info["status"] in (0, 1)
+        res = info["residual"]
+        assert np.isfinite(e0) and res < 1e-4
+        p = psi.cpu().numpy()
+        assert abs(np.linalg.norm(p) - 1.0) < 1e-12
+        rows = np.random.default_rng(9).choice(n, 256, replace=False)
+        hp = ground.hubbard_rows_apply(L, nu, nd, 1.0, 4.0, 1.0, True, p, rows)
+        assert np.all(np.abs(hp - e0 * p[rows]) <= res * (1 + 1e-6) + 1e-13)
+        b = S.scocg_excite(h, h1, 3, 1, False, psi).cpu().numpy()
+        tgt = np.random.default_rng(10).choice(b.size, 512, replace=False)
+        ref = ground.fermion_op_at(L, nu, nd, 3, 1, False, p, tgt)
+        assert np.array_equal(b.real[tgt], ref)
+    finally:
+        S.scocg_destroy(h)
+        S.scocg_destroy(h1)

@@ -186,3 +186,24 @@ def test_excitation_green_lehmann_and_moments(oracle_mod):
     gl = ground.excitation_green(Hm, b, zl)
     approx = (b @ b) / zl + (b @ (Hm @ b)) / zl ** 2
     assert np.max(np.abs(gl - approx) / np.abs(approx)) < 1e-6
+
+
+def test_fermion_op_at_equals_whole_vector():
+    """Entry-wise evaluation equals the whole-vector operator (L = 5, all
+    sites, spins, c and c+)."""
+    L, nu, nd = 5, 2, 3
+    psi = inputs.random_unit_real(10 * 10, 12)
+    for site, spin, create in itertools.product(range(L), range(2), (False, True)):
+        full = ground.fermion_op(L, nu, nd, site, spin, create, psi)
+        got = ground.fermion_op_at(L, nu, nd, site, spin, create, psi, np.arange(full.size))
+        assert np.array_equal(got, full), (site, spin, create)
+
+
+@pytest.mark.parametrize("L,nu,nd,periodic", [(5, 2, 3, True), (6, 3, 2, False), (4, 2, 2, True)])
+def test_hubbard_rows_apply_equals_matrix(oracle_mod, L, nu, nd, periodic):
+    """Row-wise H psi from the operators equals the C oracle's sector matrix."""
+    H = hubbard(oracle_mod, L, nu, nd, t=0.7, U=3.0, V=1.3, periodic=periodic)
+    psi = inputs.random_unit_real(H.shape[0], 13)
+    rows = np.arange(H.shape[0])
+    got = ground.hubbard_rows_apply(L, nu, nd, 0.7, 3.0, 1.3, periodic, psi, rows)
+    assert np.allclose(got, H @ psi, rtol=0, atol=1e-14)
