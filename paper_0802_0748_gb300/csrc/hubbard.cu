@@ -263,6 +263,8 @@ cudaError_t hubbard_apply(const Hubbard& hb, int prec, double2 z, const void* x,
     return cudaGetLastError();
 }
 
+constexpr int kHopBatch = 8;
+
 // Real FP64 operator of the ground-state iteration: y = (H - sigma) x - beta x_prev
 // (x_prev and beta optional), same unit order as the solver's apply, and the
 // block's partial of x^T y in part[blockIdx.x].  A launch whose *skip is set
@@ -287,18 +289,34 @@ __global__ void __launch_bounds__(kVecBlock) k_hub_hx(ApplyHubbard<double> ap, i
         const int cv = __popc(su & pu) + __popc(sd & pd) + __popc(su & pd) + __popc(sd & pu);
         const double xi = x[row];
         double hop = 0.0;   // sum of sign * x over the hops; H's hopping part is -t times it
+        // hops in batches of kHopBatch: the table entries, then the gathers, are
+        // issued together (the list of a string ends at its first -1)
         const double* xrow = x + (size_t)u * ap.D_dn;
-        for (int j = 0; j < ap.S; ++j) {
-            const int e = ap.hop_dn[(size_t)d * ap.S + j];
-            if (e < 0) break;
-            const double xv = xrow[e >> 1];
-            hop += (e & 1) ? -xv : xv;
+        const int32_t* tdn = ap.hop_dn + (size_t)d * ap.S;
+        for (int j0 = 0; j0 < ap.S; j0 += kHopBatch) {
+            int e[kHopBatch];
+            double xv[kHopBatch];
+#pragma unroll
+            for (int q = 0; q < kHopBatch; ++q) e[q] = j0 + q < ap.S ? tdn[j0 + q] : -1;
+#pragma unroll
+            for (int q = 0; q < kHopBatch; ++q) xv[q] = e[q] >= 0 ? xrow[e[q] >> 1] : 0.0;
+#pragma unroll
+            for (int q = 0; q < kHopBatch; ++q)
+                if (e[q] >= 0) hop += (e[q] & 1) ? -xv[q] : xv[q];
+            if (e[kHopBatch - 1] < 0) break;
         }
-        for (int j = 0; j < ap.S; ++j) {
-            const int e = ap.hop_up[(size_t)u * ap.S + j];
-            if (e < 0) break;
-            const double xv = x[(size_t)(e >> 1) * ap.D_dn + d];
-            hop += (e & 1) ? -xv : xv;
+        const int32_t* tup = ap.hop_up + (size_t)u * ap.S;
+        for (int j0 = 0; j0 < ap.S; j0 += kHopBatch) {
+            int e[kHopBatch];
+            double xv[kHopBatch];
+#pragma unroll
+            for (int q = 0; q < kHopBatch; ++q) e[q] = j0 + q < ap.S ? tup[j0 + q] : -1;
+#pragma unroll
+            for (int q = 0; q < kHopBatch; ++q) xv[q] = e[q] >= 0 ? x[(size_t)(e[q] >> 1) * ap.D_dn + d] : 0.0;
+#pragma unroll
+            for (int q = 0; q < kHopBatch; ++q)
+                if (e[q] >= 0) hop += (e[q] & 1) ? -xv[q] : xv[q];
+            if (e[kHopBatch - 1] < 0) break;
         }
         const double diag = ap.U * (double)cu + ap.V * (double)cv;
         double yi = fma(diag - sigma, xi, -ap.t * hop);

@@ -195,19 +195,22 @@ def test_ionization_and_affinity_spectra_end_to_end(S, oracle_mod):
         S.scocg_destroy(h0)
 
 
-def test_full_size_ring_sampled(S):
-    """14 sites, 7 up 7 down (11,778,624 states, the size of the Hubbard
-    shifted-solve workload): after the ground-state cycles, 256 sampled rows of
-    H psi - E psi computed one by one by the oracle are each below the reported
-    residual, psi has unit norm, and 512 sampled entries of c_{3 dn} psi equal
-    the oracle's one-by-one operator bit for bit."""
+@pytest.mark.parametrize("L,m", [(12, 40), (14, 80)])
+def test_ring_sampled(S, L, m):
+    """12 sites (853,776 states) and 14 sites, 7 up 7 down (11,778,624 states,
+    the size of the Hubbard shifted-solve workload), half filling: after the
+    ground-state cycles, 256 sampled rows of H psi - E psi computed one by one
+    by the oracle are each below the reported residual, psi has unit norm, and
+    512 sampled entries of c_{3 dn} psi equal the oracle's one-by-one operator
+    bit for bit."""
+    import math
     from oracle import ground
-    L, nu, nd = 14, 7, 7
-    n = 3432 * 3432
+    nu = nd = L // 2
+    n = math.comb(L, nu) ** 2
     h = S.scocg_create_hubbard(L, nu, nd, 1.0, 4.0, 1.0, True)
     h1 = S.scocg_create_hubbard(L, nu, nd - 1, 1.0, 4.0, 1.0, True)
     try:
-        e0, psi, info = S.scocg_ground_state(h, start(n, 8), m=80, cg_steps=40, max_cycles=6, tol=1e-8)
+        e0, psi, info = S.scocg_ground_state(h, start(n, 8), m=m, cg_steps=40, max_cycles=6, tol=1e-8)
         assert info["status"] in (0, 1)
         res = info["residual"]
         assert np.isfinite(e0) and res < 1e-4
