@@ -263,7 +263,28 @@ cudaError_t hubbard_apply(const Hubbard& hb, int prec, double2 z, const void* x,
     return cudaGetLastError();
 }
 
-constexpr int kHopBatch = 8;
+constexpr int kHopBatch = 4;
+constexpr int kMaxSites = 16;   // scocg_create_hubbard accepts L <= 16
+
+// acc + sum over the hop list tab[0..S) (ended by -1) of sign * base[target * stride],
+// sign = -1 where bit 0 of the entry is set, added in list order
+__device__ __forceinline__ double hop_sum(const int32_t* tab, int S, const double* base, int64_t stride, double acc) {
+    for (int j0 = 0; j0 < S; j0 += kHopBatch) {
+        int e[kHopBatch];
+        double xv[kHopBatch];
+#pragma unroll
+        for (int q = 0; q < kHopBatch; ++q) e[q] = j0 + q < S ? tab[j0 + q] : -1;
+#pragma unroll
+        for (int q = 0; q < kHopBatch; ++q)
+            if (e[q] >= 0) xv[q] = base[(int64_t)(e[q] >> 1) * stride];
+#pragma unroll
+        for (int q = 0; q < kHopBatch; ++q) {
+            if (e[q] < 0) return acc;
+            acc += __longlong_as_double(__double_as_longlong(xv[q]) ^ ((long long)(e[q] & 1) << 63));
+        }
+    }
+    return acc;
+}
 
 // Real FP64 operator of the ground-state iteration: y = (H - sigma) x - beta x_prev
 // (x_prev and beta optional), same unit order as the solver's apply, and the
@@ -273,6 +294,13 @@ __global__ void __launch_bounds__(kVecBlock) k_hub_hx(ApplyHubbard<double> ap, i
                                                       double* y, const double* xprev, const double* beta,
                                                       double sigma, const int* skip, double* part) {
     if (skip && *skip) return;
+    // diagonal minus sigma for every (double occupancies, neighbour pairs):
+    // U cu + V cv - sigma, cu <= L, cv <= 4 L, built once per block
+    __shared__ double s_diag[(kMaxSites + 1) * (4 * kMaxSites + 1)];
+    const int ncv = 4 * ap.L + 1;
+    for (int i = threadIdx.x; i < (ap.L + 1) * ncv; i += kVecBlock)
+        s_diag[i] = fma(ap.U, (double)(i / ncv), fma(ap.V, (double)(i % ncv), -sigma));
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (blockIdx.x * (int64_t)kVecBlock + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * kVecBlock) >> 5;
@@ -290,36 +318,12 @@ __global__ void __launch_bounds__(kVecBlock) k_hub_hx(ApplyHubbard<double> ap, i
         const double xi = x[row];
         double hop = 0.0;   // sum of sign * x over the hops; H's hopping part is -t times it
         // hops in batches of kHopBatch: the table entries, then the gathers, are
-        // issued together (the list of a string ends at its first -1)
+        // issued together; the list of a string ends at its first -1, and the
+        // sign is put on the gathered value's sign bit (one FP64 add per hop)
         const double* xrow = x + (size_t)u * ap.D_dn;
-        const int32_t* tdn = ap.hop_dn + (size_t)d * ap.S;
-        for (int j0 = 0; j0 < ap.S; j0 += kHopBatch) {
-            int e[kHopBatch];
-            double xv[kHopBatch];
-#pragma unroll
-            for (int q = 0; q < kHopBatch; ++q) e[q] = j0 + q < ap.S ? tdn[j0 + q] : -1;
-#pragma unroll
-            for (int q = 0; q < kHopBatch; ++q) xv[q] = e[q] >= 0 ? xrow[e[q] >> 1] : 0.0;
-#pragma unroll
-            for (int q = 0; q < kHopBatch; ++q)
-                if (e[q] >= 0) hop += (e[q] & 1) ? -xv[q] : xv[q];
-            if (e[kHopBatch - 1] < 0) break;
-        }
-        const int32_t* tup = ap.hop_up + (size_t)u * ap.S;
-        for (int j0 = 0; j0 < ap.S; j0 += kHopBatch) {
-            int e[kHopBatch];
-            double xv[kHopBatch];
-#pragma unroll
-            for (int q = 0; q < kHopBatch; ++q) e[q] = j0 + q < ap.S ? tup[j0 + q] : -1;
-#pragma unroll
-            for (int q = 0; q < kHopBatch; ++q) xv[q] = e[q] >= 0 ? x[(size_t)(e[q] >> 1) * ap.D_dn + d] : 0.0;
-#pragma unroll
-            for (int q = 0; q < kHopBatch; ++q)
-                if (e[q] >= 0) hop += (e[q] & 1) ? -xv[q] : xv[q];
-            if (e[kHopBatch - 1] < 0) break;
-        }
-        const double diag = ap.U * (double)cu + ap.V * (double)cv;
-        double yi = fma(diag - sigma, xi, -ap.t * hop);
+        hop = hop_sum(ap.hop_dn + (size_t)d * ap.S, ap.S, xrow, 1, hop);
+        hop = hop_sum(ap.hop_up + (size_t)u * ap.S, ap.S, x + d, ap.D_dn, hop);
+        double yi = fma(s_diag[cu * ncv + cv], xi, -ap.t * hop);
         if (xprev) yi = fma(-bp, xprev[row], yi);
         y[row] = yi;
         acc = fma(xi, yi, acc);
