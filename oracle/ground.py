@@ -20,6 +20,8 @@ scipy.sparse matrix).
                             occupation patterns (Sec. IV.D's model)
 * ``fermion_op_at``         selected entries of the same, one by one
 * ``hubbard_rows_apply``    (H psi) on selected rows, from the operators
+* ``krylov_sd``             Green's functions by subspace diagonalisation in the
+                            Krylov subspace (Sec. III.B, Eq. Ham_in_KS)
 * ``excitation_green``      <b|(z - H)^{-1}|b> by dense solves (Eq. gf)
 * ``lehmann_green``         the same from the eigen-decomposition of H
 
@@ -247,6 +249,33 @@ def hubbard_rows_apply(L, n_up, n_dn, t, U, V, periodic, psi, rows):
     return out
 
 
+class KrylovSD:
+    def __init__(self, G, ritz, weight, nu):
+        self.G = G              # [M][K]
+        self.ritz = ritz        # [nu] eigenvalues of T, ascending
+        self.weight = weight    # [M][nu] (c_m^T w_a)(w_a^T b)
+        self.nu = nu            # Lanczos steps done
+
+
+def krylov_sd(H, b, nu, shifts, C):
+    """Subspace diagonalisation in the Krylov subspace K_nu(H, b) (Sec. III.B,
+    Eq. Ham_in_KS): the reduced Hamiltonian in the Lanczos basis v_0..v_{nu-1}
+    (no reorthogonalization) is the tridiagonal T; its eigenpairs (e_a, s_a)
+    give approximate eigenvectors w_a = sum_j s_a(j) v_j, and
+        G_m(z) = sum_a (c_m^T w_a)(w_a^T b) / (z - e_a),
+    with w_a^T b = ||b|| s_a(0).  C: [M][N] real projection vectors."""
+    b = np.asarray(b, dtype=np.float64)
+    C = np.atleast_2d(np.asarray(C, dtype=np.float64))
+    alpha, beta, V = _lanczos(H, b, nu)
+    T = np.diag(alpha) + np.diag(beta, 1) + np.diag(beta, -1)
+    e, S = np.linalg.eigh(T)
+    P = C @ V.T                                   # [M][k]: c_m^T v_j
+    weight = (P @ S) * (np.linalg.norm(b) * S[0])[None, :]
+    shifts = np.asarray(shifts, dtype=np.complex128)
+    G = weight @ (1.0 / (shifts[None, :] - e[:, None]))
+    return KrylovSD(G, e, weight, alpha.size)
+
+
 def excitation_green(H, b, shifts):
     """G(z_k) = b^T (z_k - H)^{-1} b by dense solves (Eq. gf with c = b real)."""
     H = np.asarray(H.todense() if hasattr(H, "todense") else H, dtype=np.float64)
@@ -287,5 +316,5 @@ def occupations(L, n_up, n_dn, psi):
     return out
 
 
-__all__ = ["lanczos_ground_state", "fermion_op", "fermion_op_at", "hubbard_rows_apply", "excitation_green", "lehmann_green",
+__all__ = ["krylov_sd", "KrylovSD", "lanczos_ground_state", "fermion_op", "fermion_op_at", "hubbard_rows_apply", "excitation_green", "lehmann_green",
            "free_fermion_ground_energy", "occupations", "GroundState", "CG_RTOL"]

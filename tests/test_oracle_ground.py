@@ -207,3 +207,46 @@ def test_hubbard_rows_apply_equals_matrix(oracle_mod, L, nu, nd, periodic):
     rows = np.arange(H.shape[0])
     got = ground.hubbard_rows_apply(L, nu, nd, 0.7, 3.0, 1.3, periodic, psi, rows)
     assert np.allclose(got, H @ psi, rtol=0, atol=1e-14)
+
+
+# ------------------------------------------------------------ Krylov subspace diagonalisation
+def test_krylov_sd_chain_is_truncated_chain():
+    """From the end site of an open chain the Lanczos basis is e_0, e_1, ...
+    (alpha = 0, beta = |t|), so K_nu gives exactly the Green's function of the
+    chain of nu sites: G_00 = closed form of the nu-site chain."""
+    h = inputs.chain_csr(400, t=-1.0)
+    b = np.zeros(h.n); b[0] = 1.0
+    z = np.linspace(-2.5, 2.5, 11) + 0.05j
+    res = ground.krylov_sd(h.scipy(), b, 30, z, b[None, :])
+    assert res.nu == 30
+    assert np.max(np.abs(res.G[0] - dense.chain_g00_exact(30, -1.0, z))) < 1e-12
+
+
+def test_krylov_sd_complete_space_equals_dense():
+    """nu = 2 N on 108 rows: past N steps the basis has lost orthogonality,
+    but T's spectral measure (converged eigenvalues with their ghost copies)
+    reproduces the dense Green's function (unit and dense projections); at
+    nu = N it is not there yet."""
+    h = inputs.anderson_csr(3, seed=4)           # 108 rows
+    b = inputs.random_unit_real(h.n, 21)
+    C = np.stack([b, np.eye(h.n)[5], inputs.random_unit_real(h.n, 22)])
+    z = np.linspace(-5, 5, 9) + 0.3j
+    ref = dense.green_dense(h.dense(), z, b.astype(np.complex128), C.astype(np.complex128))
+    res = ground.krylov_sd(h.scipy(), b, 2 * h.n, z, C)
+    assert np.max(np.abs(res.G - ref)) / np.max(np.abs(ref)) < 1e-10
+    res = ground.krylov_sd(h.scipy(), b, 60, z, C)
+    assert np.max(np.abs(res.G - ref)) / np.max(np.abs(ref)) > 1e-4
+
+
+def test_krylov_sd_moments():
+    """Gauss quadrature: with c = b the weights reproduce the moments
+    b^T H^k b for k < 2 nu (nu = 6, before any loss of orthogonality)."""
+    h = inputs.anderson_csr(4, seed=6)
+    H = h.scipy()
+    b = inputs.random_unit_real(h.n, 23)
+    res = ground.krylov_sd(H, b, 6, [0.0 + 1j], b[None, :])
+    v = b.copy()
+    for k in range(12):
+        mk = float(b @ v)
+        assert abs(np.sum(res.weight[0] * res.ritz ** k) - mk) < 1e-9 * max(1.0, abs(mk)), k
+        v = H @ v
