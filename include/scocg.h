@@ -369,6 +369,41 @@ int scocg_ground_state(scocg_handle h, const double *v0, double *psi, int m, int
 int scocg_excite(scocg_handle from, scocg_handle to, int site, int spin, int create, const double *psi,
                  void *out);
 
+/*
+ * scocg_krylov_sd -- Green's functions by subspace diagonalisation in the
+ * Krylov subspace K_nu(H, b) (Sec. III.B, Eq. Ham_in_KS), the cheaper
+ * estimator that the shifted COCG method refines: nu Lanczos steps from b (no
+ * reorthogonalization; fewer steps when beta_j vanishes) give the reduced
+ * Hamiltonian T (tridiagonal) and the projections c_m^T v_j; T's eigenpairs
+ * (e_a, s_a) give the approximate eigenvectors w_a = sum_j s_a(j) v_j and
+ *   G_m(z_k) = sum_a weight[m][a] / (z_k - e_a),
+ *   weight[m][a] = (c_m^T w_a)(w_a^T b) = (sum_j s_a(j) c_m^T v_j) ||b|| s_a(0).
+ * FP64 arithmetic regardless of the handle's precision option; CSR or Hubbard
+ * handle.  The eigenvalues come from bisection on the Sturm count, the
+ * eigenvectors from inverse iteration, orthogonalised within clusters of
+ * eigenvalues closer than 1e-3 ||T|| (where the lost orthogonality puts the
+ * ghost copies of converged eigenvalues).  A density-matrix element follows
+ * as sum_a f(e_a) weight[m][a].
+ *   b            device double [N] (real, not zero)
+ *   nu           1..1024 Lanczos steps
+ *   shifts       host [nshift] (1..2^20)
+ *   proj_idx     host int64 [nproj] unit projections e_i, OR
+ *   proj_vec     device double [nproj][N] real projection vectors; 1 <= nproj <= 64
+ *   G_out        device complex128 [nproj][nshift], written
+ *   ritz         device double [nu] or NULL: the eigenvalues e_a, ascending
+ *                (the first *nu_used are written)
+ *   weight       device double [nproj][nu] or NULL (row stride nu; the first
+ *                *nu_used of each row are written)
+ *   nu_used      host int or NULL: Lanczos steps done
+ *   seconds      host double or NULL: device time
+ * Allocates about (4 N + nu^2 + 2 nproj nu) doubles of device memory per call.
+ * Returns SCOCG_OK, SCOCG_ERR_INVALID (also for b = 0), SCOCG_ERR_OOM or
+ * SCOCG_ERR_CUDA.
+ */
+int scocg_krylov_sd(scocg_handle h, const double *b, int nu, const scocg_c128 *shifts, int nshift,
+                    const int64_t *proj_idx, const double *proj_vec, int nproj, scocg_c128 *G_out,
+                    double *ritz, double *weight, int *nu_used, double *seconds);
+
 /* Free the handle and everything it owns (NULL is ignored). */
 void scocg_destroy(scocg_handle h);
 

@@ -313,6 +313,176 @@ __global__ void __launch_bounds__(kVecBlock) k_cg_p(int64_t n, int s, const doub
     GRID_STRIDE(i, n) p[i] = fma(be, p[i], r[i]);
 }
 
+// ---- Krylov subspace diagonalisation (Sec. III.B) ----
+
+// P[m][j] = c_m^T v_j for unit projections c_m = e_{idx[m]}
+__global__ void k_proj_unit(int M, const int64_t* idx, const double* v, double* P, int nu, int j, const int* stop) {
+    if (stop[j]) return;
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < M) P[(size_t)m * nu + j] = v[idx[m]];
+}
+
+// partials of c_m^T v for dense projections C[M][n], part[m * G + block]
+__global__ void __launch_bounds__(kVecBlock) k_proj_dense(int64_t n, int M, const double* C, const double* v,
+                                                          double* part, int G, const int* stop, int j) {
+    if (stop[j]) return;
+    for (int m = 0; m < M; ++m) {
+        double acc = 0.0;
+        GRID_STRIDE(i, n) acc = fma(C[(size_t)m * n + i], v[i], acc);
+        block_partial(acc, part + (size_t)m * G);
+        __syncthreads();
+    }
+}
+
+// one block per projection: P[m][j] = sum of its partials
+__global__ void __launch_bounds__(kVecBlock) k_proj_fin(const double* part, int G, double* P, int nu, int j,
+                                                        const int* stop) {
+    if (stop[j]) return;
+    const double s = sum_partials(part + (size_t)blockIdx.x * G, G);
+    if (threadIdx.x == 0) P[(size_t)blockIdx.x * nu + j] = s;
+}
+
+// Sturm count: eigenvalues of the k x k tridiagonal below x
+__device__ int tri_count_below(const double* a, const double* b, int k, double x, double pivmin) {
+    int c = 0;
+    double d = 1.0;
+    for (int i = 0; i < k; ++i) {
+        d = (a[i] - x) - (i > 0 ? b[i - 1] * (b[i - 1] / d) : 0.0);
+        if (fabs(d) < pivmin) d = -pivmin;
+        if (d < 0.0) ++c;
+    }
+    return c;
+}
+
+// eigenvalue q (ascending) of T, one thread each: bisection on the Sturm count
+// inside the Gershgorin interval
+__global__ void k_tri_evals(const int* kdim, const double* alpha, const double* beta, double* ev, double* scale_out) {
+    const int k = *kdim;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    double lo = INFINITY, hi = -INFINITY;
+    for (int i = 0; i < k; ++i) {
+        const double r = (i > 0 ? fabs(beta[i - 1]) : 0.0) + (i + 1 < k ? fabs(beta[i]) : 0.0);
+        lo = fmin(lo, alpha[i] - r);
+        hi = fmax(hi, alpha[i] + r);
+    }
+    const double scale = fmax(fmax(fabs(lo), fabs(hi)), 1e-300);
+    if (q == 0 && scale_out) *scale_out = scale;
+    if (q >= k) return;
+    const double eps = 2.220446049250313e-16;
+    const double pivmin = eps * scale * 1e-3 + 1e-300;
+    lo -= 2.0 * eps * scale + pivmin;
+    hi += 2.0 * eps * scale + pivmin;
+    for (int it = 0; it < 200 && hi - lo > 2.0 * eps * fmax(fabs(lo), fabs(hi)) + pivmin; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (tri_count_below(alpha, beta, k, mid, pivmin) >= q + 1) hi = mid; else lo = mid;
+    }
+    ev[q] = 0.5 * (lo + hi);
+}
+
+// eigenvectors of T (rows of S, S[q][i]), one thread: inverse iteration at
+// each eigenvalue with T - e_q factorised by Gaussian elimination with
+// partial pivoting; within a cluster (neighbouring eigenvalues closer than
+// 1e-3 ||T||) each iterate is orthogonalised against the cluster's earlier
+// vectors (the ghost copies of converged eigenvalues that the Lanczos
+// recursion produces without reorthogonalization come in such clusters)
+__global__ void k_tri_evecs(const int* kdim, const double* alpha, const double* beta, const double* ev,
+                            const double* scale_p, double* S, double* work) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int k = *kdim;
+    const double scale = *scale_p;
+    const double eps = 2.220446049250313e-16;
+    const double tiny = eps * scale + 1e-280;
+    double* U0 = work;
+    double* U1 = work + k;
+    double* U2 = work + 2 * k;
+    double* l = work + 3 * k;
+    double* sw = work + 4 * k;
+    int cl0 = 0;   // first eigenvalue of the current cluster
+    for (int q = 0; q < k; ++q) {
+        if (q > 0 && ev[q] - ev[q - 1] > 1e-3 * scale) cl0 = q;
+        // perturb a repeated shift slightly so that the factorisation differs
+        const double th = ev[q] + (q > cl0 ? (q - cl0) * 10.0 * eps * scale : 0.0);
+        double r0 = alpha[0] - th, r1 = k > 1 ? beta[0] : 0.0, r2 = 0.0;
+        for (int i = 0; i + 1 < k; ++i) {
+            const double c = beta[i];
+            const double d1 = alpha[i + 1] - th, d2 = i + 2 < k ? beta[i + 1] : 0.0;
+            if (fabs(r0) >= fabs(c)) {
+                const double m = r0 != 0.0 ? c / r0 : 0.0;
+                U0[i] = r0; U1[i] = r1; U2[i] = r2; l[i] = m; sw[i] = 0.0;
+                r0 = d1 - m * r1; r1 = d2 - m * r2; r2 = 0.0;
+            } else {
+                const double m = r0 / c;
+                U0[i] = c; U1[i] = d1; U2[i] = d2; l[i] = m; sw[i] = 1.0;
+                const double n0 = r1 - m * d1, n1 = r2 - m * d2;
+                r0 = n0; r1 = n1; r2 = 0.0;
+            }
+            if (fabs(U0[i]) < tiny) U0[i] = U0[i] < 0.0 ? -tiny : tiny;
+        }
+        U0[k - 1] = fabs(r0) < tiny ? (r0 < 0.0 ? -tiny : tiny) : r0;
+        double* s = S + (size_t)q * k;
+        for (int i = 0; i < k; ++i) s[i] = 1.0 + (double)(((i + 3 * q) * 7919) % 13) / 13.0;
+        for (int rep = 0; rep < 3; ++rep) {
+            for (int i = 0; i + 1 < k; ++i) {
+                if (sw[i] != 0.0) { const double t = s[i]; s[i] = s[i + 1]; s[i + 1] = t; }
+                s[i + 1] -= l[i] * s[i];
+            }
+            for (int i = k - 1; i >= 0; --i) {
+                double v = s[i];
+                if (i + 1 < k) v -= U1[i] * s[i + 1];
+                if (i + 2 < k) v -= U2[i] * s[i + 2];
+                s[i] = v / U0[i];
+            }
+            double mx = 0.0;
+            for (int i = 0; i < k; ++i) mx = fmax(mx, fabs(s[i]));
+            if (!(mx > 0.0) || !isfinite(mx)) break;
+            for (int i = 0; i < k; ++i) s[i] /= mx;
+            for (int p = cl0; p < q; ++p) {          // Gram-Schmidt against the cluster
+                const double* sp = S + (size_t)p * k;
+                double dot = 0.0;
+                for (int i = 0; i < k; ++i) dot += sp[i] * s[i];
+                for (int i = 0; i < k; ++i) s[i] -= dot * sp[i];
+            }
+            double nr = 0.0;
+            for (int i = 0; i < k; ++i) nr += s[i] * s[i];
+            nr = sqrt(nr);
+            if (!(nr > 0.0)) break;
+            for (int i = 0; i < k; ++i) s[i] /= nr;
+        }
+    }
+}
+
+// weight[m][q] = (c_m^T w_q)(w_q^T b) = (sum_j S[q][j] P[m][j]) ||b|| S[q][0]; one thread per (m, q)
+__global__ void k_krylov_weight(const int* kdim, int M, int nu, const double* S, const double* P,
+                                const double* bnorm, double* W) {
+    const int k = *kdim;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= M * k) return;
+    const int m = t / k, q = t % k;
+    const double* s = S + (size_t)q * k;
+    const double* p = P + (size_t)m * nu;
+    double acc = 0.0;
+    for (int j = 0; j < k; ++j) acc = fma(s[j], p[j], acc);
+    W[(size_t)m * nu + q] = acc * (*bnorm) * s[0];
+}
+
+// G[m][kk] = sum_q weight[m][q] / (z_kk - e_q); one thread per (m, kk)
+__global__ void k_krylov_g(const int* kdim, int M, int nu, int K, const double* ev, const double* W,
+                           const double2* z, double2* G) {
+    const int k = *kdim;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= M * K) return;
+    const int m = t / K, kk = t % K;
+    const double2 zz = z[kk];
+    double gr = 0.0, gi = 0.0;
+    for (int q = 0; q < k; ++q) {
+        const double dr = zz.x - ev[q], di = zz.y;
+        const double w = W[(size_t)m * nu + q] / fma(dr, dr, di * di);   // w / |z - e|^2
+        gr = fma(w, dr, gr);
+        gi = fma(-w, di, gi);
+    }
+    G[t] = make_double2(gr, gi);
+}
+
 #undef GRID_STRIDE
 
 // Device scalars of one call, carved from one allocation.
@@ -495,5 +665,115 @@ extern "C" int scocg_ground_state(scocg_handle h, const double* v0, double* psi_
         info->seconds = ms * 1e-3;
         info->bytes_per_step = lanczos_step_bytes(h);
     }
+    return status;
+}
+
+extern "C" int scocg_krylov_sd(scocg_handle h, const double* b, int nu, const scocg_c128* shifts, int nshift,
+                               const int64_t* proj_idx, const double* proj_vec, int nproj, scocg_c128* G_out,
+                               double* ritz, double* weight, int* nu_used, double* seconds) {
+    if (!h || !b || nu < 1 || nu > kMaxLanczos || !shifts || nshift < 1 || nshift > (1 << 20) || nproj < 1 ||
+        nproj > 64 || (!proj_idx) == (!proj_vec) || !G_out)
+        return SCOCG_ERR_INVALID;
+    if (h->kind == HandleKind::kCsr && !h->d_val64) return SCOCG_ERR_INVALID;
+    const int64_t n = h->n;
+    if (n < 1) return SCOCG_ERR_INVALID;
+    for (int k = 0; k < nshift; ++k)
+        if (!std::isfinite(shifts[k].re) || !std::isfinite(shifts[k].im)) return SCOCG_ERR_INVALID;
+    if (proj_idx)
+        for (int m = 0; m < nproj; ++m)
+            if (proj_idx[m] < 0 || proj_idx[m] >= n) return SCOCG_ERR_INVALID;
+    const int G = (int)std::max<int64_t>(1, std::min<int64_t>((n + kVecBlock - 1) / kVecBlock, 8LL * h->num_sms));
+    const int M = nproj, K = nshift;
+    Carver cv{nullptr, 0};
+    double *vb[3], *w, *P, *S, *W, *work, *alpha, *beta, *tnorm, *ev, *scal, *part, *part2, *partM;
+    int *stop, *kdim;
+    int64_t* d_idx;
+    double2* d_z;
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+            void* base = nullptr;
+            if (cudaMalloc(&base, cv.off) != cudaSuccess) { cudaGetLastError(); return SCOCG_ERR_OOM; }
+            cv = Carver{static_cast<char*>(base), 0};
+        }
+        for (int v = 0; v < 3; ++v) vb[v] = (double*)cv.take(sizeof(double) * n);
+        w = (double*)cv.take(sizeof(double) * n);
+        P = (double*)cv.take(sizeof(double) * (size_t)M * nu);
+        S = (double*)cv.take(sizeof(double) * (size_t)nu * nu);
+        W = (double*)cv.take(sizeof(double) * (size_t)M * nu);
+        work = (double*)cv.take(sizeof(double) * 5 * (size_t)nu);
+        alpha = (double*)cv.take(sizeof(double) * nu);
+        beta = (double*)cv.take(sizeof(double) * nu);
+        tnorm = (double*)cv.take(sizeof(double) * nu);
+        ev = (double*)cv.take(sizeof(double) * nu);
+        scal = (double*)cv.take(sizeof(double) * 4);
+        part = (double*)cv.take(sizeof(double) * G);
+        part2 = (double*)cv.take(sizeof(double) * G);
+        partM = (double*)cv.take(sizeof(double) * (size_t)M * G);
+        stop = (int*)cv.take(sizeof(int) * (nu + 1));
+        kdim = (int*)cv.take(sizeof(int));
+        d_idx = (int64_t*)cv.take(sizeof(int64_t) * M);
+        d_z = (double2*)cv.take(sizeof(double2) * K);
+    }
+    char* base = cv.base;
+    cudaStream_t st = h->stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_z, shifts, sizeof(double2) * K, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && proj_idx)
+        e = cudaMemcpyAsync(d_idx, proj_idx, sizeof(int64_t) * M, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(stop, 0, sizeof(int) * (nu + 1), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P, 0, sizeof(double) * (size_t)M * nu, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    int status = SCOCG_OK;
+    if (e == cudaSuccess) {
+        // v_0 = b / ||b||, ||b|| kept for the weights
+        k_norm_part<<<G, kVecBlock, 0, st>>>(n, b, part);
+        k_sum_store<<<1, kVecBlock, 0, st>>>(part, G, scal, 1);
+        k_scale_to<<<G, kVecBlock, 0, st>>>(n, b, vb[0], part, G, kdim);
+        int ok = 0;
+        e = cudaMemcpyAsync(&ok, kdim, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess && !ok) status = SCOCG_ERR_INVALID;
+    }
+    for (int j = 0; j < nu && e == cudaSuccess && status == SCOCG_OK; ++j) {
+        const double* vj = vb[j % 3];
+        if (proj_idx) {
+            k_proj_unit<<<(M + 63) / 64, 64, 0, st>>>(M, d_idx, vj, P, nu, j, stop);
+        } else {
+            k_proj_dense<<<G, kVecBlock, 0, st>>>(n, M, proj_vec, vj, partM, G, stop, j);
+            k_proj_fin<<<M, kVecBlock, 0, st>>>(partM, G, P, nu, j, stop);
+        }
+        e = hx(h, vj, w, j ? vb[(j + 2) % 3] : nullptr, j ? beta + j - 1 : nullptr, 0.0, stop + j, part, G);
+        if (e != cudaSuccess) break;
+        k_lz_ortho<<<G, kVecBlock, 0, st>>>(n, j, vj, w, part, G, stop, alpha, part2);
+        k_lz_next<<<G, kVecBlock, 0, st>>>(n, j, nu, w, vb[(j + 1) % 3], part2, G, alpha, beta, tnorm, stop, kdim);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && status == SCOCG_OK) {
+        k_tri_evals<<<(nu + 127) / 128, 128, 0, st>>>(kdim, alpha, beta, ev, scal + 1);
+        k_tri_evecs<<<1, 32, 0, st>>>(kdim, alpha, beta, ev, scal + 1, S, work);
+        k_krylov_weight<<<(M * nu + 127) / 128, 128, 0, st>>>(kdim, M, nu, S, P, scal, W);
+        k_krylov_g<<<(M * K + 127) / 128, 128, 0, st>>>(kdim, M, nu, K, ev, W, d_z, (double2*)G_out);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess && ritz) e = cudaMemcpyAsync(ritz, ev, sizeof(double) * nu, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess && weight)
+            e = cudaMemcpyAsync(weight, W, sizeof(double) * (size_t)M * nu, cudaMemcpyDeviceToDevice, st);
+        int kd = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&kd, kdim, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess) {
+            if (nu_used) *nu_used = kd;
+            if (seconds) *seconds = ms * 1e-3;
+        }
+    }
+    if (e != cudaSuccess) cudaStreamSynchronize(st);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(base);
+    if (e != cudaSuccess) return cuda_status(e);
     return status;
 }

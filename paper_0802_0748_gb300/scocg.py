@@ -28,7 +28,7 @@ EXPORTED = [
     "scocg_create_csr", "scocg_create_hubbard", "scocg_dim", "scocg_set_opts", "scocg_apply",
     "scocg_solve", "scocg_solve_full", "scocg_grad", "scocg_destroy", "scocg_strerror",
     "scocg_hubbard_tables", "scocg_solve_csr_noalloc", "scocg_solve_multi", "scocg_multi_release",
-    "scocg_density", "scocg_ground_state", "scocg_excite",
+    "scocg_density", "scocg_ground_state", "scocg_excite", "scocg_krylov_sd",
 ]
 
 
@@ -103,6 +103,7 @@ def lib() -> ctypes.CDLL:
         L.scocg_density.argtypes = [P, D, D, D, D, D, I, P, I, P, P, I, D, P, ctypes.POINTER(Info)]
         L.scocg_ground_state.argtypes = [P, P, P, I, I, I, D, ctypes.POINTER(D), ctypes.POINTER(GroundInfo)]
         L.scocg_excite.argtypes = [P, P, I, I, I, P, P]
+        L.scocg_krylov_sd.argtypes = [P, P, I, P, I, P, P, I, P, P, P, ctypes.POINTER(I), ctypes.POINTER(D)]
         L.scocg_destroy.argtypes = [P]
         L.scocg_destroy.restype = None
         L.scocg_strerror.argtypes = [I]
@@ -381,6 +382,42 @@ def scocg_ground_state(h: Handle, v0, m: int = 60, cg_steps: int = 0, max_cycles
     return E.value, psi, {"status": code, "cycles": info.cycles, "lanczos_steps": int(info.lanczos_steps),
                           "cg_steps": int(info.cg_steps), "residual": info.residual, "seconds": info.seconds,
                           "bytes_per_step": info.bytes_per_step}
+
+
+def scocg_krylov_sd(h: Handle, b, nu: int, shifts, proj_idx=None, proj_vec=None):
+    """scocg_krylov_sd: returns (G [nproj][nshift] CUDA complex128, ritz [nu_used]
+    CUDA float64, weight [nproj][nu_used] CUDA float64, info dict).
+
+    b: CUDA float64 [N]; proj_idx: host int [nproj] or proj_vec: CUDA float64
+    [nproj][N]."""
+    import torch
+    if b.dtype != torch.float64 or not b.is_cuda:
+        raise TypeError("b must be a CUDA float64 tensor")
+    b = b.reshape(-1).contiguous()
+    z, zp = _shifts(shifts)
+    K = z.size
+    pidx_p = pvec_p = None
+    keep = None
+    if proj_idx is not None:
+        keep = np.ascontiguousarray(np.asarray(proj_idx, dtype=np.int64).reshape(-1))
+        M = keep.size
+        pidx_p = keep.ctypes.data
+    else:
+        keep = (proj_vec if proj_vec.dim() == 2 else proj_vec.reshape(1, -1)).contiguous()
+        if keep.dtype != torch.float64 or not keep.is_cuda:
+            raise TypeError("proj_vec must be a CUDA float64 tensor")
+        M = keep.shape[0]
+        pvec_p = _dev(keep)
+    G = torch.empty((M, K), dtype=torch.complex128, device=b.device)
+    ritz = torch.zeros(int(nu), dtype=torch.float64, device=b.device)
+    weight = torch.zeros((M, int(nu)), dtype=torch.float64, device=b.device)
+    used = ctypes.c_int()
+    sec = ctypes.c_double()
+    code = lib().scocg_krylov_sd(h.ptr, _dev(b), int(nu), zp, K, pidx_p, pvec_p, M, _dev(G), _dev(ritz), _dev(weight),
+                                 ctypes.byref(used), ctypes.byref(sec))
+    _check(code, "scocg_krylov_sd")
+    k = used.value
+    return G, ritz[:k], weight[:, :k], {"status": code, "nu_used": k, "seconds": sec.value}
 
 
 def scocg_excite(h_from: Handle, h_to: Handle, site: int, spin: int, create: bool, psi):

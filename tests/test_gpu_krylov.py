@@ -1,0 +1,158 @@
+"""Green's functions by subspace diagonalisation in the Krylov subspace
+(Sec. III.B) through the C ABI, against the oracle.
+
+Without reorthogonalization the Lanczos recursion is forward unstable once a
+Ritz value converges: two correct implementations with different rounding
+then place the ghost copies of converged eigenvalues differently.  A
+rounding-level change of b moves G by ~1e-14 up to 40 steps on the 4^3 x 4
+matrix and by 1e-3 at 100 steps, so element-wise parity with the oracle is
+tested at nu <= 40 and larger nu through what holds for any correct
+recursion: the truncated-chain closed form, the dense G once the spectral
+measure of T has converged, the moments b^T H^k b, and sum rules.
+"""
+import numpy as np
+import pytest
+
+from paper_0802_0748_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def S():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0802_0748_gb300 import scocg
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return scocg
+
+
+def csr_handle(S, h):
+    return S.scocg_create_csr(h.rowptr, h.col, h.val)
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def test_chain_closed_form(S):
+    """Open chain of 4,096 sites from its end site: the Lanczos basis is
+    e_0, e_1, ... exactly, so K_nu gives the nu-site chain's G_00 (closed form)."""
+    from oracle import dense
+    h_csr = inputs.chain_csr(4096, t=-1.0)
+    b = np.zeros(h_csr.n); b[0] = 1.0
+    z = np.linspace(-2.5, 2.5, 33) + 0.05j
+    h = csr_handle(S, h_csr)
+    try:
+        G, ritz, w, info = S.scocg_krylov_sd(h, dev(b), 50, z, proj_idx=[0])
+    finally:
+        S.scocg_destroy(h)
+    assert info["nu_used"] == 50
+    assert np.max(np.abs(G.cpu().numpy()[0] - dense.chain_g00_exact(50, -1.0, z))) < 1e-12
+    # the Ritz values of the 50-site chain: 2 cos(pi a / 51)
+    ref = np.sort(-2.0 * np.cos(np.pi * np.arange(1, 51) / 51))
+    assert np.max(np.abs(ritz.cpu().numpy() - ref)) < 1e-13
+
+
+@pytest.mark.parametrize("nu", [12, 40])
+def test_matches_oracle_before_orthogonality_is_lost(S, nu):
+    """4^3 x 4 Anderson matrix (256 rows), random real b, unit and dense
+    projections: G, Ritz values and weights equal the oracle's."""
+    from oracle import ground
+    h_csr = inputs.anderson_csr(4, seed=5)
+    b = inputs.random_unit_real(h_csr.n, 30)
+    C = np.stack([b, np.eye(h_csr.n)[3], inputs.random_unit_real(h_csr.n, 31)])
+    z = np.linspace(-7, 7, 15) + 0.1j
+    ref = ground.krylov_sd(h_csr.scipy(), b, nu, z, C)
+    h = csr_handle(S, h_csr)
+    try:
+        Gd, rd, wd, idn = S.scocg_krylov_sd(h, dev(b), nu, z, proj_vec=dev(C))
+        Gu, ru, wu, iun = S.scocg_krylov_sd(h, dev(b), nu, z, proj_idx=[3])
+    finally:
+        S.scocg_destroy(h)
+    assert idn["nu_used"] == nu and iun["nu_used"] == nu
+    scale = np.max(np.abs(ref.ritz))
+    assert np.max(np.abs(rd.cpu().numpy() - ref.ritz)) < 1e-12 * scale
+    assert np.max(np.abs(Gd.cpu().numpy() - ref.G)) / np.max(np.abs(ref.G)) < 1e-10
+    assert np.max(np.abs(wd.cpu().numpy() - ref.weight)) < 1e-10 * np.max(np.abs(ref.weight))
+    assert np.max(np.abs(Gu.cpu().numpy()[0] - ref.G[1])) / np.max(np.abs(ref.G[1])) < 1e-10
+
+
+def test_converged_measure_equals_dense(S):
+    """108 rows, nu = 2 N (past N steps the ghosts carry the weight): G equals
+    the dense Green's function; with c = b the weights sum to ||b||^2."""
+    from oracle import dense
+    h_csr = inputs.anderson_csr(3, seed=4)
+    b = inputs.random_unit_real(h_csr.n, 21) * 3.0
+    C = np.stack([b, np.eye(h_csr.n)[5]])
+    z = np.linspace(-5, 5, 9) + 0.3j
+    h = csr_handle(S, h_csr)
+    try:
+        G, ritz, w, info = S.scocg_krylov_sd(h, dev(b), 2 * h_csr.n, z, proj_vec=dev(C))
+    finally:
+        S.scocg_destroy(h)
+    ref = dense.green_dense(h_csr.dense(), z, b.astype(np.complex128), C.astype(np.complex128))
+    assert np.max(np.abs(G.cpu().numpy() - ref)) / np.max(np.abs(ref)) < 1e-9
+    assert abs(w.cpu().numpy()[0].sum() - b @ b) < 1e-11 * (b @ b)
+
+
+def test_hubbard_handle_matches_oracle(S, oracle_mod):
+    """Matrix-free Hubbard ring L=8, 3 up 3 down (3,136 states), nu = 30,
+    against the oracle on the sector matrix built from the Fock-space
+    definition."""
+    import scipy.sparse as sp
+    from oracle import ground
+    rowptr, col, val = oracle_mod.hubbard_csr(8, 3, 3, 1.0, 4.0, 1.0, True)
+    n = rowptr.size - 1
+    H = sp.csr_matrix((val, col, rowptr), shape=(n, n))
+    b = inputs.random_unit_real(n, 33)
+    z = np.linspace(-6, 16, 12) + 0.2j
+    ref = ground.krylov_sd(H, b, 30, z, np.stack([b, np.eye(n)[17]]))
+    h = S.scocg_create_hubbard(8, 3, 3, 1.0, 4.0, 1.0, True)
+    try:
+        G, ritz, w, info = S.scocg_krylov_sd(h, dev(b), 30, z, proj_idx=[17])
+        G2, _, _, _ = S.scocg_krylov_sd(h, dev(b), 30, z, proj_vec=dev(b[None, :]))
+    finally:
+        S.scocg_destroy(h)
+    assert np.max(np.abs(G.cpu().numpy()[0] - ref.G[1])) / np.max(np.abs(ref.G[1])) < 1e-10
+    assert np.max(np.abs(G2.cpu().numpy()[0] - ref.G[0])) / np.max(np.abs(ref.G[0])) < 1e-10
+
+
+def test_moments_at_batch_size(S):
+    """The 32^3 x 4 matrix (131,072 rows), nu = 200 from unit vectors e_j: the
+    weights reproduce b^T H^k b for k <= 9 (scipy matvecs), and sum to 1."""
+    h_csr = inputs.anderson_csr(32, seed=1)
+    H = h_csr.scipy()
+    h = csr_handle(S, h_csr)
+    try:
+        for j in (0, 77_777):
+            b = np.zeros(h_csr.n); b[j] = 1.0
+            G, ritz, w, info = S.scocg_krylov_sd(h, dev(b), 200, [0.1j], proj_idx=[j])
+            e = ritz.cpu().numpy(); wt = w.cpu().numpy()[0]
+            assert info["nu_used"] == 200
+            v = b.copy()
+            for k in range(10):
+                mk = float(b @ v)
+                scale = float(np.linalg.norm(v))
+                assert abs(np.sum(wt * e ** k) - mk) < 1e-11 * max(1.0, scale), (j, k)
+                v = H @ v
+    finally:
+        S.scocg_destroy(h)
+
+
+def test_invalid_arguments(S):
+    h_csr = inputs.anderson_csr(3, seed=4)
+    h = csr_handle(S, h_csr)
+    b = dev(inputs.random_unit_real(h_csr.n, 1))
+    try:
+        for kw in ({"nu": 0}, {"nu": 2000}):
+            with pytest.raises(S.ScocgError):
+                S.scocg_krylov_sd(h, b, kw["nu"], [0.1j], proj_idx=[0])
+        with pytest.raises(S.ScocgError):
+            S.scocg_krylov_sd(h, b, 10, [0.1j], proj_idx=[h_csr.n])
+        with pytest.raises(S.ScocgError):
+            S.scocg_krylov_sd(h, torch.zeros_like(b), 10, [0.1j], proj_idx=[0])
+    finally:
+        S.scocg_destroy(h)
