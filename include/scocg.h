@@ -396,7 +396,7 @@ int scocg_excite(scocg_handle from, scocg_handle to, int site, int spin, int cre
  *                *nu_used of each row are written)
  *   nu_used      host int or NULL: Lanczos steps done
  *   seconds      host double or NULL: device time
- * Allocates about (4 N + nu^2 + 2 nproj nu) doubles of device memory per call.
+ * Allocates about (4 N + 6 nu^2 + 2 nproj nu) doubles of device memory per call.
  * Returns SCOCG_OK, SCOCG_ERR_INVALID (also for b = 0), SCOCG_ERR_OOM or
  * SCOCG_ERR_CUDA.
  */

@@ -379,46 +379,52 @@ __global__ void k_tri_evals(const int* kdim, const double* alpha, const double* 
     ev[q] = 0.5 * (lo + hi);
 }
 
-// eigenvectors of T (rows of S, S[q][i]), one thread: inverse iteration at
-// each eigenvalue with T - e_q factorised by Gaussian elimination with
-// partial pivoting; within a cluster (neighbouring eigenvalues closer than
-// 1e-3 ||T||) each iterate is orthogonalised against the cluster's earlier
-// vectors (the ghost copies of converged eigenvalues that the Lanczos
-// recursion produces without reorthogonalization come in such clusters)
+// eigenvectors of T (rows of S, S[q][i]): inverse iteration at each
+// eigenvalue with T - e_q factorised by Gaussian elimination with partial
+// pivoting.  Eigenvalues closer than 1e-3 ||T|| to their neighbour form a
+// cluster (the ghost copies of converged eigenvalues that the Lanczos
+// recursion produces without reorthogonalization come in such clusters);
+// one thread takes a whole cluster, in ascending order, and orthogonalises
+// each iterate against the cluster's earlier vectors.  Clusters are
+// independent, one thread each (the thread of the cluster's first
+// eigenvalue); `work` holds 5 k doubles per thread.
 __global__ void k_tri_evecs(const int* kdim, const double* alpha, const double* beta, const double* ev,
                             const double* scale_p, double* S, double* work) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const int k = *kdim;
+    const int q0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q0 >= k) return;
     const double scale = *scale_p;
+    const double gap = 1e-3 * scale;
+    if (q0 > 0 && ev[q0] - ev[q0 - 1] <= gap) return;          // not the first of its cluster
     const double eps = 2.220446049250313e-16;
     const double tiny = eps * scale + 1e-280;
-    double* U0 = work;
-    double* U1 = work + k;
-    double* U2 = work + 2 * k;
-    double* l = work + 3 * k;
-    double* sw = work + 4 * k;
-    int cl0 = 0;   // first eigenvalue of the current cluster
-    for (int q = 0; q < k; ++q) {
-        if (q > 0 && ev[q] - ev[q - 1] > 1e-3 * scale) cl0 = q;
+    double* U0 = work + (size_t)q0 * 5 * k;   // reciprocal of the pivot after the factorisation
+    double* U1 = U0 + k;
+    double* U2 = U0 + 2 * k;
+    double* l = U0 + 3 * k;
+    double* sw = U0 + 4 * k;
+    for (int q = q0; q < k && (q == q0 || ev[q] - ev[q - 1] <= gap); ++q) {
         // perturb a repeated shift slightly so that the factorisation differs
-        const double th = ev[q] + (q > cl0 ? (q - cl0) * 10.0 * eps * scale : 0.0);
+        const double th = ev[q] + (q - q0) * 10.0 * eps * scale;
         double r0 = alpha[0] - th, r1 = k > 1 ? beta[0] : 0.0, r2 = 0.0;
         for (int i = 0; i + 1 < k; ++i) {
             const double c = beta[i];
             const double d1 = alpha[i + 1] - th, d2 = i + 2 < k ? beta[i + 1] : 0.0;
+            double piv;
             if (fabs(r0) >= fabs(c)) {
                 const double m = r0 != 0.0 ? c / r0 : 0.0;
-                U0[i] = r0; U1[i] = r1; U2[i] = r2; l[i] = m; sw[i] = 0.0;
+                piv = r0; U1[i] = r1; U2[i] = r2; l[i] = m; sw[i] = 0.0;
                 r0 = d1 - m * r1; r1 = d2 - m * r2; r2 = 0.0;
             } else {
                 const double m = r0 / c;
-                U0[i] = c; U1[i] = d1; U2[i] = d2; l[i] = m; sw[i] = 1.0;
+                piv = c; U1[i] = d1; U2[i] = d2; l[i] = m; sw[i] = 1.0;
                 const double n0 = r1 - m * d1, n1 = r2 - m * d2;
                 r0 = n0; r1 = n1; r2 = 0.0;
             }
-            if (fabs(U0[i]) < tiny) U0[i] = U0[i] < 0.0 ? -tiny : tiny;
+            if (fabs(piv) < tiny) piv = piv < 0.0 ? -tiny : tiny;
+            U0[i] = 1.0 / piv;
         }
-        U0[k - 1] = fabs(r0) < tiny ? (r0 < 0.0 ? -tiny : tiny) : r0;
+        U0[k - 1] = 1.0 / (fabs(r0) < tiny ? (r0 < 0.0 ? -tiny : tiny) : r0);
         double* s = S + (size_t)q * k;
         for (int i = 0; i < k; ++i) s[i] = 1.0 + (double)(((i + 3 * q) * 7919) % 13) / 13.0;
         for (int rep = 0; rep < 3; ++rep) {
@@ -430,13 +436,14 @@ __global__ void k_tri_evecs(const int* kdim, const double* alpha, const double* 
                 double v = s[i];
                 if (i + 1 < k) v -= U1[i] * s[i + 1];
                 if (i + 2 < k) v -= U2[i] * s[i + 2];
-                s[i] = v / U0[i];
+                s[i] = v * U0[i];
             }
             double mx = 0.0;
             for (int i = 0; i < k; ++i) mx = fmax(mx, fabs(s[i]));
             if (!(mx > 0.0) || !isfinite(mx)) break;
-            for (int i = 0; i < k; ++i) s[i] /= mx;
-            for (int p = cl0; p < q; ++p) {          // Gram-Schmidt against the cluster
+            const double imx = 1.0 / mx;
+            for (int i = 0; i < k; ++i) s[i] *= imx;
+            for (int p = q0; p < q; ++p) {          // Gram-Schmidt against the cluster
                 const double* sp = S + (size_t)p * k;
                 double dot = 0.0;
                 for (int i = 0; i < k; ++i) dot += sp[i] * s[i];
@@ -444,9 +451,9 @@ __global__ void k_tri_evecs(const int* kdim, const double* alpha, const double* 
             }
             double nr = 0.0;
             for (int i = 0; i < k; ++i) nr += s[i] * s[i];
-            nr = sqrt(nr);
             if (!(nr > 0.0)) break;
-            for (int i = 0; i < k; ++i) s[i] /= nr;
+            const double inr = 1.0 / sqrt(nr);
+            for (int i = 0; i < k; ++i) s[i] *= inr;
         }
     }
 }
@@ -700,7 +707,7 @@ extern "C" int scocg_krylov_sd(scocg_handle h, const double* b, int nu, const sc
         P = (double*)cv.take(sizeof(double) * (size_t)M * nu);
         S = (double*)cv.take(sizeof(double) * (size_t)nu * nu);
         W = (double*)cv.take(sizeof(double) * (size_t)M * nu);
-        work = (double*)cv.take(sizeof(double) * 5 * (size_t)nu);
+        work = (double*)cv.take(sizeof(double) * 5 * (size_t)nu * nu);
         alpha = (double*)cv.take(sizeof(double) * nu);
         beta = (double*)cv.take(sizeof(double) * nu);
         tnorm = (double*)cv.take(sizeof(double) * nu);
@@ -751,8 +758,8 @@ extern "C" int scocg_krylov_sd(scocg_handle h, const double* b, int nu, const sc
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && status == SCOCG_OK) {
-        k_tri_evals<<<(nu + 127) / 128, 128, 0, st>>>(kdim, alpha, beta, ev, scal + 1);
-        k_tri_evecs<<<1, 32, 0, st>>>(kdim, alpha, beta, ev, scal + 1, S, work);
+        k_tri_evals<<<(nu + 31) / 32, 32, 0, st>>>(kdim, alpha, beta, ev, scal + 1);
+        k_tri_evecs<<<(nu + 31) / 32, 32, 0, st>>>(kdim, alpha, beta, ev, scal + 1, S, work);
         k_krylov_weight<<<(M * nu + 127) / 128, 128, 0, st>>>(kdim, M, nu, S, P, scal, W);
         k_krylov_g<<<(M * K + 127) / 128, 128, 0, st>>>(kdim, M, nu, K, ev, W, d_z, (double2*)G_out);
         e = cudaGetLastError();
