@@ -69,6 +69,60 @@ __global__ void __launch_bounds__(kVecBlock) k_csr_hx(int64_t n, const int* rowp
     block_partial(acc, part);
 }
 
+// The same operator on the 4x4-blocked sliced ELL (FP64 blocks): a warp
+// takes a unit of 8 block rows (lane = 4 * block row + row within it); each
+// slot is one contiguous 1 KB line of blocks, of which a lane reads the four
+// values of its row, and the four entries of x of the block's column; four
+// slots are in flight at a time.
+__global__ void __launch_bounds__(kVecBlock) k_bsr4_hx(int64_t nunits, const int* unit_off, const int* bcol,
+                                                       const double* bval, int64_t n, const double* x, double* y,
+                                                       const double* xprev, const double* beta, double sigma,
+                                                       const int* skip, double* part) {
+    if (skip && *skip) return;
+    const int lane = threadIdx.x & 31, br = lane >> 2, rr = lane & 3;
+    const int64_t w0 = (blockIdx.x * (int64_t)kVecBlock + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * kVecBlock) >> 5;
+    const double bp = (xprev && beta) ? *beta : 0.0;
+    double acc = 0.0;
+    for (int64_t u = w0; u < nunits; u += nw) {
+        const int s0 = unit_off[u], s1 = unit_off[u + 1];
+        double hs = 0.0;
+        int s = s0;
+        for (; s < s1; s += 4) {
+            int cb[4];
+            double2 va[4], vb[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                cb[q] = s + q < s1 ? __ldcs(bcol + (size_t)(s + q) * 8 + br) : -1;
+                if (cb[q] >= 0) {
+                    const double2* v = reinterpret_cast<const double2*>(bval + ((size_t)(s + q) * 8 + br) * 16 + rr * 4);
+                    va[q] = __ldcs(v);
+                    vb[q] = __ldcs(v + 1);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (cb[q] < 0) continue;
+                const double2* xp = reinterpret_cast<const double2*>(x + (size_t)cb[q] * 4);
+                const double2 xa = xp[0], xb = xp[1];
+                hs = fma(va[q].x, xa.x, hs);
+                hs = fma(va[q].y, xa.y, hs);
+                hs = fma(vb[q].x, xb.x, hs);
+                hs = fma(vb[q].y, xb.y, hs);
+            }
+        }
+        const int64_t row = u * 32 + lane;
+        if (row < n) {
+            const double xi = x[row];
+            double yi = fma(-sigma, xi, hs);
+            if (xprev) yi = fma(-bp, xprev[row], yi);
+            y[row] = yi;
+            acc = fma(xi, yi, acc);
+        }
+    }
+    block_partial(acc, part);
+}
+
 __device__ __forceinline__ bool lead() { return blockIdx.x == 0 && threadIdx.x == 0; }
 
 #define GRID_STRIDE(i, n) \
@@ -133,6 +187,27 @@ __global__ void __launch_bounds__(kVecBlock) k_lz_next(int64_t n, int j, int m, 
     GRID_STRIDE(i, n) vnext[i] = w[i] * inv;
 }
 
+// Sturm count: the number of eigenvalues of the k x k tridiagonal T below x,
+// = the number of sign changes in the leading principal minors
+// P_i = det(T_i - x), P_0 = 1, P_{i+1} = (a_i - x) P_i - b_{i-1}^2 P_{i-1}
+// (no division, so no FP64 divide per step).  A minor that vanishes (or
+// falls below pivmin |P_i|) is replaced by -pivmin P_i, like a tiny negative
+// pivot; both minors are rescaled by 2^-600 / 2^600 to stay in range.
+__device__ int tri_count_below(const double* a, const double* b, int k, double x, double pivmin) {
+    int c = 0;
+    double pm = 0.0, p = 1.0;   // P_{i-1}, P_i
+    for (int i = 0; i < k; ++i) {
+        double pn = fma(a[i] - x, p, i > 0 ? -(b[i - 1] * b[i - 1]) * pm : 0.0);
+        if (fabs(pn) <= pivmin * fabs(p)) pn = -pivmin * p;
+        if ((pn < 0.0) != (p < 0.0)) ++c;
+        pm = p;
+        p = pn;
+        if (fabs(p) > 0x1p600) { p *= 0x1p-600; pm *= 0x1p-600; }
+        else if (fabs(p) < 0x1p-600 && fabs(pm) < 0x1p-600) { p *= 0x1p600; pm *= 0x1p600; }
+    }
+    return c;
+}
+
 // Lowest eigenpair of the k x k tridiagonal T (alpha on the diagonal, beta
 // off it), one warp: multisection on the Sturm count (negative pivots of the
 // LDL^T factorisation of T - x) inside the Gershgorin interval, 32 points per
@@ -157,16 +232,7 @@ __global__ void k_tri_lowest(const int* kdim, const double* alpha, const double*
     const double pivmin = eps * scale * 1e-3 + 1e-300;
     lo -= 2.0 * eps * scale + pivmin;
     hi += 2.0 * eps * scale + pivmin;
-    auto count_below = [&](double x) {
-        int c = 0;
-        double d = 1.0;
-        for (int i = 0; i < k; ++i) {
-            d = (a[i] - x) - (i > 0 ? b[i - 1] * (b[i - 1] / d) : 0.0);
-            if (fabs(d) < pivmin) d = -pivmin;
-            if (d < 0.0) ++c;
-        }
-        return c;
-    };
+    auto count_below = [&](double x) { return tri_count_below(a, b, k, x, pivmin); };
     // invariant: no eigenvalue below lo, at least one below hi (the same on every lane)
     for (int it = 0; it < 64 && hi - lo > 2.0 * eps * fmax(fabs(lo), fabs(hi)) + pivmin; ++it) {
         const double x = lo + (hi - lo) * ((double)(lane + 1) / 33.0);
@@ -342,23 +408,14 @@ __global__ void __launch_bounds__(kVecBlock) k_proj_fin(const double* part, int 
     if (threadIdx.x == 0) P[(size_t)blockIdx.x * nu + j] = s;
 }
 
-// Sturm count: eigenvalues of the k x k tridiagonal below x
-__device__ int tri_count_below(const double* a, const double* b, int k, double x, double pivmin) {
-    int c = 0;
-    double d = 1.0;
-    for (int i = 0; i < k; ++i) {
-        d = (a[i] - x) - (i > 0 ? b[i - 1] * (b[i - 1] / d) : 0.0);
-        if (fabs(d) < pivmin) d = -pivmin;
-        if (d < 0.0) ++c;
-    }
-    return c;
-}
-
-// eigenvalue q (ascending) of T, one thread each: bisection on the Sturm count
-// inside the Gershgorin interval
+// eigenvalue q (ascending) of T, one warp each: multisection on the Sturm
+// count inside the Gershgorin interval, 32 points per round (each lane counts
+// at one point), keeping "fewer than q + 1 eigenvalues below lo, at least
+// q + 1 below hi"
 __global__ void k_tri_evals(const int* kdim, const double* alpha, const double* beta, double* ev, double* scale_out) {
     const int k = *kdim;
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int q = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     double lo = INFINITY, hi = -INFINITY;
     for (int i = 0; i < k; ++i) {
         const double r = (i > 0 ? fabs(beta[i - 1]) : 0.0) + (i + 1 < k ? fabs(beta[i]) : 0.0);
@@ -366,17 +423,22 @@ __global__ void k_tri_evals(const int* kdim, const double* alpha, const double* 
         hi = fmax(hi, alpha[i] + r);
     }
     const double scale = fmax(fmax(fabs(lo), fabs(hi)), 1e-300);
-    if (q == 0 && scale_out) *scale_out = scale;
+    if (q == 0 && lane == 0 && scale_out) *scale_out = scale;
     if (q >= k) return;
     const double eps = 2.220446049250313e-16;
     const double pivmin = eps * scale * 1e-3 + 1e-300;
     lo -= 2.0 * eps * scale + pivmin;
     hi += 2.0 * eps * scale + pivmin;
-    for (int it = 0; it < 200 && hi - lo > 2.0 * eps * fmax(fabs(lo), fabs(hi)) + pivmin; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (tri_count_below(alpha, beta, k, mid, pivmin) >= q + 1) hi = mid; else lo = mid;
+    for (int it = 0; it < 64 && hi - lo > 2.0 * eps * fmax(fabs(lo), fabs(hi)) + pivmin; ++it) {
+        const double x = lo + (hi - lo) * ((double)(lane + 1) / 33.0);
+        const unsigned above = __ballot_sync(0xffffffffu, tri_count_below(alpha, beta, k, x, pivmin) >= q + 1);
+        const int f = above ? __ffs(above) - 1 : 32;
+        const double xf = __shfl_sync(0xffffffffu, x, f < 32 ? f : 31);
+        const double xp = __shfl_sync(0xffffffffu, x, f > 0 ? f - 1 : 0);
+        if (f == 32) lo = xf;
+        else { hi = xf; if (f > 0) lo = xp; }
     }
-    ev[q] = 0.5 * (lo + hi);
+    if (lane == 0) ev[q] = 0.5 * (lo + hi);
 }
 
 // eigenvectors of T (rows of S, S[q][i]): inverse iteration at each
@@ -512,10 +574,30 @@ struct GroundScalars {
 
 }  // namespace
 
+// Blocks of the operator launch (= its partials): the Hubbard operator is
+// FP64 bound and takes the vector grid; the CSR operator is bound by its
+// dependent index -> gather loads and takes one 8-lane group per row (up to
+// 32 blocks per SM), so every row's loads are in flight at once.
+static bool use_bsr(const scocg_ctx* h) {
+    return h->kind == HandleKind::kCsr && h->bsr_ok && h->d_bval64 && h->d_unit_off && h->d_bcol;
+}
+
+static int apply_grid(const scocg_ctx* h, int G) {
+    if (h->kind == HandleKind::kHubbard) return G;
+    const int64_t want = use_bsr(h) ? (h->nunits_bsr * 32 + kVecBlock - 1) / kVecBlock
+                                    : (h->n * 8 + kVecBlock - 1) / kVecBlock;
+    return (int)std::max<int64_t>(G, std::min<int64_t>(want, 32LL * h->num_sms));
+}
+
 // Real FP64 operator of the handle: y = (H - sigma) x - beta x_prev, partial of x^T y.
 static cudaError_t hx(scocg_ctx* h, const double* x, double* y, const double* xprev, const double* beta,
                       double sigma, const int* skip, double* part, int G) {
     if (h->kind == HandleKind::kHubbard) return hubbard_hx(h->hub, x, y, xprev, beta, sigma, skip, part, G, h->stream);
+    if (use_bsr(h)) {
+        k_bsr4_hx<<<G, kVecBlock, 0, h->stream>>>(h->nunits_bsr, h->d_unit_off, h->d_bcol, h->d_bval64, h->n, x, y,
+                                                   xprev, beta, sigma, skip, part);
+        return cudaGetLastError();
+    }
     k_csr_hx<<<G, kVecBlock, 0, h->stream>>>(h->n, h->d_rowptr, h->d_col, h->d_val64, x, y, xprev, beta, sigma, skip,
                                               part);
     return cudaGetLastError();
@@ -545,6 +627,7 @@ extern "C" int scocg_ground_state(scocg_handle h, const double* v0, double* psi_
     if (n < 1) return SCOCG_ERR_INVALID;
     const int G = (int)std::max<int64_t>(1, std::min<int64_t>((n + kVecBlock - 1) / kVecBlock, 8LL * h->num_sms));
     const int mm = (int)std::min<int64_t>(m, n);   // at most n Lanczos vectors are independent
+    const int Gh = apply_grid(h, G);               // blocks (partials) of the operator launches
     // device memory: V[mm][n], w, psi, y, r, p and the scalars
     Carver cv{nullptr, 0};
     for (int pass = 0; pass < 2; ++pass) {
@@ -555,7 +638,7 @@ extern "C" int scocg_ground_state(scocg_handle h, const double* v0, double* psi_
         }
         cv.take(sizeof(double) * (size_t)mm * n);
         for (int v = 0; v < 5; ++v) cv.take(sizeof(double) * n);
-        cv.take(sizeof(double) * (9 * (size_t)mm + 4 + 2 * (size_t)G + cg_steps + 1));
+        cv.take(sizeof(double) * (9 * (size_t)mm + 4 + 2 * (size_t)Gh + cg_steps + 1));
         cv.take(sizeof(int) * ((size_t)mm + 3 + 2 * (size_t)cg_steps + 1));
     }
     char* base = cv.base;
@@ -568,9 +651,9 @@ extern "C" int scocg_ground_state(scocg_handle h, const double* v0, double* psi_
     double* p = (double*)cv.take(sizeof(double) * n);
     GroundScalars S;
     {
-        double* d = (double*)cv.take(sizeof(double) * (9 * (size_t)mm + 4 + 2 * (size_t)G + cg_steps + 1));
+        double* d = (double*)cv.take(sizeof(double) * (9 * (size_t)mm + 4 + 2 * (size_t)Gh + cg_steps + 1));
         S.alpha = d; S.beta = d + mm; S.tnorm = d + 2 * mm; S.s = d + 3 * mm; S.work = d + 4 * mm;
-        S.scal = d + 9 * mm; S.part = S.scal + 4; S.part2 = S.part + G; S.rr = S.part2 + G;
+        S.scal = d + 9 * mm; S.part = S.scal + 4; S.part2 = S.part + Gh; S.rr = S.part2 + Gh;
         int* q = (int*)cv.take(sizeof(int) * ((size_t)mm + 3 + 2 * (size_t)cg_steps + 1));
         S.stop = q; S.kdim = q + mm + 1; S.ok = S.kdim + 1; S.cgstop = S.ok + 1; S.cgbrk = S.cgstop + cg_steps + 1;
     }
@@ -602,9 +685,9 @@ extern "C" int scocg_ground_state(scocg_handle h, const double* v0, double* psi_
         if (e == cudaSuccess) e = cudaMemcpyAsync(S.kdim, &mm_v, sizeof(int), cudaMemcpyHostToDevice, st);
         for (int j = 0; j < mm && e == cudaSuccess; ++j) {
             const double* vj = V + (size_t)j * n;
-            e = hx(h, vj, w, j ? vj - n : nullptr, j ? S.beta + j - 1 : nullptr, 0.0, S.stop + j, S.part, G);
+            e = hx(h, vj, w, j ? vj - n : nullptr, j ? S.beta + j - 1 : nullptr, 0.0, S.stop + j, S.part, Gh);
             if (e != cudaSuccess) break;
-            k_lz_ortho<<<G, kVecBlock, 0, st>>>(n, j, vj, w, S.part, G, S.stop, S.alpha, S.part2);
+            k_lz_ortho<<<G, kVecBlock, 0, st>>>(n, j, vj, w, S.part, Gh, S.stop, S.alpha, S.part2);
             k_lz_next<<<G, kVecBlock, 0, st>>>(n, j, mm, w, j + 1 < mm ? V + (size_t)(j + 1) * n : w, S.part2, G,
                                                S.alpha, S.beta, S.tnorm, S.stop, S.kdim);
             e = cudaGetLastError();
@@ -613,9 +696,9 @@ extern "C" int scocg_ground_state(scocg_handle h, const double* v0, double* psi_
         k_tri_lowest<<<1, 32, 0, st>>>(S.kdim, S.alpha, S.beta, S.s, S.work, S.scal);
         k_ritz<<<G, kVecBlock, 0, st>>>(n, S.kdim, S.s, V, w, S.part);
         k_scale_to<<<G, kVecBlock, 0, st>>>(n, w, psi, S.part, G, S.ok);
-        e = hx(h, psi, w, nullptr, nullptr, 0.0, nullptr, S.part, G);
+        e = hx(h, psi, w, nullptr, nullptr, 0.0, nullptr, S.part, Gh);
         if (e != cudaSuccess) break;
-        k_resid<<<G, kVecBlock, 0, st>>>(n, psi, w, S.part, G, S.part2, S.scal + 1);
+        k_resid<<<G, kVecBlock, 0, st>>>(n, psi, w, S.part, Gh, S.part2, S.scal + 1);
         k_sum_store<<<1, kVecBlock, 0, st>>>(S.part2, G, S.scal + 2, 1);
         double sc[3];
         int kd = 0;
@@ -636,9 +719,9 @@ extern "C" int scocg_ground_state(scocg_handle h, const double* v0, double* psi_
         k_sum_store<<<1, kVecBlock, 0, st>>>(S.part, G, S.rr, 0);
         e = cudaMemsetAsync(S.cgstop, 0, sizeof(int) * (2 * (size_t)cg_steps + 1), st);
         for (int s = 0; s < cg_steps && e == cudaSuccess; ++s) {
-            e = hx(h, p, w, nullptr, nullptr, sigma, S.cgstop + s, S.part, G);
+            e = hx(h, p, w, nullptr, nullptr, sigma, S.cgstop + s, S.part, Gh);
             if (e != cudaSuccess) break;
-            k_cg_xr<<<G, kVecBlock, 0, st>>>(n, s, y, r, p, w, S.part, G, S.rr, S.cgstop, S.cgbrk, S.part2);
+            k_cg_xr<<<G, kVecBlock, 0, st>>>(n, s, y, r, p, w, S.part, Gh, S.rr, S.cgstop, S.cgbrk, S.part2);
             k_cg_p<<<G, kVecBlock, 0, st>>>(n, s, r, p, S.part2, G, S.rr, S.cgstop, S.cgbrk);
             e = cudaGetLastError();
         }
@@ -691,6 +774,7 @@ extern "C" int scocg_krylov_sd(scocg_handle h, const double* b, int nu, const sc
             if (proj_idx[m] < 0 || proj_idx[m] >= n) return SCOCG_ERR_INVALID;
     const int G = (int)std::max<int64_t>(1, std::min<int64_t>((n + kVecBlock - 1) / kVecBlock, 8LL * h->num_sms));
     const int M = nproj, K = nshift;
+    const int Gh = apply_grid(h, G);
     Carver cv{nullptr, 0};
     double *vb[3], *w, *P, *S, *W, *work, *alpha, *beta, *tnorm, *ev, *scal, *part, *part2, *partM;
     int *stop, *kdim;
@@ -713,7 +797,7 @@ extern "C" int scocg_krylov_sd(scocg_handle h, const double* b, int nu, const sc
         tnorm = (double*)cv.take(sizeof(double) * nu);
         ev = (double*)cv.take(sizeof(double) * nu);
         scal = (double*)cv.take(sizeof(double) * 4);
-        part = (double*)cv.take(sizeof(double) * G);
+        part = (double*)cv.take(sizeof(double) * Gh);
         part2 = (double*)cv.take(sizeof(double) * G);
         partM = (double*)cv.take(sizeof(double) * (size_t)M * G);
         stop = (int*)cv.take(sizeof(int) * (nu + 1));
@@ -751,14 +835,14 @@ extern "C" int scocg_krylov_sd(scocg_handle h, const double* b, int nu, const sc
             k_proj_dense<<<G, kVecBlock, 0, st>>>(n, M, proj_vec, vj, partM, G, stop, j);
             k_proj_fin<<<M, kVecBlock, 0, st>>>(partM, G, P, nu, j, stop);
         }
-        e = hx(h, vj, w, j ? vb[(j + 2) % 3] : nullptr, j ? beta + j - 1 : nullptr, 0.0, stop + j, part, G);
+        e = hx(h, vj, w, j ? vb[(j + 2) % 3] : nullptr, j ? beta + j - 1 : nullptr, 0.0, stop + j, part, Gh);
         if (e != cudaSuccess) break;
-        k_lz_ortho<<<G, kVecBlock, 0, st>>>(n, j, vj, w, part, G, stop, alpha, part2);
+        k_lz_ortho<<<G, kVecBlock, 0, st>>>(n, j, vj, w, part, Gh, stop, alpha, part2);
         k_lz_next<<<G, kVecBlock, 0, st>>>(n, j, nu, w, vb[(j + 1) % 3], part2, G, alpha, beta, tnorm, stop, kdim);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && status == SCOCG_OK) {
-        k_tri_evals<<<(nu + 31) / 32, 32, 0, st>>>(kdim, alpha, beta, ev, scal + 1);
+        k_tri_evals<<<(nu + 3) / 4, 128, 0, st>>>(kdim, alpha, beta, ev, scal + 1);
         k_tri_evecs<<<(nu + 31) / 32, 32, 0, st>>>(kdim, alpha, beta, ev, scal + 1, S, work);
         k_krylov_weight<<<(M * nu + 127) / 128, 128, 0, st>>>(kdim, M, nu, S, P, scal, W);
         k_krylov_g<<<(M * K + 127) / 128, 128, 0, st>>>(kdim, M, nu, K, ev, W, d_z, (double2*)G_out);
