@@ -69,48 +69,60 @@ __global__ void __launch_bounds__(kVecBlock) k_csr_hx(int64_t n, const int* rowp
     block_partial(acc, part);
 }
 
-// The same operator on the 4x4-blocked sliced ELL (FP64 blocks): a warp
-// takes a unit of 8 block rows (lane = 4 * block row + row within it); each
-// slot is one contiguous 1 KB line of blocks, of which a lane reads the four
-// values of its row, and the four entries of x of the block's column; four
-// slots are in flight at a time.
+__device__ __forceinline__ bool lead() { return blockIdx.x == 0 && threadIdx.x == 0; }
+
+#define GRID_STRIDE(i, n) \
+    for (int64_t i = blockIdx.x * (int64_t)kVecBlock + threadIdx.x; i < (n); i += (int64_t)gridDim.x * kVecBlock)
+
+// (H x) for the rows of one unit of the 4x4-blocked sliced ELL (FP64 blocks):
+// a warp takes a unit of 8 block rows (lane = 4 * block row + row within it);
+// each slot is one contiguous 1 KB line of blocks, of which a lane reads the
+// four values of its row, and the four entries of x of the block's column;
+// four slots are in flight at a time.
+__device__ __forceinline__ double bsr4_row(int64_t u, int lane, const int* unit_off, const int* bcol,
+                                           const double* bval, const double* x) {
+    const int br = lane >> 2, rr = lane & 3;
+    const int s0 = unit_off[u], s1 = unit_off[u + 1];
+    double hs = 0.0;
+    for (int s = s0; s < s1; s += 4) {
+        int cb[4];
+        double2 va[4], vb[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            cb[q] = s + q < s1 ? __ldcs(bcol + (size_t)(s + q) * 8 + br) : -1;
+            if (cb[q] >= 0) {
+                const double2* v = reinterpret_cast<const double2*>(bval + ((size_t)(s + q) * 8 + br) * 16 + rr * 4);
+                va[q] = __ldcs(v);
+                vb[q] = __ldcs(v + 1);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (cb[q] < 0) continue;
+            const double2* xp = reinterpret_cast<const double2*>(x + (size_t)cb[q] * 4);
+            const double2 xa = xp[0], xb = xp[1];
+            hs = fma(va[q].x, xa.x, hs);
+            hs = fma(va[q].y, xa.y, hs);
+            hs = fma(vb[q].x, xb.x, hs);
+            hs = fma(vb[q].y, xb.y, hs);
+        }
+    }
+    return hs;
+}
+
+// The operator of k_csr_hx on the 4x4-blocked layout.
 __global__ void __launch_bounds__(kVecBlock) k_bsr4_hx(int64_t nunits, const int* unit_off, const int* bcol,
                                                        const double* bval, int64_t n, const double* x, double* y,
                                                        const double* xprev, const double* beta, double sigma,
                                                        const int* skip, double* part) {
     if (skip && *skip) return;
-    const int lane = threadIdx.x & 31, br = lane >> 2, rr = lane & 3;
+    const int lane = threadIdx.x & 31;
     const int64_t w0 = (blockIdx.x * (int64_t)kVecBlock + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * kVecBlock) >> 5;
     const double bp = (xprev && beta) ? *beta : 0.0;
     double acc = 0.0;
     for (int64_t u = w0; u < nunits; u += nw) {
-        const int s0 = unit_off[u], s1 = unit_off[u + 1];
-        double hs = 0.0;
-        int s = s0;
-        for (; s < s1; s += 4) {
-            int cb[4];
-            double2 va[4], vb[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                cb[q] = s + q < s1 ? __ldcs(bcol + (size_t)(s + q) * 8 + br) : -1;
-                if (cb[q] >= 0) {
-                    const double2* v = reinterpret_cast<const double2*>(bval + ((size_t)(s + q) * 8 + br) * 16 + rr * 4);
-                    va[q] = __ldcs(v);
-                    vb[q] = __ldcs(v + 1);
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (cb[q] < 0) continue;
-                const double2* xp = reinterpret_cast<const double2*>(x + (size_t)cb[q] * 4);
-                const double2 xa = xp[0], xb = xp[1];
-                hs = fma(va[q].x, xa.x, hs);
-                hs = fma(va[q].y, xa.y, hs);
-                hs = fma(vb[q].x, xb.x, hs);
-                hs = fma(vb[q].y, xb.y, hs);
-            }
-        }
+        const double hs = bsr4_row(u, lane, unit_off, bcol, bval, x);
         const int64_t row = u * 32 + lane;
         if (row < n) {
             const double xi = x[row];
@@ -123,10 +135,101 @@ __global__ void __launch_bounds__(kVecBlock) k_bsr4_hx(int64_t nunits, const int
     block_partial(acc, part);
 }
 
-__device__ __forceinline__ bool lead() { return blockIdx.x == 0 && threadIdx.x == 0; }
+// KR-SD's Lanczos recursion in one cooperative launch (4x4-blocked layout,
+// unit projections), two grid barriers per step.  With w_{-1} = b and
+// beta_{-1} = ||b||, step j forms v_j = w_{j-1} / beta_{j-1} on the fly:
+//   phase 1: w_j = (H w_{j-1}) / beta_{j-1} - beta_{j-1} v_{j-1} and
+//            v_j for the own rows, partial of v_j^T w_j; CTA 0 records
+//            c_m^T v_j = w_{j-1}[idx_m] / beta_{j-1}
+//   barrier; alpha_j = sum of the partials (same order in every CTA)
+//   phase 2: w_j -= alpha_j v_j, partial of ||w_j||^2
+//   barrier; beta_j = sqrt(sum); the recursion ends after step j when
+//            j + 1 = nu or beta_j <= 1e-12 max_i(|alpha_i| + beta_i + beta_{i-1})
+// A row is always handled by the warp of its unit; v and w alternate between
+// two buffers each, so a buffer is rewritten only after the barrier that ends
+// every gather of its old contents.  Waits are bounded (GridSync timeout).
+struct KrylovArgs {
+    int64_t n, nunits;
+    const int* unit_off;
+    const int* bcol;
+    const double* bval;
+    const double* b;
+    double* V[2];
+    double* W[2];
+    int nu, M;
+    const int64_t* idx;
+    double* P;
+    double* alpha;
+    double* beta;
+    int* kdim;
+    double* part_a;   // partials of v_j^T w_j
+    double* part_b;   // partials of ||b||^2, then of ||w_j||^2
+    GridSync sync;
+};
 
-#define GRID_STRIDE(i, n) \
-    for (int64_t i = blockIdx.x * (int64_t)kVecBlock + threadIdx.x; i < (n); i += (int64_t)gridDim.x * kVecBlock)
+__global__ void __launch_bounds__(kVecBlock) k_krylov_lanczos(KrylovArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int G = gridDim.x;
+    const int64_t w0 = (blockIdx.x * (int64_t)kVecBlock + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)G * kVecBlock) >> 5;
+    unsigned long long epoch = 0;
+    // ||b||
+    double acc = 0.0;
+    GRID_STRIDE(i, a.n) acc = fma(a.b[i], a.b[i], acc);
+    block_partial(acc, a.part_b);
+    if (!grid_barrier(a.sync, epoch)) return;
+    double bprev = sqrt(sum_partials(a.part_b, G));   // beta_{j-1}
+    double tn = 0.0;
+    const double* wprev = a.b;
+    for (int j = 0; j < a.nu; ++j) {
+        double* vcur = a.V[j & 1];
+        const double* vprev = a.V[(j + 1) & 1];
+        double* wcur = a.W[j & 1];
+        const double inv = 1.0 / bprev;
+        if (blockIdx.x == 0 && threadIdx.x < a.M) a.P[(size_t)threadIdx.x * a.nu + j] = wprev[a.idx[threadIdx.x]] * inv;
+        acc = 0.0;
+        for (int64_t u = w0; u < a.nunits; u += nw) {
+            const double hs = bsr4_row(u, lane, a.unit_off, a.bcol, a.bval, wprev);
+            const int64_t row = u * 32 + lane;
+            if (row < a.n) {
+                const double vi = wprev[row] * inv;
+                double wi = hs * inv;
+                if (j > 0) wi = fma(-bprev, vprev[row], wi);
+                vcur[row] = vi;
+                wcur[row] = wi;
+                acc = fma(vi, wi, acc);
+            }
+        }
+        block_partial(acc, a.part_a);
+        if (!grid_barrier(a.sync, epoch)) return;
+        const double al = sum_partials(a.part_a, G);
+        acc = 0.0;
+        for (int64_t u = w0; u < a.nunits; u += nw) {
+            const int64_t row = u * 32 + lane;
+            if (row < a.n) {
+                const double wi = fma(-al, vcur[row], wcur[row]);
+                wcur[row] = wi;
+                acc = fma(wi, wi, acc);
+            }
+        }
+        // part_b is read after the next barrier and rewritten only after the
+        // first barrier of the next step, by which time every CTA has read it
+        block_partial(acc, a.part_b);
+        if (!grid_barrier(a.sync, epoch)) return;
+        const double be = sqrt(sum_partials(a.part_b, G));
+        tn = fmax(tn, fabs(al) + be + (j > 0 ? bprev : 0.0));
+        const bool end = (j + 1 == a.nu) || !(be > 1e-12 * tn);
+        if (lead()) {
+            a.alpha[j] = al;
+            a.beta[j] = be;
+            if (end) *a.kdim = j + 1;
+        }
+        if (end) break;
+        bprev = be;
+        wprev = wcur;
+    }
+}
+
 
 // partial of x^T x
 __global__ void __launch_bounds__(kVecBlock) k_norm_part(int64_t n, const double* x, double* part) {
@@ -774,7 +877,17 @@ extern "C" int scocg_krylov_sd(scocg_handle h, const double* b, int nu, const sc
             if (proj_idx[m] < 0 || proj_idx[m] >= n) return SCOCG_ERR_INVALID;
     const int G = (int)std::max<int64_t>(1, std::min<int64_t>((n + kVecBlock - 1) / kVecBlock, 8LL * h->num_sms));
     const int M = nproj, K = nshift;
-    const int Gh = apply_grid(h, G);
+    int Gh = apply_grid(h, G);
+    // one cooperative launch for the whole recursion when the layout allows it
+    int Gp = 0;
+    if (use_bsr(h) && proj_idx) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_krylov_lanczos, kVecBlock, 0) == cudaSuccess && nb > 0)
+            Gp = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nb * h->num_sms,
+                                                             (h->nunits_bsr * 32 + kVecBlock - 1) / kVecBlock));
+        cudaGetLastError();
+        Gh = std::max(Gh, Gp);
+    }
     Carver cv{nullptr, 0};
     double *vb[3], *w, *P, *S, *W, *work, *alpha, *beta, *tnorm, *ev, *scal, *part, *part2, *partM;
     int *stop, *kdim;
@@ -798,7 +911,7 @@ extern "C" int scocg_krylov_sd(scocg_handle h, const double* b, int nu, const sc
         ev = (double*)cv.take(sizeof(double) * nu);
         scal = (double*)cv.take(sizeof(double) * 4);
         part = (double*)cv.take(sizeof(double) * Gh);
-        part2 = (double*)cv.take(sizeof(double) * G);
+        part2 = (double*)cv.take(sizeof(double) * Gh);
         partM = (double*)cv.take(sizeof(double) * (size_t)M * G);
         stop = (int*)cv.take(sizeof(int) * (nu + 1));
         kdim = (int*)cv.take(sizeof(int));
@@ -827,7 +940,25 @@ extern "C" int scocg_krylov_sd(scocg_handle h, const double* b, int nu, const sc
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e == cudaSuccess && !ok) status = SCOCG_ERR_INVALID;
     }
-    for (int j = 0; j < nu && e == cudaSuccess && status == SCOCG_OK; ++j) {
+    if (Gp > 0 && e == cudaSuccess && status == SCOCG_OK) {
+        KrylovArgs ka;
+        ka.n = n; ka.nunits = h->nunits_bsr;
+        ka.unit_off = h->d_unit_off; ka.bcol = h->d_bcol; ka.bval = h->d_bval64;
+        ka.b = b;
+        ka.V[0] = vb[0]; ka.V[1] = vb[1]; ka.W[0] = vb[2]; ka.W[1] = w;
+        ka.nu = nu; ka.M = M; ka.idx = d_idx; ka.P = P;
+        ka.alpha = alpha; ka.beta = beta; ka.kdim = kdim;
+        ka.part_a = part; ka.part_b = part2;
+        ka.sync.count = &h->d_ctrl->count;
+        ka.sync.status = &h->d_ctrl->status;
+        ka.sync.timeout_ns = (uint64_t)(h->opts.timeout_ms * 1e6);
+        ka.sync.nctas = Gp;
+        e = cudaMemsetAsync(h->d_ctrl, 0, sizeof(Ctrl), st);
+        void* args[] = {(void*)&ka};
+        if (e == cudaSuccess)
+            e = cudaLaunchCooperativeKernel((const void*)k_krylov_lanczos, dim3(Gp), dim3(kVecBlock), args, 0, st);
+    }
+    for (int j = 0; Gp == 0 && j < nu && e == cudaSuccess && status == SCOCG_OK; ++j) {
         const double* vj = vb[j % 3];
         if (proj_idx) {
             k_proj_unit<<<(M + 63) / 64, 64, 0, st>>>(M, d_idx, vj, P, nu, j, stop);
@@ -851,9 +982,11 @@ extern "C" int scocg_krylov_sd(scocg_handle h, const double* b, int nu, const sc
         if (e == cudaSuccess && ritz) e = cudaMemcpyAsync(ritz, ev, sizeof(double) * nu, cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess && weight)
             e = cudaMemcpyAsync(weight, W, sizeof(double) * (size_t)M * nu, cudaMemcpyDeviceToDevice, st);
-        int kd = 0;
+        int kd = 0, bar = 0;
         if (e == cudaSuccess) e = cudaMemcpyAsync(&kd, kdim, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && Gp > 0) e = cudaMemcpyAsync(&bar, &h->d_ctrl->status, sizeof(int), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess && bar < 0) status = bar;   // a grid barrier gave up (SCOCG_ERR_TIMEOUT)
         float ms = 0.0f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
         if (e == cudaSuccess) {

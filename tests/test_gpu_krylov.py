@@ -142,6 +142,29 @@ def test_moments_at_batch_size(S):
         S.scocg_destroy(h)
 
 
+def test_one_launch_recursion_equals_launch_per_step(S):
+    """Unit projections on the 4x4-blocked layout run the whole recursion in
+    one cooperative launch; forcing the plain CSR layout runs one launch per
+    operation.  Same G, Ritz values and weights (nu = 30, before orthogonality
+    is lost), on the 8^3 x 4 matrix (2,048 rows, several CTAs)."""
+    h_csr = inputs.anderson_csr(8, seed=9)
+    b = inputs.random_unit_real(h_csr.n, 40)
+    z = np.linspace(-7, 7, 21) + 0.05j
+    out = []
+    for layout in (0, 1):
+        h = S.scocg_create_csr(h_csr.rowptr, h_csr.col, h_csr.val, opts=S.SolveOptions(layout=layout))
+        try:
+            G, r, w, info = S.scocg_krylov_sd(h, dev(b), 30, z, proj_idx=[1, 700])
+        finally:
+            S.scocg_destroy(h)
+        assert info["nu_used"] == 30
+        out.append((G.cpu().numpy(), r.cpu().numpy(), w.cpu().numpy()))
+    (G0, r0, w0), (G1, r1, w1) = out
+    assert np.max(np.abs(r0 - r1)) < 1e-12 * np.max(np.abs(r1))
+    assert np.max(np.abs(G0 - G1)) < 1e-10 * np.max(np.abs(G1))
+    assert np.max(np.abs(w0 - w1)) < 1e-10 * np.max(np.abs(w1))
+
+
 def test_invalid_arguments(S):
     h_csr = inputs.anderson_csr(3, seed=4)
     h = csr_handle(S, h_csr)
