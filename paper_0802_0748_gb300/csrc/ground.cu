@@ -682,7 +682,8 @@ struct GroundScalars {
 // dependent index -> gather loads and takes one 8-lane group per row (up to
 // 32 blocks per SM), so every row's loads are in flight at once.
 static bool use_bsr(const scocg_ctx* h) {
-    return h->kind == HandleKind::kCsr && h->bsr_ok && h->d_bval64 && h->d_unit_off && h->d_bcol;
+    return h->kind == HandleKind::kCsr && h->bsr_ok && h->opts.layout != 1 && h->d_bval64 && h->d_unit_off &&
+           h->d_bcol;
 }
 
 static int apply_grid(const scocg_ctx* h, int G) {
