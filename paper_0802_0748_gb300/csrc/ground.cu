@@ -173,19 +173,29 @@ __global__ void __launch_bounds__(kVecBlock) k_krylov_lanczos(KrylovArgs a) {
     const int64_t w0 = (blockIdx.x * (int64_t)kVecBlock + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)G * kVecBlock) >> 5;
     unsigned long long epoch = 0;
+    // step scalars: roots and divisions by thread 0 only, broadcast through
+    // shared memory (done by every thread they would load the FP64 pipe with
+    // as many instructions as the operator itself)
+    __shared__ double s_bprev, s_inv;
+    __shared__ int s_end;
+    double tn = 0.0;   // thread 0's running max of |alpha_i| + beta_i + beta_{i-1}
     // ||b||
     double acc = 0.0;
     GRID_STRIDE(i, a.n) acc = fma(a.b[i], a.b[i], acc);
     block_partial(acc, a.part_b);
     if (!grid_barrier(a.sync, epoch)) return;
-    double bprev = sqrt(sum_partials(a.part_b, G));   // beta_{j-1}
-    double tn = 0.0;
+    {
+        const double s0 = sum_partials(a.part_b, G);
+        if (threadIdx.x == 0) { s_bprev = sqrt(s0); s_inv = 1.0 / s_bprev; }
+        __syncthreads();
+    }
     const double* wprev = a.b;
     for (int j = 0; j < a.nu; ++j) {
         double* vcur = a.V[j & 1];
         const double* vprev = a.V[(j + 1) & 1];
         double* wcur = a.W[j & 1];
-        const double inv = 1.0 / bprev;
+        const double bprev = s_bprev;   // beta_{j-1}
+        const double inv = s_inv;
         if (blockIdx.x == 0 && threadIdx.x < a.M) a.P[(size_t)threadIdx.x * a.nu + j] = wprev[a.idx[threadIdx.x]] * inv;
         acc = 0.0;
         for (int64_t u = w0; u < a.nunits; u += nw) {
@@ -216,16 +226,22 @@ __global__ void __launch_bounds__(kVecBlock) k_krylov_lanczos(KrylovArgs a) {
         // first barrier of the next step, by which time every CTA has read it
         block_partial(acc, a.part_b);
         if (!grid_barrier(a.sync, epoch)) return;
-        const double be = sqrt(sum_partials(a.part_b, G));
-        tn = fmax(tn, fabs(al) + be + (j > 0 ? bprev : 0.0));
-        const bool end = (j + 1 == a.nu) || !(be > 1e-12 * tn);
-        if (lead()) {
-            a.alpha[j] = al;
-            a.beta[j] = be;
-            if (end) *a.kdim = j + 1;
+        const double bsq = sum_partials(a.part_b, G);
+        if (threadIdx.x == 0) {
+            const double be = sqrt(bsq);
+            tn = fmax(tn, fabs(al) + be + (j > 0 ? bprev : 0.0));
+            const bool end = (j + 1 == a.nu) || !(be > 1e-12 * tn);
+            if (blockIdx.x == 0) {
+                a.alpha[j] = al;
+                a.beta[j] = be;
+                if (end) *a.kdim = j + 1;
+            }
+            s_end = end;
+            s_bprev = be;
+            s_inv = 1.0 / be;
         }
-        if (end) break;
-        bprev = be;
+        __syncthreads();
+        if (s_end) break;
         wprev = wcur;
     }
 }
@@ -242,11 +258,14 @@ __global__ void __launch_bounds__(kVecBlock) k_norm_part(int64_t n, const double
 // zero or not finite (*ok = 0, written by the lead thread)
 __global__ void __launch_bounds__(kVecBlock) k_scale_to(int64_t n, const double* src, double* dst,
                                                         const double* part, int G, int* ok) {
+    __shared__ double s_inv;
     const double s = sum_partials(part, G);
     const bool good = s > 0.0 && isfinite(s);
     if (lead() && ok) *ok = good;
     if (!good) return;
-    const double inv = 1.0 / sqrt(s);
+    if (threadIdx.x == 0) s_inv = 1.0 / sqrt(s);   // one thread: roots and divisions are long FP64 chains
+    __syncthreads();
+    const double inv = s_inv;
     GRID_STRIDE(i, n) dst[i] = src[i] * inv;
 }
 
@@ -276,17 +295,25 @@ __global__ void __launch_bounds__(kVecBlock) k_lz_next(int64_t n, int j, int m, 
         if (lead()) stop[j + 1] = 1;
         return;
     }
-    const double b = sqrt(sum_partials(part2, G));
-    const double tn = fmax(j ? tnorm[j - 1] : 0.0, fabs(alpha[j]) + b + (j ? beta[j - 1] : 0.0));
-    const bool end = (j + 1 == m) || !(b > 1e-12 * tn);
-    if (lead()) {
-        beta[j] = b;
-        tnorm[j] = tn;
-        stop[j + 1] = end;
-        if (end) *kdim = j + 1;
+    __shared__ double s_inv;
+    __shared__ int s_end;
+    const double bsq = sum_partials(part2, G);
+    if (threadIdx.x == 0) {   // one thread: roots and divisions are long FP64 chains
+        const double b = sqrt(bsq);
+        const double tn = fmax(j ? tnorm[j - 1] : 0.0, fabs(alpha[j]) + b + (j ? beta[j - 1] : 0.0));
+        const bool end = (j + 1 == m) || !(b > 1e-12 * tn);
+        if (blockIdx.x == 0) {
+            beta[j] = b;
+            tnorm[j] = tn;
+            stop[j + 1] = end;
+            if (end) *kdim = j + 1;
+        }
+        s_end = end;
+        s_inv = 1.0 / b;
     }
-    if (end) return;
-    const double inv = 1.0 / b;
+    __syncthreads();
+    if (s_end) return;
+    const double inv = s_inv;
     GRID_STRIDE(i, n) vnext[i] = w[i] * inv;
 }
 
@@ -450,11 +477,14 @@ __global__ void __launch_bounds__(kVecBlock) k_cg_xr(int64_t n, int s, double* y
                                                      const double* q, const double* part, int G, const double* rr,
                                                      const int* cgstop, int* cgbrk, double* part2) {
     if (cgstop[s]) return;
+    __shared__ double s_g;
     const double pq = sum_partials(part, G);
     const bool brk = !(pq > 0.0) || !isfinite(pq);
     if (lead()) cgbrk[s] = brk;
     if (brk) return;
-    const double g = rr[s] / pq;
+    if (threadIdx.x == 0) s_g = rr[s] / pq;   // one thread: divisions are long FP64 chains
+    __syncthreads();
+    const double g = s_g;
     double acc = 0.0;
     GRID_STRIDE(i, n) {
         y[i] = fma(g, p[i], y[i]);
@@ -473,12 +503,17 @@ __global__ void __launch_bounds__(kVecBlock) k_cg_p(int64_t n, int s, const doub
         if (lead()) cgstop[s + 1] = 1;
         return;
     }
+    __shared__ double s_be;
     const double rn = sum_partials(part2, G);
-    if (lead()) {
-        rr[s + 1] = rn;
-        cgstop[s + 1] = !(rn > kCgRtol * kCgRtol * rr[0]);
+    if (threadIdx.x == 0) {   // one thread: divisions are long FP64 chains
+        s_be = rn / rr[s];
+        if (blockIdx.x == 0) {
+            rr[s + 1] = rn;
+            cgstop[s + 1] = !(rn > kCgRtol * kCgRtol * rr[0]);
+        }
     }
-    const double be = rn / rr[s];
+    __syncthreads();
+    const double be = s_be;
     GRID_STRIDE(i, n) p[i] = fma(be, p[i], r[i]);
 }
 
