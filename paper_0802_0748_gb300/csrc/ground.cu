@@ -323,11 +323,12 @@ __global__ void __launch_bounds__(kVecBlock) k_lz_next(int64_t n, int j, int m, 
 // (no division, so no FP64 divide per step).  A minor that vanishes (or
 // falls below pivmin |P_i|) is replaced by -pivmin P_i, like a tiny negative
 // pivot; both minors are rescaled by 2^-600 / 2^600 to stay in range.
-__device__ int tri_count_below(const double* a, const double* b, int k, double x, double pivmin) {
+// a and b2 (= b_{i-1}^2 at index i) are staged in shared memory by the caller.
+__device__ int tri_count_below(const double* a, const double* b2, int k, double x, double pivmin) {
     int c = 0;
     double pm = 0.0, p = 1.0;   // P_{i-1}, P_i
     for (int i = 0; i < k; ++i) {
-        double pn = fma(a[i] - x, p, i > 0 ? -(b[i - 1] * b[i - 1]) * pm : 0.0);
+        double pn = fma(a[i] - x, p, -b2[i] * pm);
         if (fabs(pn) <= pivmin * fabs(p)) pn = -pivmin * p;
         if ((pn < 0.0) != (p < 0.0)) ++c;
         pm = p;
@@ -336,6 +337,15 @@ __device__ int tri_count_below(const double* a, const double* b, int k, double x
         else if (fabs(p) < 0x1p-600 && fabs(pm) < 0x1p-600) { p *= 0x1p600; pm *= 0x1p600; }
     }
     return c;
+}
+
+// stage alpha and the squared off-diagonals (b2[0] = 0) in shared memory
+__device__ __forceinline__ void stage_tri(const double* alpha, const double* beta, int k, double* s_a, double* s_b2) {
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        s_a[i] = alpha[i];
+        s_b2[i] = i > 0 ? beta[i - 1] * beta[i - 1] : 0.0;
+    }
+    __syncthreads();
 }
 
 // Lowest eigenpair of the k x k tridiagonal T (alpha on the diagonal, beta
@@ -347,10 +357,12 @@ __device__ int tri_count_below(const double* a, const double* b, int k, double x
 __global__ void k_tri_lowest(const int* kdim, const double* alpha, const double* beta, double* s, double* work,
                              double* theta_out) {
     if (blockIdx.x != 0) return;
+    __shared__ double s_a[kMaxLanczos], s_b2[kMaxLanczos];
     const int lane = threadIdx.x & 31;
     const int k = *kdim;
     const double* a = alpha;
     const double* b = beta;
+    stage_tri(alpha, beta, k, s_a, s_b2);
     double lo = INFINITY, hi = -INFINITY;
     for (int i = 0; i < k; ++i) {
         const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < k ? fabs(b[i]) : 0.0);
@@ -362,7 +374,7 @@ __global__ void k_tri_lowest(const int* kdim, const double* alpha, const double*
     const double pivmin = eps * scale * 1e-3 + 1e-300;
     lo -= 2.0 * eps * scale + pivmin;
     hi += 2.0 * eps * scale + pivmin;
-    auto count_below = [&](double x) { return tri_count_below(a, b, k, x, pivmin); };
+    auto count_below = [&](double x) { return tri_count_below(s_a, s_b2, k, x, pivmin); };
     // invariant: no eigenvalue below lo, at least one below hi (the same on every lane)
     for (int it = 0; it < 64 && hi - lo > 2.0 * eps * fmax(fabs(lo), fabs(hi)) + pivmin; ++it) {
         const double x = lo + (hi - lo) * ((double)(lane + 1) / 33.0);
@@ -551,9 +563,11 @@ __global__ void __launch_bounds__(kVecBlock) k_proj_fin(const double* part, int 
 // at one point), keeping "fewer than q + 1 eigenvalues below lo, at least
 // q + 1 below hi"
 __global__ void k_tri_evals(const int* kdim, const double* alpha, const double* beta, double* ev, double* scale_out) {
+    __shared__ double s_a[kMaxLanczos], s_b2[kMaxLanczos];
     const int k = *kdim;
     const int lane = threadIdx.x & 31;
     const int q = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    stage_tri(alpha, beta, k, s_a, s_b2);
     double lo = INFINITY, hi = -INFINITY;
     for (int i = 0; i < k; ++i) {
         const double r = (i > 0 ? fabs(beta[i - 1]) : 0.0) + (i + 1 < k ? fabs(beta[i]) : 0.0);
@@ -569,7 +583,7 @@ __global__ void k_tri_evals(const int* kdim, const double* alpha, const double* 
     hi += 2.0 * eps * scale + pivmin;
     for (int it = 0; it < 64 && hi - lo > 2.0 * eps * fmax(fabs(lo), fabs(hi)) + pivmin; ++it) {
         const double x = lo + (hi - lo) * ((double)(lane + 1) / 33.0);
-        const unsigned above = __ballot_sync(0xffffffffu, tri_count_below(alpha, beta, k, x, pivmin) >= q + 1);
+        const unsigned above = __ballot_sync(0xffffffffu, tri_count_below(s_a, s_b2, k, x, pivmin) >= q + 1);
         const int f = above ? __ffs(above) - 1 : 32;
         const double xf = __shfl_sync(0xffffffffu, x, f < 32 ? f : 31);
         const double xp = __shfl_sync(0xffffffffu, x, f > 0 ? f - 1 : 0);
