@@ -1,15 +1,22 @@
-// Ground state of a real symmetric H by the Lanczos method followed by the
-// conjugate-gradient method used as inverse iteration, the two repeated until
-// the residual norm is small enough (Sec. II.C).  The vector it returns is the
-// starting point of the excitation spectra: c|psi_0> and c+|psi_0>
-// (scocg_excite, hubbard.cu) are right-hand sides of the shifted solve.
+// The Lanczos-based parts of the library, all in FP64 on real vectors:
 //
-// One cycle:
+// * scocg_ground_state: the ground state of a real symmetric H by the Lanczos
+//   method followed by the conjugate-gradient method used as inverse
+//   iteration, the two repeated until the residual norm is small enough
+//   (Sec. II.C).  The vector it returns is the starting point of the
+//   excitation spectra: c|psi_0> and c+|psi_0> (scocg_excite, hubbard.cu) are
+//   right-hand sides of the shifted solve.
+// * scocg_krylov_sd: Green's functions by subspace diagonalisation in the
+//   Krylov subspace K_nu(H, b) (Sec. III.B, Eq. Ham_in_KS): the eigenpairs of
+//   the Lanczos tridiagonal T and the projections c_m^T v_j give
+//   G_m(z) = sum_a (c_m^T w_a)(w_a^T b) / (z - e_a).
+//
+// One ground-state cycle:
 //   Lanczos, m steps from psi (no reorthogonalization):
 //     w = H v_j - beta_{j-1} v_{j-1};  alpha_j = v_j^T w;  w -= alpha_j v_j;
 //     beta_j = ||w||;  v_{j+1} = w / beta_j  (stop when beta_j vanishes)
 //   lowest eigenpair (theta, s) of T = tridiag(beta, alpha, beta): Sturm
-//     bisection, then inverse iteration with a pivoted tridiagonal LU
+//     multisection, then inverse iteration with a pivoted tridiagonal LU
 //   psi = V s / ||V s||;  E = psi^T H psi;  res = ||H psi - E psi||
 //   stop if res <= tol; else CG on (H - sigma) y = psi, sigma = E - res
 //     (below the lowest eigenvalue once psi is close to it, so H - sigma is
