@@ -379,7 +379,10 @@ int scocg_excite(scocg_handle from, scocg_handle to, int site, int spin, int cre
  *   G_m(z_k) = sum_a weight[m][a] / (z_k - e_a),
  *   weight[m][a] = (c_m^T w_a)(w_a^T b) = (sum_j s_a(j) c_m^T v_j) ||b|| s_a(0).
  * FP64 arithmetic regardless of the handle's precision option; CSR or Hubbard
- * handle.  The eigenvalues come from bisection on the Sturm count, the
+ * handle.  On the 4x4-blocked layout with unit projections the recursion runs
+ * as one cooperative launch (two CTAs per SM, or the handle's grid option if
+ * smaller; its grid barriers give up after the handle's timeout_ms with
+ * SCOCG_ERR_TIMEOUT).  The eigenvalues come from bisection on the Sturm count, the
  * eigenvectors from inverse iteration, orthogonalised within clusters of
  * eigenvalues closer than 1e-3 ||T|| (where the lost orthogonality puts the
  * ghost copies of converged eigenvalues).  A density-matrix element follows

@@ -939,10 +939,14 @@ extern "C" int scocg_krylov_sd(scocg_handle h, const double* b, int nu, const sc
     int Gp = 0;
     if (use_bsr(h) && proj_idx) {
         int nb = 0;
+        // two CTAs per SM: measured faster than the occupancy maximum of three on
+        // the 32^3 x 4 matrix (7.9 vs 9.2 ms per 200 steps; the grid barriers and
+        // the block sums grow with the CTA count), and than one (8.8 ms)
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_krylov_lanczos, kVecBlock, 0) == cudaSuccess && nb > 0)
-            Gp = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nb * h->num_sms,
+            Gp = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::min(nb, 2) * h->num_sms,
                                                              (h->nunits_bsr * 32 + kVecBlock - 1) / kVecBlock));
         cudaGetLastError();
+        if (Gp > 0 && h->opts.grid > 0) Gp = std::min(Gp, h->opts.grid);   // the handle's grid option, clamped
         Gh = std::max(Gh, Gp);
     }
     Carver cv{nullptr, 0};
