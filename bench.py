@@ -65,11 +65,10 @@ sys.path.insert(0, str(ROOT))
 METRIC = "shift-iter/s (G(z) tol 1e-6, 64^3x4 Anderson, 512 shifts)"
 UNIT = "shift-iter/s"
 TOL = 1e-6
-# Spectral bounds of the seed-2 64^3 x 4 Anderson matrix (ARPACK, tol 1e-4),
-# fixed here so every run uses the identical shift list.
-BOUNDS = (-6.086151226927176, 6.469558282777935)
-# The same for the seed-3 32^3 x 4 matrix of the batched leg.
-BATCH_BOUNDS = (-6.041048698881869, 5.997536652116761)
+# Spectral bounds of the seed-2 64^3 x 4 Anderson matrix and of the seed-3
+# 32^3 x 4 matrix of the batched leg (ARPACK, fixed so that every run uses the
+# identical shift list).
+from paper_0802_0748_gb300.inputs import ANDERSON64_BOUNDS as BOUNDS, BATCH32_BOUNDS as BATCH_BOUNDS  # noqa: E402
 
 # DRAM traffic per seed iteration of the persistent solve kernel, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum over a 60-iteration

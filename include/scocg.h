@@ -17,7 +17,7 @@
  * for unit vectors c_m = e_i (Green's-function elements, local DOS
  * -Im G_ii / pi) or dense vectors c_m (for a spectrum <b|G|b> pass c = conj(b)).
  * H is either a CSR matrix (tight-binding form, Sec. II) or the matrix-free
- * extended Hubbard model in a fixed (N_up, N_dn) sector (Sec. IV.D).
+ * extended Hubbard model in a fixed (N_up, N_dn) sector (Sec. IV.B).
  *
  * Conventions for every entry point:
  *  - Complex numbers are (re, im) pairs of doubles, scocg_c128.
@@ -146,7 +146,7 @@ int scocg_create_csr(scocg_handle *out, int64_t n, int64_t nnz, const int64_t *r
                      const scocg_opts *opts, void *cuda_stream);
 
 /*
- * scocg_create_hubbard -- matrix-free extended Hubbard ring (Sec. IV.D):
+ * scocg_create_hubbard -- matrix-free extended Hubbard ring (Sec. IV.B):
  *   H = -t sum_{<ij>,s} (c+_is c_js + h.c.) + U sum_i n_i,up n_i,dn + V sum_<ij> n_i n_j
  * on L sites (2 <= L <= 16) in the sector with n_up up and n_dn down electrons.
  * Bonds are (i, i+1), plus (L-1, 0) when periodic and L >= 3.  Basis index =
@@ -285,7 +285,9 @@ void scocg_multi_release(void);
  * Inputs and outputs belong to the caller:
  *   n, nnz, rowptr[n+1] (device int32), col[nnz] (device int32), val[nnz]
  *                        (device double): H in CSR; NOT validated -- H must be
- *                        real symmetric with in-range indices
+ *                        real symmetric with in-range indices (a bounds-checked
+ *                        build, -DSCOCG_CHECKED, skips an out-of-range index
+ *                        and returns SCOCG_ERR_INVALID)
  *   shifts[nshift]       host; rhs device complex128 [n]
  *   proj_idx[nproj] host int64 | proj_vec device complex128 [nproj][n]
  *   tol, max_iter (0 -> 100000), G_out device complex128 [nproj][nshift],
@@ -297,8 +299,10 @@ void scocg_multi_release(void);
  * 2 * 16 * n + 120 * nshift * (1 + nproj) bytes plus ~40 KB, i.e. n up to
  * about 780,000 rows at a few hundred shifts.
  * The first call on a device looks the array's device address up with
- * cudaGetSymbolAddress (with that device current); make that first call
- * before any stream capture.  Every call reuses the same array and leaves its
+ * cudaGetSymbolAddress (with that device current) and keeps it together with
+ * the id of the current CUDA context; a call in another context (after
+ * cudaDeviceReset, for instance) looks it up again.  Make the first call in
+ * each context before any stream capture.  Every call reuses the same array and leaves its
  * contents behind (the call clears what must start at zero), so calls whose
  * work overlaps on the GPU -- from several threads or streams -- race: issue
  * them one after another.
@@ -310,7 +314,7 @@ int scocg_solve_csr_noalloc(int64_t n, int64_t nnz, const int32_t *rowptr, const
 
 /*
  * scocg_ground_state -- lowest eigenvalue E and unit eigenvector psi of the
- * real symmetric H of a CSR or Hubbard handle, by the cycle of Sec. II.C: the
+ * real symmetric H of a CSR or Hubbard handle, by the cycle of Sec. II.B: the
  * Lanczos method (its basis loses orthogonality; it is not reorthogonalized),
  * then the conjugate-gradient method used as inverse iteration, repeated until
  * the residual norm is small enough.  One cycle:
@@ -351,7 +355,7 @@ int scocg_ground_state(scocg_handle h, const double *v0, double *psi, int m, int
 
 /*
  * scocg_excite -- one-particle excitation vector between Hubbard sectors
- * (Sec. IV.D: the ionization and affinity spectra are G(z) = b^T (z - H)^{-1} b
+ * (Sec. IV.B: the ionization and affinity spectra are G(z) = b^T (z - H)^{-1} b
  * for b = c_{i s}|psi_0> and b = c+_{i s}|psi_0>):
  *   out = c_{site,spin} psi   (create = 0; to = sector with one spin-s electron less)
  *   out = c+_{site,spin} psi  (create = 1; to = sector with one spin-s electron more)

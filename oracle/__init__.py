@@ -12,12 +12,12 @@ Contents (each function cites the passage of arXiv:0802.0748 it follows):
                          shift_lin_eq, residual).
 * ``apply_shifted``      y = (z I - H) x (Eq. lin_eq's matrix).
 * ``hubbard_csr``        extended Hubbard sector Hamiltonian from the literal
-                         Jordan-Wigner definition (Sec. IV.D).
+                         Jordan-Wigner definition (Sec. IV.B).
 * ``dense``              dense LU Green's functions, closed forms, Fock-space
                          exact diagonalisation, dense gradients.
 * ``ground``             Lanczos / CG-inverse-iteration ground state and the
                          one-particle operators c, c+ between sectors
-                         (Sec. II.C, Sec. IV.D).
+                         (Sec. II.B, Sec. IV.B).
 """
 from __future__ import annotations
 
@@ -141,13 +141,13 @@ def apply_shifted(rowptr, col, val, z: complex, x) -> np.ndarray:
 
 
 def sector_dim(L: int, k: int) -> int:
-    """Number of L-bit strings with k ones, counted by enumeration (Sec. IV.D)."""
+    """Number of L-bit strings with k ones, counted by enumeration (Sec. IV.B)."""
     return int(lib().oracle_sector_dim(L, k))
 
 
 def hubbard_csr(L, n_up, n_dn, t, U, V, periodic=True):
     """Extended Hubbard sector Hamiltonian in CSR from the literal Jordan-Wigner
-    definition (Sec. IV.D).  Returns (rowptr, col, val)."""
+    definition (Sec. IV.B).  Returns (rowptr, col, val)."""
     f = lib().oracle_hubbard_csr
     nnz = f(L, n_up, n_dn, t, U, V, int(periodic), None, None, None)
     if nnz < 0:

@@ -8,7 +8,7 @@ Each function is the plain definition it names, with a library routine
                       finite-chain eigen-sum, the semi-infinite surface form and
                       the bulk form (textbook tight-binding results for the
                       chain Hamiltonian of Sec. II).
-* ``fock_hubbard``    extended Hubbard Hamiltonian of Sec. IV.D built in the full
+* ``fock_hubbard``    extended Hubbard Hamiltonian of Sec. IV.B built in the full
                       4^L Fock space from Jordan-Wigner Kronecker products, then
                       restricted to an (N_up, N_dn) sector.
 * ``grad_dense``      dG/dH_ab = (A^{-T} c)_a (A^{-1} b)_b from the dense inverse.
@@ -91,7 +91,7 @@ def hubbard_bonds(L: int, periodic: bool):
 
 
 def fock_hubbard(L: int, t: float, U: float, V: float, periodic: bool = True):
-    """Extended Hubbard Hamiltonian (Sec. IV.D) on the full 4^L Fock space.
+    """Extended Hubbard Hamiltonian (Sec. IV.B) on the full 4^L Fock space.
 
     H = -t sum_{<ij>,s} (c+_is c_js + h.c.) + U sum_i n_iu n_id + V sum_<ij> n_i n_j.
     Modes: up-spin sites 0..L-1 are modes 0..L-1, down-spin sites are modes L..2L-1.

@@ -3,21 +3,21 @@
 TEST INFRASTRUCTURE ONLY: the tests and ``__graft_entry__.smoke()`` use it;
 the product path never imports it and shares no code with it.
 
-Sec. II.C of arXiv:0802.0748: the ground state is found by the Lanczos
+Sec. II.B of arXiv:0802.0748: the ground state is found by the Lanczos
 method, whose basis loses orthogonality after a few steps, and is then
 improved by the conjugate-gradient method used as inverse iteration; the two
 are repeated until the residual norm is small enough.  The excitation
 spectra then follow from the shifted solver applied to c|psi_0> and
-c+|psi_0> (Sec. IV.D, ionization and affinity levels).
+c+|psi_0> (Sec. IV.B, ionization and affinity levels).
 
 Plain NumPy in FP64; ``H`` is anything with ``@`` (a dense array or a
 scipy.sparse matrix).
 
 * ``lanczos_ground_state``  Lanczos (no reorthogonalization), lowest Ritz pair,
-                            residual, CG inverse iteration, repeated (Sec. II.C)
+                            residual, CG inverse iteration, repeated (Sec. II.B)
 * ``fermion_op``            c_{i s} or c+_{i s} between particle-number sectors,
                             from the Jordan-Wigner definition acting on
-                            occupation patterns (Sec. IV.D's model)
+                            occupation patterns (Sec. IV.B's model)
 * ``fermion_op_at``         selected entries of the same, one by one
 * ``hubbard_rows_apply``    (H psi) on selected rows, from the operators
 * ``krylov_sd``             Green's functions by subspace diagonalisation in the
@@ -45,7 +45,7 @@ CG_RTOL = 1e-10
 
 
 def _lanczos(H, v0, m):
-    """m Lanczos steps from v0 (Sec. II.C): returns (alpha, beta, V) with
+    """m Lanczos steps from v0 (Sec. II.B): returns (alpha, beta, V) with
     H V_k = V_k T_k + beta_{k-1} v_k e_k^T, T_k = tridiag(beta, alpha, beta).
     Stops early when beta_j vanishes (an invariant subspace)."""
     n = v0.shape[0]
@@ -71,7 +71,7 @@ def _lanczos(H, v0, m):
 
 
 def _cg_inverse_step(H, psi, sigma, cg_steps):
-    """CG on (H - sigma) y = psi from y = 0 (inverse iteration by CG, Sec. II.C)."""
+    """CG on (H - sigma) y = psi from y = 0 (inverse iteration by CG, Sec. II.B)."""
     y = np.zeros_like(psi)
     r = psi.copy()
     p = psi.copy()
@@ -106,7 +106,7 @@ class GroundState:
 
 def lanczos_ground_state(H, v0, m=60, cg_steps=0, max_cycles=50, tol=1e-10):
     """Lowest eigenpair of the real symmetric H by the Lanczos / CG-inverse-
-    iteration cycle of Sec. II.C.  Converged when ||H psi - E psi||_2 <= tol
+    iteration cycle of Sec. II.B.  Converged when ||H psi - E psi||_2 <= tol
     with ||psi||_2 = 1 and E = psi^T H psi."""
     psi = np.asarray(v0, dtype=np.float64)
     psi = psi / np.linalg.norm(psi)
@@ -216,7 +216,7 @@ def fermion_op_at(L, n_up, n_dn, site, spin, create, psi, targets):
 
 
 def hubbard_rows_apply(L, n_up, n_dn, t, U, V, periodic, psi, rows):
-    """(H psi)[rows] for the extended Hubbard ring of Sec. IV.D,
+    """(H psi)[rows] for the extended Hubbard ring of Sec. IV.B,
     H = -t sum_{<ij>,s} (c+_is c_js + h.c.) + U sum_i n_iu n_id + V sum_<ij> n_i n_j,
     each row from the operators acting on that basis pattern (H is real
     symmetric, so row s is H|s> read in the basis).  Bonds (i, i+1), and

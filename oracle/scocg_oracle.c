@@ -19,7 +19,7 @@
  *                     shifted systems (Eq. shift_lin_eq) through collinear
  *                     residuals, seed switching
  *   Eq. (residual)    |r> = (e + i delta - H)|x> - |j>, monitored to stop
- *   Sec. IV.D         extended Hubbard model in a fixed-S_z sector
+ *   Sec. IV.B         extended Hubbard model in a fixed-S_z sector
  *
  * The paper states what shifted COCG does but prints no recurrence.  The
  * recurrences below are those of textbook COCG (van der Vorst & Melissen 1990)
@@ -297,7 +297,7 @@ void oracle_apply_shifted(int64_t n, const int64_t *rowptr, const int32_t *col, 
 }
 
 /* ------------------------------------------------------------------------ */
-/* Extended Hubbard model in a fixed (N_up, N_dn) sector (Sec. IV.D).
+/* Extended Hubbard model in a fixed (N_up, N_dn) sector (Sec. IV.B).
  *
  *   H = -t sum_{<ij>, s} (c+_{is} c_{js} + c+_{js} c_{is})
  *       + U sum_i n_{i up} n_{i dn} + V sum_{<ij>} n_i n_j,   n_i = n_{i up} + n_{i dn}

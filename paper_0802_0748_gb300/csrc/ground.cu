@@ -3,7 +3,7 @@
 // * scocg_ground_state: the ground state of a real symmetric H by the Lanczos
 //   method followed by the conjugate-gradient method used as inverse
 //   iteration, the two repeated until the residual norm is small enough
-//   (Sec. II.C).  The vector it returns is the starting point of the
+//   (Sec. II.B).  The vector it returns is the starting point of the
 //   excitation spectra: c|psi_0> and c+|psi_0> (scocg_excite, hubbard.cu) are
 //   right-hand sides of the shifted solve.
 // * scocg_krylov_sd: Green's functions by subspace diagonalisation in the

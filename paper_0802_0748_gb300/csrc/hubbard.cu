@@ -1,4 +1,4 @@
-// Matrix-free extended Hubbard ring (Sec. IV.D of arXiv:0802.0748):
+// Matrix-free extended Hubbard ring (Sec. IV.B of arXiv:0802.0748):
 //   H = -t sum_{<ij>,s} (c+_is c_js + h.c.) + U sum_i n_i,up n_i,dn + V sum_<ij> n_i n_j
 // in the sector with n_up up and n_dn down electrons on L sites.
 //

@@ -13,6 +13,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+
+#include <cuda.h>   // driver types for the context id (entry points come through the runtime)
 
 #include "api_internal.h"
 #include "solver_kernel.cuh"
@@ -26,21 +29,66 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 namespace {
 
+// The array's name in host code is only a host-side stand-in; its device
+// address comes from cudaGetSymbolAddress, looked up with the device current.
+// The address belongs to the module as loaded into one CUDA context: after
+// cudaDeviceReset (or any teardown of the primary context) the module is
+// loaded again and the array may move.  So the cache keeps, per device, the
+// unique id of the context the address was taken in (cuCtxGetId through the
+// runtime's driver entry points; no link against the driver library) and looks
+// the symbol up again whenever the current context has another id.
 constexpr int kMaxDevices = 64;
-void* g_scratch_addr[kMaxDevices] = {};   // device address of the array, per device
+struct ScratchAddr {
+    unsigned long long ctx_id;
+    void* addr;
+};
+ScratchAddr g_scratch[kMaxDevices] = {};
+std::mutex g_scratch_mu;
 
-// The array's name in host code is only a host-side stand-in; the device
-// address comes from cudaGetSymbolAddress, looked up once per device with that
-// device current (the first call on each device does it).
+using PfnCtxGetCurrent = CUresult (*)(CUcontext*);
+using PfnCtxGetId = CUresult (*)(CUcontext, unsigned long long*);
+
+// Id of the calling thread's current context (0 when there is none yet).
+cudaError_t current_ctx_id(unsigned long long* id) {
+    static PfnCtxGetCurrent get_cur = nullptr;
+    static PfnCtxGetId get_id = nullptr;
+    if (!get_cur || !get_id) {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+        if (e == cudaSuccess)
+            e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e != cudaSuccess) return e;
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return cudaErrorNotSupported;
+        get_cur = reinterpret_cast<PfnCtxGetCurrent>(f1);
+        get_id = reinterpret_cast<PfnCtxGetId>(f2);
+    }
+    CUcontext ctx = nullptr;
+    if (get_cur(&ctx) != CUDA_SUCCESS) return cudaErrorUnknown;
+    *id = 0;
+    if (ctx && get_id(ctx, id) != CUDA_SUCCESS) return cudaErrorUnknown;
+    return cudaSuccess;
+}
+
+// Device address of the scratch array in the current context of device `dev`
+// (which must be current).  The first call in a context does the look-up.
 cudaError_t scratch_address(int dev, void** out) {
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    if (!g_scratch_addr[dev]) {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    unsigned long long id = 0;
+    cudaError_t e = current_ctx_id(&id);
+    if (e != cudaSuccess) return e;
+    if (id == 0 || g_scratch[dev].addr == nullptr || g_scratch[dev].ctx_id != id) {
         void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);   // creates the primary context if needed
         if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
+        e = current_ctx_id(&id);
+        if (e != cudaSuccess) return e;
+        g_scratch[dev] = ScratchAddr{id, p};
     }
-    *out = g_scratch_addr[dev];
+    *out = g_scratch[dev].addr;
     return cudaSuccess;
 }
 
@@ -52,7 +100,7 @@ struct ApplyCSRFixed : ApplyCSR<double, LPR> {};
 template <int LPR>
 cudaError_t launch_csr(const SolveArgs<double>& a, const int* rowptr, const int* col, const double* val,
                        int64_t n, int64_t nnz, int grid, cudaStream_t st) {
-    ApplyCSRFixed<LPR> ap{{rowptr, col, val, n, nnz, nullptr}};
+    ApplyCSRFixed<LPR> ap{{rowptr, col, val, n, nnz, a.dbg}};
     void* args[] = {(void*)&a, (void*)&ap};
     return cudaLaunchCooperativeKernel((const void*)cocg_persistent<double, ApplyCSRFixed<LPR>>, dim3(grid),
                                        dim3(kBlock), args, 0, st);
@@ -65,21 +113,6 @@ int occupancy_csr() {
                                                       0) != cudaSuccess)
         return 0;
     return nb;
-}
-
-// The seed rule of scocg_solve (smallest Im z, then Re z nearest the median
-// Re z, then the lowest index), with a stack buffer instead of a heap one.
-int seed_rule(const scocg_c128* z, int K) {
-    double re[4096];
-    for (int k = 0; k < K; ++k) re[k] = z[k].re;
-    std::sort(re, re + K);
-    const double med = (K % 2) ? re[K / 2] : 0.5 * (re[K / 2 - 1] + re[K / 2]);
-    int best = 0;
-    for (int k = 1; k < K; ++k) {
-        if (z[k].im < z[best].im) { best = k; continue; }
-        if (z[k].im == z[best].im && std::fabs(z[k].re - med) < std::fabs(z[best].re - med)) best = k;
-    }
-    return best;
 }
 
 }  // namespace
@@ -168,7 +201,7 @@ extern "C" int scocg_solve_csr_noalloc(int64_t n, int64_t nnz, const int32_t* ro
     a.cvec = static_cast<const double2*>(proj_vec);
     a.nproj = M;
     a.K = K;
-    a.seed = seed_rule(shifts, K);
+    a.seed = default_seed(shifts, K);   // the rule scocg_solve uses (host memory only)
     a.allow_switch = 1;
     a.tol = tol;
     a.max_iter = max_iter > 0 ? max_iter : o.max_iter;
@@ -192,6 +225,9 @@ extern "C" int scocg_solve_csr_noalloc(int64_t n, int64_t nnz, const int32_t* ro
         e = cudaMemcpyAsync(info->resid, a.S.resid, sizeof(double) * K, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(e);
+    // checked builds: an out-of-range row pointer or column index of the
+    // caller's CSR was recorded (and skipped) by the kernel
+    if (c.dbg[0]) return SCOCG_ERR_INVALID;
     if (info) {
         if (info->resid)   // the kernel keeps squared residual estimates
             for (int k = 0; k < K; ++k) info->resid[k] = std::sqrt(info->resid[k]);

@@ -16,7 +16,7 @@ for them with the same structure):
                     entry is rounded to an FP32-representable double so that a
                     single-precision copy of H is exact.
 * Hubbard ring parameters for the matrix-free extended Hubbard model of
-  Sec. IV.D (the basis itself is built by each consumer).
+  Sec. IV.B (the basis itself is built by each consumer).
 
 All randomness comes from numpy's PCG64 (``np.random.default_rng(seed)``).
 """
@@ -29,8 +29,14 @@ import numpy as np
 
 __all__ = [
     "CSR", "chain_csr", "anderson_csr", "spectral_bounds", "random_unit_complex",
-    "to_fp32_exact", "Workload", "workload", "cluster_sizes",
+    "to_fp32_exact", "Workload", "workload", "cluster_sizes", "ANDERSON64_BOUNDS", "BATCH32_BOUNDS",
 ]
+
+# Spectral bounds (ARPACK, tol 1e-4) of the seed-2 64^3 x 4 Anderson matrix and
+# of the seed-3 32^3 x 4 matrix, fixed so that every consumer draws the
+# identical shift list without re-running the eigensolver.
+ANDERSON64_BOUNDS = (-6.086151226927176, 6.469558282777935)
+BATCH32_BOUNDS = (-6.041048698881869, 5.997536652116761)
 
 
 @dataclass

@@ -141,6 +141,26 @@ def _dev(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _need(t, dtype, numel: int | None, name: str):
+    """Checks that a device argument is a contiguous CUDA tensor of the given
+    dtype and element count (the C side reads exactly that many elements)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, not {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, not {t.numel()}")
+    return t
+
+
+def _handle_n(h) -> int:
+    n = getattr(h, "n", None)
+    return int(n) if n is not None else scocg_dim(h)
+
+
 class Handle:
     """Owns one scocg_handle; destroyed by close() or garbage collection."""
 
@@ -191,7 +211,7 @@ def scocg_create_csr(rowptr, col, val, opts: SolveOptions | None = None, stream=
 
 def scocg_create_hubbard(L, n_up, n_dn, t, U, V, periodic=True, opts: SolveOptions | None = None,
                          stream=None) -> Handle:
-    """scocg_create_hubbard: matrix-free extended Hubbard ring (Sec. IV.D)."""
+    """scocg_create_hubbard: matrix-free extended Hubbard ring (Sec. IV.B)."""
     out = ctypes.c_void_p()
     o = (opts or SolveOptions()).c()
     code = lib().scocg_create_hubbard(ctypes.byref(out), L, n_up, n_dn, t, U, V, int(bool(periodic)),
@@ -257,11 +277,13 @@ def scocg_solve(h: Handle, shifts, rhs, proj_idx=None, proj_vec=None, tol: float
     import torch
     z, zp = _shifts(shifts)
     K = z.size
+    n = _handle_n(h)
     rhs = rhs if rhs.dim() == 2 else rhs.reshape(1, -1)
     if rhs.dtype != torch.complex128 or not rhs.is_cuda:
         raise TypeError("rhs must be a CUDA complex128 tensor")
     rhs = rhs.contiguous()
     nrhs = rhs.shape[0]
+    _need(rhs, torch.complex128, nrhs * n, "rhs")
     pidx_p = pvec_p = None
     if proj_idx is not None:
         pidx = np.ascontiguousarray(np.asarray(proj_idx, dtype=np.int64))
@@ -275,6 +297,7 @@ def scocg_solve(h: Handle, shifts, rhs, proj_idx=None, proj_vec=None, tol: float
             raise TypeError("proj_vec must be a CUDA complex128 tensor")
         pv = pv.contiguous()
         M = pv.shape[0]
+        _need(pv, torch.complex128, M * n, "proj_vec")
         pvec_p = _dev(pv)
     G = torch.zeros((nrhs, M, K), dtype=torch.complex128, device=rhs.device)
     info, it, rs = _info_struct(nrhs, K)
@@ -291,11 +314,13 @@ def scocg_density(h: Handle, mu: float, kT: float, delta: float, emin: float, em
     rhs / proj_idx / proj_vec as in scocg_solve; the shifts are the nquad grid
     energies of [emin, emax] plus i delta."""
     import torch
+    n = _handle_n(h)
     rhs = rhs if rhs.dim() == 2 else rhs.reshape(1, -1)
     if rhs.dtype != torch.complex128 or not rhs.is_cuda:
         raise TypeError("rhs must be a CUDA complex128 tensor")
     rhs = rhs.contiguous()
     nrhs = rhs.shape[0]
+    _need(rhs, torch.complex128, nrhs * n, "rhs")
     pidx_p = pvec_p = None
     keep = None
     if proj_idx is not None:
@@ -310,6 +335,7 @@ def scocg_density(h: Handle, mu: float, kT: float, delta: float, emin: float, em
             raise TypeError("proj_vec must be a CUDA complex128 tensor")
         keep = pv
         M = pv.shape[0]
+        _need(pv, torch.complex128, M * n, "proj_vec")
         pvec_p = _dev(pv)
     rho = torch.zeros((nrhs, M), dtype=torch.float64, device=rhs.device)
     info, it, rs = _info_struct(nrhs, int(nquad))
@@ -324,7 +350,7 @@ def scocg_solve_full(h: Handle, shifts, rhs, tol: float = 1e-10):
     import torch
     z, zp = _shifts(shifts)
     K = z.size
-    rhs = rhs.reshape(-1).contiguous()
+    rhs = _need(rhs.reshape(-1).contiguous(), torch.complex128, _handle_n(h), "rhs")
     X = torch.zeros((K, rhs.numel()), dtype=torch.complex128, device=rhs.device)
     info, it, rs = _info_struct(1, K)
     code = lib().scocg_solve_full(h.ptr, zp, K, _dev(rhs), float(tol), _dev(X), ctypes.byref(info))
@@ -337,7 +363,8 @@ def scocg_grad(h: Handle, shifts, rhs, dL_dG, proj_idx=None, proj_vec=None, tol:
     import torch
     z, zp = _shifts(shifts)
     K = z.size
-    rhs = rhs.reshape(1, -1).contiguous()
+    n = _handle_n(h)
+    rhs = _need(rhs.reshape(1, -1).contiguous(), torch.complex128, n, "rhs")
     pidx_p = pvec_p = None
     if proj_idx is not None:
         pidx = np.ascontiguousarray(np.asarray(proj_idx, dtype=np.int64).reshape(1, -1))
@@ -346,8 +373,9 @@ def scocg_grad(h: Handle, shifts, rhs, dL_dG, proj_idx=None, proj_vec=None, tol:
     else:
         pv = (proj_vec if proj_vec.dim() == 2 else proj_vec.reshape(1, -1)).contiguous()
         M = pv.shape[0]
+        _need(pv, torch.complex128, M * n, "proj_vec")
         pvec_p = _dev(pv)
-    g = dL_dG.to(torch.complex128).contiguous()
+    g = _need(dL_dG.to(torch.complex128).contiguous(), torch.complex128, M * K, "dL_dG")
     out = torch.zeros(int(h.nnz), dtype=torch.float64, device=rhs.device)
     info, it, rs = _info_struct(1, K)
     code = lib().scocg_grad(h.ptr, zp, K, _dev(rhs), 1, pidx_p, pvec_p, M, float(tol), _dev(g), _dev(out),
@@ -368,7 +396,7 @@ def scocg_ground_state(h: Handle, v0, m: int = 60, cg_steps: int = 0, max_cycles
     """scocg_ground_state: returns (E, psi CUDA float64 [N], info dict).
 
     v0: CUDA float64 [N] start vector.  Lanczos / CG-inverse-iteration cycles
-    (Sec. II.C) until ||H psi - E psi|| <= tol."""
+    (Sec. II.B) until ||H psi - E psi|| <= tol."""
     import torch
     if v0.dtype != torch.float64 or not v0.is_cuda:
         raise TypeError("v0 must be a CUDA float64 tensor")
@@ -466,6 +494,10 @@ def scocg_solve_csr_noalloc(rowptr32, col, val, shifts, rhs, proj_idx=None, proj
     z, zp = _shifts(shifts)
     K = z.size
     n = rowptr32.numel() - 1
+    _need(rowptr32, torch.int32, None, "rowptr32")
+    _need(col, torch.int32, None, "col")
+    _need(val, torch.float64, col.numel(), "val")
+    _need(rhs, torch.complex128, n, "rhs")
     pidx_p = pvec_p = None
     if proj_idx is not None:
         pidx = np.ascontiguousarray(np.asarray(proj_idx, dtype=np.int64).ravel())
@@ -473,9 +505,11 @@ def scocg_solve_csr_noalloc(rowptr32, col, val, shifts, rhs, proj_idx=None, proj
         pidx_p = pidx.ctypes.data
     else:
         M = proj_vec.shape[0] if proj_vec.dim() == 2 else 1
+        _need(proj_vec, torch.complex128, M * n, "proj_vec")
         pvec_p = _dev(proj_vec)
     if G_out is None:
         G_out = torch.zeros((M, K), dtype=torch.complex128, device=rhs.device)
+    _need(G_out, torch.complex128, M * K, "G_out")
     info, it, rs = _info_struct(1, K)
     code = lib().scocg_solve_csr_noalloc(n, col.numel(), _dev(rowptr32), _dev(col), _dev(val), zp, K, _dev(rhs),
                                          pidx_p, pvec_p, M, float(tol), int(max_iter), _dev(G_out),

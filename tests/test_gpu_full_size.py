@@ -24,7 +24,7 @@ from paper_0802_0748_gb300 import inputs
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-BATCH_BOUNDS = (-6.041048698881869, 5.997536652116761)
+BATCH_BOUNDS = inputs.BATCH32_BOUNDS
 
 
 @pytest.fixture(scope="module")

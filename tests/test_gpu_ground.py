@@ -1,5 +1,5 @@
-"""Ground state by Lanczos + CG inverse iteration (Sec. II.C) and the
-one-particle excitation vectors c|psi_0>, c+|psi_0> (Sec. IV.D) through the C
+"""Ground state by Lanczos + CG inverse iteration (Sec. II.B) and the
+one-particle excitation vectors c|psi_0>, c+|psi_0> (Sec. IV.B) through the C
 ABI, against the oracle: the dense eigenpair (the definition), closed forms,
 the Jordan-Wigner operators bit for bit, the ionization spectrum end to end,
 and at the 14-site size sampled rows of H psi - E psi and sampled entries of

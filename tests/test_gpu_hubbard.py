@@ -1,4 +1,4 @@
-"""GPU matrix-free extended Hubbard model (Sec. IV.D) against the oracle's
+"""GPU matrix-free extended Hubbard model (Sec. IV.B) against the oracle's
 literal Jordan-Wigner construction: bit-exact basis tables and H apply (all
 matrix elements are small integers at t=1, U=4, V=1), FP64 solve parity."""
 import numpy as np

@@ -217,7 +217,7 @@ def test_stopping_and_breakdown_edges(oracle_mod):
 
 # ---------------------------------------------------------------- Hubbard
 def test_paper_sector_dimension(oracle_mod):
-    """(16 C 6)^2 = 64,128,064 (Sec. IV.D) and (14 C 7)^2 = 11,778,624 by enumeration."""
+    """(16 C 6)^2 = 64,128,064 (Sec. IV.B) and (14 C 7)^2 = 11,778,624 by enumeration."""
     g = json.load(open(os.path.join(GOLDEN, "paper_numbers.json")))["hubbard_sector_dim"]
     d = oracle_mod.sector_dim(g["modes_per_spin"], g["electrons_per_spin"])
     assert d * d == g["value"] == 64128064

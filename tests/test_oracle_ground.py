@@ -1,5 +1,5 @@
-"""Pins for the ground-state and excitation part of the oracle (Sec. II.C,
-Sec. IV.D) against what the mathematics fixes: dense eigen-decomposition,
+"""Pins for the ground-state and excitation part of the oracle (Sec. II.B,
+Sec. IV.B) against what the mathematics fixes: dense eigen-decomposition,
 closed forms (free fermions on a ring, two sites), the canonical
 anticommutation relations, the Kronecker-product construction of the
 Jordan-Wigner operators, sum rules and the high-energy expansion of G.  A
