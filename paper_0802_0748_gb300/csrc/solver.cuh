@@ -97,7 +97,7 @@ __device__ __forceinline__ void lane_add(float4& acc, int o) {   // compensated:
     w.y = __shfl_xor_sync(0xffffffffu, acc.y, o);
     w.z = __shfl_xor_sync(0xffffffffu, acc.z, o);
     w.w = __shfl_xor_sync(0xffffffffu, acc.w, o);
-    acc = cpack(df_add(df_norm(acc.x, acc.z), df_norm(w.x, w.z)), df_add(df_norm(acc.y, acc.w), df_norm(w.y, w.w)));
+    acc = vadd_acc(acc, w);
 }
 
 template <typename R, int LPR>
@@ -178,23 +178,20 @@ struct ApplyBSR4 {
         int s0 = unit_off[unit], s1 = unit_off[unit + 1];
         if (!chk(dbg, 4, s1, nslots + 1) || !chk(dbg, 4, s0, s1 + 1)) s0 = s1 = 0;
         VV acc = vzero<VV>();
-        int s = s0;
-        for (; s + 4 <= s1; s += 4) {                 // four slots in flight
+        for (int s = s0; s < s1; s += 4) {            // four slots in flight; the last group predicated
             int cb[4];
             R v[4][4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                cb[j] = ld_stream(bcol + (size_t)(s + j) * 8 + br);
-                load_row(bval + ((size_t)(s + j) * 8 + br) * 16 + rr * 4, v[j]);
+                if (s + j < s1) {
+                    cb[j] = ld_stream(bcol + (size_t)(s + j) * 8 + br);
+                    load_row(bval + ((size_t)(s + j) * 8 + br) * 16 + rr * 4, v[j]);
+                } else {
+                    cb[j] = -1;
+                }
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) block_fma(acc, cb[j], v[j], x);
-        }
-        for (; s < s1; ++s) {
-            R v[4];
-            const int cb = ld_stream(bcol + (size_t)s * 8 + br);
-            load_row(bval + ((size_t)s * 8 + br) * 16 + rr * 4, v);
-            block_fma(acc, cb, v, x);
         }
         if (row < n) {
             w = vsub(vcfma(zs, x[row], vzero<VV>()), acc);

@@ -69,12 +69,15 @@ __device__ __forceinline__ void acc_bil(float& re, float& im, float2 u, float2 v
 }
 __device__ __forceinline__ void acc_nrm(double& s, double2 u) { s = fma(u.x, u.x, fma(u.y, u.y, s)); }
 __device__ __forceinline__ void acc_nrm(float& s, float2 u) { s = fmaf(u.x, u.x, fmaf(u.y, u.y, s)); }
-// compensated: products exact to DF, sums with TwoSum
+// compensated: products exact to DF, sums with TwoSum; the real and
+// imaginary parts as one packed pair, (re, im) += (u.re, u.re) (v.re, v.im)
+// + (-u.im, u.im) (v.im, v.re)
 __device__ __forceinline__ void acc_bil(dfs& re, dfs& im, float4 u, float4 v) {
-    df_acc_prod(re, cre(u), cre(v));
-    df_acc_prod(re, df_neg(cim(u)), cim(v));
-    df_acc_prod(im, cre(u), cim(v));
-    df_acc_prod(im, cim(u), cre(v));
+    float2 h = make_float2(re.hi, im.hi), l = make_float2(re.lo, im.lo);
+    pk_acc_prod(h, l, make_float2(u.x, u.x), make_float2(u.z, u.z), hi2(v), lo2(v));
+    pk_acc_prod(h, l, make_float2(-u.y, u.y), make_float2(-u.w, u.w), make_float2(v.y, v.x), make_float2(v.w, v.z));
+    re = dfs{h.x, l.x};
+    im = dfs{h.y, l.y};
 }
 __device__ __forceinline__ void acc_nrm(dfs& s, float4 u) {
     df_acc_prod(s, cre(u), cre(u));
@@ -93,10 +96,14 @@ __device__ __forceinline__ void acc_rr(AT& re, AT& im, AT& nrm, V ri) {
 // accuracy of 1e-7 is ample.
 template <>
 __device__ __forceinline__ void acc_rr<dfs, float4>(dfs& re, dfs& im, dfs& nrm, float4 ri) {
-    const dfs x = cre(ri), y = cim(ri);
-    df_acc_prod(re, x, x);
-    df_acc_prod(re, df_neg(y), y);
-    df_acc_prod(im, dfs{2.f * x.hi, 2.f * x.lo}, y);
+    // (re, im) += (x, x) (x, 2y) + (-y, 0) (y, 0), packed
+    float2 h = make_float2(re.hi, im.hi), l = make_float2(re.lo, im.lo);
+    pk_acc_prod(h, l, make_float2(ri.x, ri.x), make_float2(ri.z, ri.z), make_float2(ri.x, 2.f * ri.y),
+                make_float2(ri.z, 2.f * ri.w));
+    pk_acc_prod(h, l, make_float2(-ri.y, 0.f), make_float2(-ri.w, 0.f), make_float2(ri.y, 0.f),
+                make_float2(ri.w, 0.f));
+    re = dfs{h.x, l.x};
+    im = dfs{h.y, l.y};
     nrm.hi = fmaf(ri.x, ri.x, fmaf(ri.y, ri.y, nrm.hi));
 }
 
@@ -708,8 +715,12 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
 // thread) hide the latency of the FP32-pipe modes; FP64 solves are bound by
 // the FP64 pipe, where one CTA per SM (128 registers, half the CTAs at every
 // grid barrier) measured faster.
+#ifndef SCOCG_DF_CTAS_PER_SM
+#define SCOCG_DF_CTAS_PER_SM 2
+#endif
 template <typename R> struct MinBlocks { static constexpr int value = 2; };
 template <> struct MinBlocks<double> { static constexpr int value = 1; };
+template <> struct MinBlocks<DF> { static constexpr int value = SCOCG_DF_CTAS_PER_SM; };
 
 template <typename R, class Apply>
 __global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) cocg_persistent(SolveArgs<R> a, Apply ap) {
