@@ -13,6 +13,8 @@ Contents (each function cites the passage of arXiv:0802.0748 it follows):
 * ``apply_shifted``      y = (z I - H) x (Eq. lin_eq's matrix).
 * ``hubbard_csr``        extended Hubbard sector Hamiltonian from the literal
                          Jordan-Wigner definition (Sec. IV.B).
+* ``grad_from_vectors``  dL/dH on the stored entries from the full solutions of
+                         the forward and adjoint shifted systems.
 * ``dense``              dense LU Green's functions, closed forms, Fock-space
                          exact diagonalisation, dense gradients.
 * ``ground``             Lanczos / CG-inverse-iteration ground state and the
@@ -159,3 +161,28 @@ def hubbard_csr(L, n_up, n_dn, t, U, V, periodic=True):
     nnz2 = f(L, n_up, n_dn, t, U, V, int(periodic), _ptr(rowptr), _ptr(col), _ptr(val))
     assert nnz2 == nnz
     return rowptr, col, val
+
+
+def grad_from_vectors(rowptr, col, X, Y, gbar) -> np.ndarray:
+    """Gradient of a real loss L(G) with respect to every stored value of H.
+
+    G_k = c^T (z_k I - H)^{-1} b (Eq. gf with a projection c), so with
+    x_k = (z_k I - H)^{-1} b and y_k = (z_k I - H)^{-T} c (the same matrix: it is
+    complex symmetric, Sec. III.C) the derivative by one stored entry (a, b)
+    treated as an independent parameter is dG_k/dH_ab = y_k[a] x_k[b]; for
+    gbar_k = dL/dRe G_k + i dL/dIm G_k, dL/dH_ab = Re sum_k conj(gbar_k)
+    y_k[a] x_k[b].  X, Y: [nshift][n] complex; returns float64 [nnz] in CSR order.
+    """
+    rowptr = np.asarray(rowptr, dtype=np.int64)
+    col = np.asarray(col, dtype=np.int64)
+    X = np.asarray(X, dtype=np.complex128)
+    Y = np.asarray(Y, dtype=np.complex128)
+    w = np.conj(np.asarray(gbar, dtype=np.complex128))
+    rows = np.repeat(np.arange(rowptr.size - 1, dtype=np.int64), np.diff(rowptr))
+    g = np.zeros(col.size, dtype=np.float64)
+    step = 1 << 16
+    for e0 in range(0, col.size, step):            # sum over k for a block of entries
+        a = rows[e0:e0 + step]
+        bcol = col[e0:e0 + step]
+        g[e0:e0 + step] = np.real(np.einsum("k,ke,ke->e", w, Y[:, a], X[:, bcol]))
+    return g

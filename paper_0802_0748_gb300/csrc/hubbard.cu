@@ -24,6 +24,10 @@
 #include "solver_kernel.cuh"
 #include "vector_ops.cuh"
 
+#ifndef SCOCG_HOP_GROUP
+#define SCOCG_HOP_GROUP 4
+#endif
+
 namespace scocg {
 
 template <typename VV> struct Scal;
@@ -107,9 +111,43 @@ struct ApplyHubbard {
         return (x >> 1) | (ring ? ((x & 1u) << (L - 1)) : 0u);
     }
 
-    // Compensated vectors: the diagonal U n_up n_dn + V n_i n_j and the hop
-    // amplitude t are taken as float pairs (exact for values such as t = 1,
-    // U = 4, V = 1), products exact to the pair precision, sums with TwoSum.
+    // Compensated vectors: the signed hop terms are summed first (each a
+    // TwoSum of +-x into a compensated pair, real and imaginary parts packed),
+    // then multiplied once by t; the diagonal U n_up n_dn + V n_i n_j and t are
+    // taken as float pairs (exact for values such as t = 1, U = 4, V = 1).  The
+    // hop lists are read kHopGroup entries at a time: the table entries, then
+    // their gathers, are issued together (each list ends at its first -1).
+    static constexpr int kHopGroup = SCOCG_HOP_GROUP;
+    __device__ __forceinline__ static void hop_acc_df(const int32_t* tab, int S, const float4* base, int64_t stride,
+                                                      int64_t lim, unsigned long long* dbg, float2& h, float2& l) {
+        for (int j0 = 0; j0 < S; j0 += kHopGroup) {
+            int e[kHopGroup];
+#pragma unroll
+            for (int q = 0; q < kHopGroup; ++q) {
+                e[q] = j0 + q < S ? tab[j0 + q] : -1;
+                if (e[q] >= 0 && !chk(dbg, 20, e[q] >> 1, lim)) e[q] = -1;
+            }
+            float4 xv[kHopGroup];
+#pragma unroll
+            for (int q = 0; q < kHopGroup; ++q) xv[q] = e[q] >= 0 ? base[(int64_t)(e[q] >> 1) * stride] : vzero<float4>();
+#pragma unroll
+            for (int q = 0; q < kHopGroup; ++q) {
+                if (e[q] >= 0) {
+                    const unsigned sg = (unsigned)(e[q] & 1) << 31;    // the sign on the sign bits
+                    const float2 xh = make_float2(__uint_as_float(__float_as_uint(xv[q].x) ^ sg),
+                                                  __uint_as_float(__float_as_uint(xv[q].y) ^ sg));
+                    const float2 xl = make_float2(__uint_as_float(__float_as_uint(xv[q].z) ^ sg),
+                                                  __uint_as_float(__float_as_uint(xv[q].w) ^ sg));
+                    float2 t, er;
+                    pk_two_sum(h, xh, t, er);
+                    h = t;
+                    l = pk_add(l, pk_add(er, xl));
+                }
+            }
+            if (e[kHopGroup - 1] < 0) break;
+        }
+    }
+
     __device__ __forceinline__ bool operator()(int64_t unit, int lane, float4 zs, const float4* x, int64_t& row,
                                                float4& w) const {
         const int u = (int)(unit % D_up);
@@ -120,32 +158,18 @@ struct ApplyHubbard {
         const uint32_t pu = partner(su), pd = partner(sd);
         const int cu = __popc(su & sd);
         const int cv = __popc(su & pu) + __popc(sd & pd) + __popc(su & pd) + __popc(sd & pu);
+        float2 h = make_float2(0.f, 0.f), l = make_float2(0.f, 0.f);
+        hop_acc_df(hop_dn + (size_t)d * S, S, x + (size_t)u * D_dn, 1, D_dn, dbg, h, l);
+        hop_acc_df(hop_up + (size_t)u * S, S, x + d, D_dn, D_up, dbg, h, l);
+        pk_norm(h, l);
         const float4 dg = df_from(c2(U * (double)cu + V * (double)cv, 0.0));
         const dfs zr = df_add(cre(zs), df_neg(cre(dg)));
-        float4 acc = vcfma(cpack(zr, cim(zs)), x[row], vzero<float4>());   // (z_s - diag) x_row
-        dfs ar = cre(acc), ai = cim(acc);
-        const float4 tp = df_from(c2(t, 0.0));
-        const dfs tt = cre(tp), mt = df_neg(tt);
-        const float4* xrow = x + (size_t)u * D_dn;
-        for (int j = 0; j < S; ++j) {
-            const int e = hop_dn[(size_t)d * S + j];
-            if (e < 0) break;
-            if (!chk(dbg, 20, e >> 1, D_dn)) continue;
-            const float4 xv = xrow[e >> 1];
-            const dfs c = (e & 1) ? mt : tt;
-            df_acc_prod(ar, c, cre(xv));
-            df_acc_prod(ai, c, cim(xv));
-        }
-        for (int j = 0; j < S; ++j) {
-            const int e = hop_up[(size_t)u * S + j];
-            if (e < 0) break;
-            if (!chk(dbg, 21, e >> 1, D_up)) continue;
-            const float4 xv = x[(size_t)(e >> 1) * D_dn + d];
-            const dfs c = (e & 1) ? mt : tt;
-            df_acc_prod(ar, c, cre(xv));
-            df_acc_prod(ai, c, cim(xv));
-        }
-        w = cpack(df_norm(ar.hi, ar.lo), df_norm(ai.hi, ai.lo));
+        const float4 acc = vcfma(cpack(zr, cim(zs)), x[row], vzero<float4>());   // (z_s - diag) x_row
+        float2 ah = hi2(acc), al = lo2(acc);
+        const float4 tp = df_from(c2(t, 0.0));   // - H's hopping part: + t sum sign x
+        pk_acc_prod(ah, al, make_float2(tp.x, tp.x), make_float2(tp.z, tp.z), h, l);
+        pk_norm(ah, al);
+        w = pk4(ah, al);
         return true;
     }
 

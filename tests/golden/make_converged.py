@@ -16,6 +16,11 @@ sets the oracle's thread count):
     python tests/golden/make_converged.py anderson   # 64^3 x 4, 512 shifts, eta 1e-3
     python tests/golden/make_converged.py hubbard    # 14-site ring, 128 shifts, eta 0.05
     python tests/golden/make_converged.py batch      # 32^3 x 4, 4 of the 256 unit rhs, eta 1e-2
+    python tests/golden/make_converged.py adjoint    # 24^3 x 4 gradient dL/dH, 128 shifts, eta 0.02
+
+The adjoint file holds the oracle gradient (oracle.grad_from_vectors on the
+oracle's full per-shift solutions, residual 1e-13) of L = sum_k w_k Im G_00(z_k)
+on a seeded sample of the stored entries plus the entries of largest |g|.
 """
 from __future__ import annotations
 
@@ -37,6 +42,7 @@ TOL = 1e-12
 MAX_ITER = 600000
 N_EXTRA = 16
 BATCH_RHS = (0, 77, 150, 255)
+ADJOINT_BOUNDS = (-6.0, 6.4)     # the bounds the gradient benchmark and tests use
 
 
 def shift_subset(shifts: np.ndarray, draw_seed: int) -> tuple[np.ndarray, int]:
@@ -111,9 +117,32 @@ def make_batch() -> dict:
     return out
 
 
+def make_adjoint() -> dict:
+    wl = inputs.workload("adjoint", "full", bounds=ADJOINT_BOUNDS)
+    h = wl.csr
+    t0 = time.time()
+    res = oracle.shifted_cocg(h.rowptr, h.col, h.val, wl.shifts, wl.rhs[0], proj_idx=[0], tol=1e-13,
+                              max_iter=MAX_ITER, want_x=True)
+    if res.status != oracle.OK:
+        raise RuntimeError(f"oracle status {res.status}")
+    gbar = 1j * wl.weights
+    g = oracle.grad_from_vectors(h.rowptr, h.col, res.X, res.X, gbar)   # c = b = e_0: y_k = x_k
+    rng = np.random.default_rng(44)
+    sample = rng.choice(h.nnz, size=4096, replace=False)
+    top = np.argsort(np.abs(g))[::-1][:64]
+    idx = np.unique(np.concatenate([sample, top])).astype(np.int64)
+    return {"workload": "anderson-24^3x4 seed 4, b = c = e_0, 128 shifts linspace over ADJOINT_BOUNDS + 0.02 i, "
+                        "L = sum_k w_k Im G_00(z_k), w = workload weights",
+            "bounds": list(ADJOINT_BOUNDS), "shifts": cplx_list(wl.shifts), "val_checksum": checksum(h.val),
+            "weights": [float(x) for x in wl.weights], "g_inf_norm": float(np.abs(g).max()),
+            "entries": idx.tolist(), "g": [float(x) for x in g[idx]], "n_iter": res.n_iter,
+            "resid_max": float(res.resid.max()), "cpu_seconds": time.time() - t0, "tol": 1e-13}
+
+
 MAKERS = {"anderson": (make_anderson, "anderson64x4_converged.json"),
           "hubbard": (make_hubbard, "hubbard14_converged.json"),
-          "batch": (make_batch, "batch32x4_converged.json")}
+          "batch": (make_batch, "batch32x4_converged.json"),
+          "adjoint": (make_adjoint, "adjoint24x4_gradient.json")}
 
 
 def main(argv):
@@ -121,7 +150,8 @@ def main(argv):
     for name in names:
         fn, fname = MAKERS[name]
         data = fn()
-        data.update({"oracle": "oracle.shifted_cocg (FP64, full per-shift vectors)", "tol": TOL,
+        data.setdefault("tol", TOL)
+        data.update({"oracle": "oracle.shifted_cocg (FP64, full per-shift vectors)",
                      "command": f"python tests/golden/make_converged.py {name}"})
         (HERE / fname).write_text(json.dumps(data, indent=1) + "\n")
         print(name, "done", data.get("n_iter"), flush=True)

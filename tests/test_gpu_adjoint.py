@@ -1,6 +1,9 @@
 """GPU full-vector solve and adjoint gradient (through the C ABI) against the
-oracle's full-vector solutions, dense references and central finite
-differences."""
+oracle's full-vector solutions and gradient, dense references and central
+finite differences."""
+import json
+from pathlib import Path
+
 import numpy as np
 import pytest
 
@@ -137,14 +140,11 @@ def test_config4_finite_differences(S):
     g = g.cpu().numpy()
     assert np.all(np.isfinite(g))
     rows = np.repeat(np.arange(h.n), np.diff(h.rowptr))
-    # Central differences at step 1e-6 carry the loss's rounding (~1e-13 of a
-    # converged solve) divided by 2e-6, about 5e-8 absolute: entries whose
-    # gradient is a small fraction of the largest cannot be resolved to 1e-5
-    # relative at this step, so the sample is drawn from entries of at least 5%
-    # of the largest magnitude.
-    big = np.where((np.abs(g) >= 5e-2 * np.abs(g).max()) & (rows <= h.col))[0]
+    # the sample: 20 seeded symmetric pairs among the entries with |g| of at
+    # least 1e-3 of the largest, measured by |fd - g| / max(|g|, 1e-3 max|g|)
+    big = np.where((np.abs(g) >= 1e-3 * np.abs(g).max()) & (rows <= h.col))[0]
     pick = np.random.default_rng(4).choice(big, size=min(20, big.size), replace=False)
-    assert pick.size >= 10
+    assert pick.size == 20
 
     def loss(vals):
         hh2 = S.scocg_create_csr(h.rowptr, h.col, vals)
@@ -164,3 +164,53 @@ def test_config4_finite_differences(S):
         fd = (loss(vp) - loss(vm)) / (2 * eps)
         an = g[v] + (g[mirror] if mirror != v else 0.0)
         assert abs(fd - an) / max(abs(an), 1e-3 * gmax) < 1e-5, (v, fd, an)
+
+
+def test_grad_over_several_shift_chunks(S):
+    """600 shifts: the gradient recomputes the per-shift vectors in chunks of at
+    most 512 (each chunk its own forward and adjoint solves) and sums the
+    chunks' contributions; equal to the dense-inverse gradient."""
+    h = inputs.anderson_csr(3, seed=9)
+    n = h.n
+    shifts = np.linspace(-5, 5, 600) + 0.08j
+    b = inputs.random_unit_complex(n, 5)
+    c = inputs.random_unit_complex(n, 6)
+    gbar = (np.random.default_rng(7).normal(size=600) + 1j * np.random.default_rng(8).normal(size=600))[None, :]
+    hh = S.scocg_create_csr(h.rowptr, h.col, h.val)
+    g, info = S.scocg_grad(hh, shifts, cuda(b), cuda(gbar), proj_vec=cuda(c[None, :]), tol=1e-13)
+    S.scocg_destroy(hh)
+    assert info["status"] == 0
+    gd = dense.grad_dense(h.dense(), shifts, b, c, gbar[0])
+    rows = np.repeat(np.arange(n), np.diff(h.rowptr))
+    ref = gd[rows, h.col]
+    assert np.max(np.abs(g.cpu().numpy() - ref)) < 1e-8 * np.max(np.abs(ref))
+
+
+def test_config4_gradient_vs_oracle_gradient(S):
+    """24^3 x 4 Anderson (55,296 rows, 1,548,288 stored values), 128 shifts, eta
+    0.02: dL/dH from the adjoint kernel against the oracle gradient (the
+    oracle's full per-shift solutions at residual 1e-13 through
+    oracle.grad_from_vectors; tests/golden/adjoint24x4_gradient.json) on 4,096
+    seeded entries plus the 64 largest, element by element:
+    |g - g_oracle| <= 1e-8 max(|g_oracle|, 1e-3 max|g_oracle|)."""
+    p = Path(__file__).resolve().parent / "golden" / "adjoint24x4_gradient.json"
+    if not p.exists():
+        pytest.skip("adjoint24x4_gradient.json not generated (python tests/golden/make_converged.py adjoint)")
+    gold = json.loads(p.read_text())
+    wl = inputs.workload("adjoint", "full", bounds=tuple(gold["bounds"]))
+    h = wl.csr
+    zs = np.asarray(gold["shifts"])
+    np.testing.assert_array_equal(wl.shifts, zs[:, 0] + 1j * zs[:, 1])
+    np.testing.assert_array_equal(wl.weights, np.asarray(gold["weights"]))
+    assert np.allclose([h.val.sum(), (h.val * h.val).sum()], gold["val_checksum"], rtol=1e-12)
+    hh = S.scocg_create_csr(h.rowptr, h.col, h.val)
+    gbar = (1j * wl.weights).astype(np.complex128)[None, :]
+    g, info = S.scocg_grad(hh, wl.shifts, cuda(wl.rhs[0]), cuda(gbar), proj_idx=[0], tol=1e-13)
+    S.scocg_destroy(hh)
+    assert info["status"] == 0
+    idx = np.asarray(gold["entries"])
+    ref = np.asarray(gold["g"])
+    got = g.cpu().numpy()[idx]
+    gmax = gold["g_inf_norm"]
+    err = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-3 * gmax)
+    assert err.max() < 1e-8, (float(err.max()), int(idx[err.argmax()]))

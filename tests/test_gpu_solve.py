@@ -148,7 +148,9 @@ def test_fixed_iterations_after_switch(S, oracle_mod):
                                   max_iter=30, seed=0)
     assert info["n_switch"] == ref.n_switch >= 1
     assert np.array_equal(info["freeze_iter"][0], ref.iters)
-    assert relerr(g, ref.G) < 1e-9
+    # a 2^-53 relative perturbation of b moves the oracle's own G here by at
+    # most 1.4e-11 (20 draws), so the FP64 bound holds at 30 iterations
+    assert relerr(g, ref.G) < 1e-10
 
 
 def test_not_converged_and_zero_rhs(S, oracle_mod):
@@ -266,7 +268,10 @@ def test_config2_full_size_fixed_iterations(S, oracle_mod):
     seed = oracle_mod.default_seed(wl.shifts)
     sample = np.unique(np.concatenate([[seed], np.linspace(0, 511, 11).astype(int)]))
     # every dot product is a 1M-term sum whose rounding depends on the summation
-    # order (~sqrt(N) eps ~ 2e-13); the recurrences amplify it with the step count
+    # order; the recurrences amplify such rounding-level changes with the step
+    # count: measured on the oracle itself, a 2^-53 relative perturbation of b
+    # moves this G by 1.4e-12 after 12 iterations and by 1.2e-10 after 25, so
+    # the 1e-10 bound holds at 12 and 25 iterations get 1e-9
     for n_it, bound in ((12, 1e-10), (25, 1e-9)):
         g, info = gpu_solve(S, h, wl.shifts, wl.rhs[0], proj_vec=wl.proj_vec, tol=0.0,
                             opts=S.SolveOptions(max_iter=n_it))

@@ -365,3 +365,26 @@ def test_density_quadrature_converges_to_eigenstate_sum():
         errs.append(abs(dense.density_quadrature(G, grid, mu, kT)[0] - exact))
     assert errs[2] < 0.65 * errs[1] < 0.65 ** 2 * errs[0]
     assert errs[2] < 1e-2
+
+
+def test_vector_gradient_equals_dense_gradient(oracle_mod):
+    """The gradient from the oracle's full shifted-COCG solutions (forward with b,
+    adjoint with c) equals the dense-inverse gradient on every stored entry;
+    with c = b the adjoint solutions are the forward ones."""
+    h = inputs.anderson_csr(3, seed=8)
+    n = h.n
+    shifts = np.linspace(-4, 4, 9) + 0.07j
+    b = inputs.random_unit_complex(n, 3)
+    c = inputs.random_unit_complex(n, 4)
+    gbar = np.random.default_rng(5).normal(size=9) + 1j * np.random.default_rng(6).normal(size=9)
+    X = oracle_mod.shifted_cocg(h.rowptr, h.col, h.val, shifts, b, proj_idx=[0], tol=1e-14, want_x=True).X
+    Y = oracle_mod.shifted_cocg(h.rowptr, h.col, h.val, shifts, c, proj_idx=[0], tol=1e-14, want_x=True).X
+    rows = np.repeat(np.arange(n), np.diff(h.rowptr))
+    for yy, cc in ((Y, c), (X, b)):
+        g = oracle_mod.grad_from_vectors(h.rowptr, h.col, X, yy, gbar)
+        ref = dense.grad_dense(h.dense(), shifts, b, cc, gbar)[rows, h.col]
+        assert np.max(np.abs(g - ref)) < 1e-10 * np.max(np.abs(ref))
+    # a transposed operand (x_k[a] y_k[b]) is a different gradient when c != b
+    gt = oracle_mod.grad_from_vectors(h.rowptr, h.col, Y, X, gbar)
+    ref = dense.grad_dense(h.dense(), shifts, b, c, gbar)[rows, h.col]
+    assert np.max(np.abs(gt - ref)) > 1e-3 * np.max(np.abs(ref))
