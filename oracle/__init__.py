@@ -13,6 +13,9 @@ Contents (each function cites the passage of arXiv:0802.0748 it follows):
 * ``apply_shifted``      y = (z I - H) x (Eq. lin_eq's matrix).
 * ``hubbard_csr``        extended Hubbard sector Hamiltonian from the literal
                          Jordan-Wigner definition (Sec. IV.B).
+* ``hubbard2_csr``,      the two-orbital (doubly degenerate) extended Hubbard
+  ``hubbard2_rows``      model of Sec. IV.B: sector CSR, or sampled rows of H x
+                         for sectors too large for CSR.
 * ``grad_from_vectors``  dL/dH on the stored entries from the full solutions of
                          the forward and adjoint shifted systems.
 * ``dense``              dense LU Green's functions, closed forms, Fock-space
@@ -24,6 +27,7 @@ Contents (each function cites the passage of arXiv:0802.0748 it follows):
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 from pathlib import Path
@@ -71,6 +75,11 @@ def lib():
         L.oracle_sector_dim.argtypes = [ctypes.c_int, ctypes.c_int]
         L.oracle_default_seed.restype = ctypes.c_int
         L.oracle_default_seed.argtypes = [ctypes.c_int, P]
+        h2 = [ctypes.c_int, ctypes.c_int, P, P, P] + [ctypes.c_double] * 5 + [ctypes.c_int, ctypes.c_int]
+        L.oracle_hubbard2_csr.restype = ctypes.c_int64
+        L.oracle_hubbard2_csr.argtypes = h2 + [P, P, P]
+        L.oracle_hubbard2_rows.restype = ctypes.c_int
+        L.oracle_hubbard2_rows.argtypes = h2 + [ctypes.c_int64, P, P, P]
         _lib = L
     return _lib
 
@@ -186,3 +195,48 @@ def grad_from_vectors(rowptr, col, X, Y, gbar) -> np.ndarray:
         bcol = col[e0:e0 + step]
         g[e0:e0 + step] = np.real(np.einsum("k,ke,ke->e", w, Y[:, a], X[:, bcol]))
     return g
+
+
+def _model2_args(model):
+    bi = np.ascontiguousarray([b[0] for b in model["bonds"]], dtype=np.int32)
+    bj = np.ascontiguousarray([b[1] for b in model["bonds"]], dtype=np.int32)
+    bt = np.ascontiguousarray(model["bond_t"], dtype=np.float64).reshape(-1, 2, 2)
+    if bt.shape[0] != bi.size:
+        raise ValueError("bond_t must hold one 2x2 block per bond")
+    keep = (bi, bj, bt)
+    args = [int(model["n_sites"]), int(bi.size), _ptr(bi), _ptr(bj), _ptr(bt), float(model["U"]),
+            float(model["Up"]), float(model["J"]), float(model["Jp"]), float(model["V"])]
+    return args, keep
+
+
+def hubbard2_csr(model, n_up, n_dn):
+    """Two-orbital extended Hubbard sector Hamiltonian (Sec. IV.B) in CSR, built
+    from the literal Jordan-Wigner definition of every term.  ``model``: dict
+    with n_sites, bonds [(i, j)], bond_t [nb][2][2], U, Up, J, Jp, V.
+    Returns (rowptr, col, val)."""
+    args, keep = _model2_args(model)
+    f = lib().oracle_hubbard2_csr
+    nnz = f(*args, int(n_up), int(n_dn), None, None, None)
+    if nnz < 0:
+        raise ValueError(f"hubbard2_csr failed ({nnz})")
+    M = 2 * int(model["n_sites"])
+    dim = math.comb(M, n_up) * math.comb(M, n_dn)
+    rowptr = np.zeros(dim + 1, dtype=np.int64)
+    col = np.zeros(nnz, dtype=np.int32)
+    val = np.zeros(nnz, dtype=np.float64)
+    nnz2 = f(*args, int(n_up), int(n_dn), _ptr(rowptr), _ptr(col), _ptr(val))
+    assert nnz2 == nnz
+    return rowptr, col, val
+
+
+def hubbard2_rows(model, n_up, n_dn, rows, x) -> np.ndarray:
+    """(H x)[rows] of the two-orbital model's sector, each row from the terms of
+    H applied to its basis state (for sectors too large for CSR)."""
+    args, keep = _model2_args(model)
+    r = np.ascontiguousarray(rows, dtype=np.int64)
+    xx = np.ascontiguousarray(x, dtype=np.complex128)
+    y = np.zeros(r.size, dtype=np.complex128)
+    st = lib().oracle_hubbard2_rows(*args, int(n_up), int(n_dn), r.size, _ptr(r), _ptr(xx), _ptr(y))
+    if st != 0:
+        raise ValueError(f"hubbard2_rows failed ({st})")
+    return y

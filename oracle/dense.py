@@ -11,6 +11,9 @@ Each function is the plain definition it names, with a library routine
 * ``fock_hubbard``    extended Hubbard Hamiltonian of Sec. IV.B built in the full
                       4^L Fock space from Jordan-Wigner Kronecker products, then
                       restricted to an (N_up, N_dn) sector.
+* ``fock_hubbard2``   the two-orbital extended Hubbard model of Sec. IV.B
+                      (Kanamori on-site interaction) in the full Fock space of
+                      a small cluster, plus its spin operators.
 * ``grad_dense``      dG/dH_ab = (A^{-T} c)_a (A^{-1} b)_b from the dense inverse.
 * ``fermi``, ``density_exact``, ``density_quadrature``  the density matrix of
                       Eqs. densityM-1 / densityM: the Fermi-weighted eigenstate
@@ -148,6 +151,103 @@ def two_site_spectrum(t: float, U: float, V: float) -> np.ndarray:
     """Two sites, one bond, one up and one down electron: {V, U, (U+V)/2 +- sqrt(((U-V)/2)^2 + 4t^2)}."""
     s = math.sqrt(((U - V) / 2) ** 2 + 4 * t * t)
     return np.sort(np.array([V, U, (U + V) / 2 - s, (U + V) / 2 + s]))
+
+
+def fock_hubbard2(model):
+    """Two-orbital extended Hubbard Hamiltonian (Sec. IV.B) on the full Fock
+    space of 4 ns modes from Jordan-Wigner Kronecker products:
+
+      H = sum_bonds sum_ab sum_s t_ab (c+_ias c_jbs + h.c.) + U sum_ia n_ia,up n_ia,dn
+        + U' sum_i n_i0 n_i1 - J sum_is n_i0s n_i1s
+        + J sum_is c+_i0s c+_i1s' c_i0s' c_i1s + J' sum_i (c+_i0u c+_i0d c_i1d c_i1u + h.c.)
+        + V sum_bonds n_i n_j.
+
+    Modes: spin s, site i, orbital a -> 2 i + a + s 2 ns (mode 0 is the most
+    significant bit of the Kronecker index).  Returns (H, c, M) with c the list
+    of annihilators."""
+    ns = int(model["n_sites"])
+    M = 4 * ns
+    c = _jw_annihilators(M)
+    cd = [x.T for x in c]
+    num = [cd[m] @ c[m] for m in range(M)]
+    mode = lambda i, a, s: 2 * i + a + s * 2 * ns
+    H = np.zeros((2 ** M, 2 ** M))
+    for (i, j), t in zip(model["bonds"], np.asarray(model["bond_t"], dtype=np.float64).reshape(-1, 2, 2)):
+        for a in range(2):
+            for b in range(2):
+                for s in range(2):
+                    H += t[a, b] * (cd[mode(i, a, s)] @ c[mode(j, b, s)] + cd[mode(j, b, s)] @ c[mode(i, a, s)])
+        ni = sum(num[mode(i, a, s)] for a in range(2) for s in range(2))
+        nj = sum(num[mode(j, a, s)] for a in range(2) for s in range(2))
+        H += model["V"] * ni @ nj
+    for i in range(ns):
+        for a in range(2):
+            H += model["U"] * num[mode(i, a, 0)] @ num[mode(i, a, 1)]
+        n0 = num[mode(i, 0, 0)] + num[mode(i, 0, 1)]
+        n1 = num[mode(i, 1, 0)] + num[mode(i, 1, 1)]
+        H += model["Up"] * n0 @ n1
+        for s in range(2):
+            so = 1 - s
+            H -= model["J"] * num[mode(i, 0, s)] @ num[mode(i, 1, s)]
+            H += model["J"] * cd[mode(i, 0, s)] @ cd[mode(i, 1, so)] @ c[mode(i, 0, so)] @ c[mode(i, 1, s)]
+        P = cd[mode(i, 0, 0)] @ cd[mode(i, 0, 1)] @ c[mode(i, 1, 1)] @ c[mode(i, 1, 0)]
+        H += model["Jp"] * (P + P.T)
+    return H, c, M
+
+
+def fock_spin2(ns: int, c):
+    """Total S^2 and S_z of the two-orbital cluster (modes as in fock_hubbard2)."""
+    M = 4 * ns
+    cd = [x.T for x in c]
+    up = [2 * i + a for i in range(ns) for a in range(2)]
+    dn = [m + 2 * ns for m in up]
+    Sp = sum(cd[u] @ c[d] for u, d in zip(up, dn))
+    Sz = 0.5 * sum(cd[u] @ c[u] - cd[d] @ c[d] for u, d in zip(up, dn))
+    S2 = Sp.T @ Sp + Sz @ Sz + Sz
+    return S2, Sz
+
+
+def fock_sector2(H: np.ndarray, ns: int, n_up: int, n_dn: int) -> np.ndarray:
+    """Sector block of a two-orbital Fock-space operator in the basis index
+    rank_up * D_dn + rank_dn (per-spin strings of 2 ns bits, bit m = mode m,
+    ranked among same-popcount strings in ascending order)."""
+    L = 2 * ns
+    M = 2 * L
+    ups, dns = sector_states(L, n_up), sector_states(L, n_dn)
+    idx = []
+    for u in ups:
+        for d in dns:
+            bits = [(u >> i) & 1 for i in range(L)] + [(d >> i) & 1 for i in range(L)]
+            idx.append(sum(bits[m] << (M - 1 - m) for m in range(M)))
+    idx = np.array(idx)
+    return H[np.ix_(idx, idx)]
+
+
+def kanamori_two_electron_levels(U: float, Up: float, J: float, Jp: float) -> np.ndarray:
+    """One site, two orbitals, one up and one down electron: the four levels
+    U' - J (S_z = 0 partner of the triplet), U' + J, U - J', U + J'."""
+    return np.sort(np.array([Up - J, Up + J, U - Jp, U + Jp]))
+
+
+def hopping_matrix2(model) -> np.ndarray:
+    """Single-particle hopping matrix of one spin (index 2 i + a)."""
+    ns = int(model["n_sites"])
+    T = np.zeros((2 * ns, 2 * ns))
+    for (i, j), t in zip(model["bonds"], np.asarray(model["bond_t"], dtype=np.float64).reshape(-1, 2, 2)):
+        for a in range(2):
+            for b in range(2):
+                T[2 * i + a, 2 * j + b] += t[a, b]
+                T[2 * j + b, 2 * i + a] += t[a, b]
+    return T
+
+
+def free_fermion_spectrum2(model, n_up: int, n_dn: int) -> np.ndarray:
+    """All energies of the hopping part alone in a sector: sums of occupied
+    eigenvalues of the single-particle hopping matrix, for each spin."""
+    eps = np.linalg.eigvalsh(hopping_matrix2(model))
+    up = [sum(eps[list(c)]) for c in itertools.combinations(range(eps.size), n_up)]
+    dn = [sum(eps[list(c)]) for c in itertools.combinations(range(eps.size), n_dn)]
+    return np.sort(np.add.outer(np.array(up), np.array(dn)).ravel())
 
 
 def grad_dense(H: np.ndarray, shifts, b, c, gbar) -> np.ndarray:

@@ -423,3 +423,227 @@ int64_t oracle_hubbard_csr(int L, int n_up, int n_dn, double t, double U, double
     free(rank); free(up_states); free(dn_states); free(rank_up); free(rank_dn); free(rc); free(rv);
     return nnz;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Two-orbital extended Hubbard model in a fixed (N_up, N_dn) sector: the
+ * doubly degenerate model of Sec. IV.B (two orbitals per site, inter-site
+ * Coulomb V), with the on-site interaction in the Kanamori form:
+ *
+ *   H = sum_{bonds (i,j)} sum_{a,b} sum_s t^{ij}_{ab} (c+_{ias} c_{jbs} + c+_{jbs} c_{ias})
+ *     + U  sum_{i,a} n_{ia up} n_{ia dn}
+ *     + U' sum_i n_{i0} n_{i1}                      (n_{ia} = n_{ia up} + n_{ia dn})
+ *     - J  sum_i sum_s n_{i0s} n_{i1s}
+ *     + J  sum_i sum_s c+_{i0s} c+_{i1s'} c_{i0s'} c_{i1s}   (s' = the other spin)
+ *     + J' sum_i (c+_{i0 up} c+_{i0 dn} c_{i1 dn} c_{i1 up} + c+_{i1 up} c+_{i1 dn} c_{i0 dn} c_{i0 up})
+ *     + V  sum_{bonds (i,j)} n_i n_j                 (n_i = n_{i0} + n_{i1})
+ *
+ * Modes: within a spin, mode 2 i + a (site i, orbital a); all up-spin modes
+ * first, then all down-spin modes (offset 2 ns).  Every operator is applied
+ * literally with its Jordan-Wigner sign (-1)^(occupied modes before it).
+ * Basis: index = rank_up * D_dn + rank_dn, rank = position among the
+ * (2 ns)-bit strings of the same popcount in ascending order (found by
+ * enumeration).  t^{ij} is bond_t[b][a][b'] for bond b = (bond_i[b], bond_j[b]).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int ns, nb;
+    const int32_t *bi, *bj;
+    const double *bt;          /* [nb][2][2] */
+    double U, Up, J, Jp, V;
+    int n_up, n_dn;
+    int64_t D_dn;
+    const int32_t *rank;       /* [2^(2 ns)] rank among same-popcount strings */
+} h2_model;
+
+/* c_m (create = 0) or c+_m (create = 1) on occupation word *occ: returns the
+ * Jordan-Wigner sign, or 0 when the operator annihilates the state. */
+static int jw_apply(uint64_t *occ, int m, int create)
+{
+    const uint64_t bit = (uint64_t)1 << m;
+    if (((*occ & bit) != 0) == (create != 0)) return 0;
+    int c = 0;
+    for (int j = 0; j < m; ++j) c += (int)((*occ >> j) & 1u);
+    *occ ^= bit;
+    return (c & 1) ? -1 : 1;
+}
+
+static int64_t h2_index(const h2_model *m, uint64_t occ)
+{
+    const int M = 2 * m->ns;
+    const uint64_t mask = ((uint64_t)1 << M) - 1;
+    return (int64_t)m->rank[occ & mask] * m->D_dn + m->rank[(occ >> M) & mask];
+}
+
+/* sequence of operators (rightmost applied first): ops[k] = mode, cre[k] = 1 for c+ */
+static void h2_term(const h2_model *m, uint64_t occ, int nops, const int *ops, const int *cre, double coef,
+                    int32_t *rc, double *rv, int *cnt)
+{
+    if (coef == 0.0) return;
+    uint64_t o = occ;
+    int sg = 1;
+    for (int k = nops - 1; k >= 0; --k) {
+        const int s = jw_apply(&o, ops[k], cre[k]);
+        if (!s) return;
+        sg *= s;
+    }
+    rc[*cnt] = (int32_t)h2_index(m, o);
+    rv[*cnt] = coef * (double)sg;
+    ++*cnt;
+}
+
+/* All terms of H applied to basis state occ: H|occ> = sum_k rv[k] |rc[k]>
+ * (rc holds basis indices; duplicates not merged).  Returns the count. */
+static int h2_apply_state(const h2_model *m, uint64_t occ, int32_t *rc, double *rv)
+{
+    const int M = 2 * m->ns;
+    int cnt = 0;
+    double diag = 0.0;
+    for (int i = 0; i < m->ns; ++i) {
+        int n[2][2];   /* n[a][s] */
+        for (int a = 0; a < 2; ++a)
+            for (int s = 0; s < 2; ++s) n[a][s] = (int)((occ >> (2 * i + a + s * M)) & 1u);
+        diag += m->U * (double)(n[0][0] * n[0][1] + n[1][0] * n[1][1]);
+        diag += m->Up * (double)((n[0][0] + n[0][1]) * (n[1][0] + n[1][1]));
+        diag -= m->J * (double)(n[0][0] * n[1][0] + n[0][1] * n[1][1]);
+    }
+    for (int b = 0; b < m->nb; ++b) {
+        int ni = 0, nj = 0;
+        for (int a = 0; a < 2; ++a)
+            for (int s = 0; s < 2; ++s) {
+                ni += (int)((occ >> (2 * m->bi[b] + a + s * M)) & 1u);
+                nj += (int)((occ >> (2 * m->bj[b] + a + s * M)) & 1u);
+            }
+        diag += m->V * (double)(ni * nj);
+    }
+    if (diag != 0.0) { rc[cnt] = (int32_t)h2_index(m, occ); rv[cnt] = diag; ++cnt; }
+    /* hopping: t (c+_{i a s} c_{j b s} + c+_{j b s} c_{i a s}) */
+    for (int b = 0; b < m->nb; ++b)
+        for (int a = 0; a < 2; ++a)
+            for (int a2 = 0; a2 < 2; ++a2) {
+                const double t = m->bt[(size_t)b * 4 + a * 2 + a2];
+                for (int s = 0; s < 2; ++s) {
+                    const int mi = 2 * m->bi[b] + a + s * M, mj = 2 * m->bj[b] + a2 + s * M;
+                    const int o1[2] = {mi, mj}, c1[2] = {1, 0};
+                    const int o2[2] = {mj, mi}, c2[2] = {1, 0};
+                    h2_term(m, occ, 2, o1, c1, t, rc, rv, &cnt);
+                    h2_term(m, occ, 2, o2, c2, t, rc, rv, &cnt);
+                }
+            }
+    /* spin flip and pair hopping on every site */
+    for (int i = 0; i < m->ns; ++i) {
+        for (int s = 0; s < 2; ++s) {
+            const int so = 1 - s;
+            const int ops[4] = {2 * i + 0 + s * M, 2 * i + 1 + so * M, 2 * i + 0 + so * M, 2 * i + 1 + s * M};
+            const int cre[4] = {1, 1, 0, 0};
+            h2_term(m, occ, 4, ops, cre, m->J, rc, rv, &cnt);
+        }
+        const int p1[4] = {2 * i + 0, 2 * i + 0 + M, 2 * i + 1 + M, 2 * i + 1};
+        const int p2[4] = {2 * i + 1, 2 * i + 1 + M, 2 * i + 0 + M, 2 * i + 0};
+        const int pc[4] = {1, 1, 0, 0};
+        h2_term(m, occ, 4, p1, pc, m->Jp, rc, rv, &cnt);
+        h2_term(m, occ, 4, p2, pc, m->Jp, rc, rv, &cnt);
+    }
+    return cnt;
+}
+
+static int h2_setup(h2_model *m, int ns, int nb, const int32_t *bi, const int32_t *bj, const double *bt,
+                    double U, double Up, double J, double Jp, double V, int n_up, int n_dn,
+                    int32_t **rank_out, uint32_t **up_out, uint32_t **dn_out, int64_t *Du, int64_t *Dd)
+{
+    if (ns < 1 || ns > 10 || nb < 0 || n_up < 0 || n_dn < 0 || n_up > 2 * ns || n_dn > 2 * ns) return -1;
+    for (int b = 0; b < nb; ++b)
+        if (bi[b] < 0 || bi[b] >= ns || bj[b] < 0 || bj[b] >= ns || bi[b] == bj[b]) return -1;
+    const int M = 2 * ns;
+    const uint32_t full = 1u << M;
+    int32_t *rank = malloc(sizeof(int32_t) * full);
+    uint32_t *up = malloc(sizeof(uint32_t) * full), *dn = malloc(sizeof(uint32_t) * full);
+    if (!rank || !up || !dn) { free(rank); free(up); free(dn); return -3; }
+    int64_t cu = 0, cd = 0, cnt[33] = {0};
+    for (uint32_t s = 0; s < full; ++s) {
+        const int p = popcount_u32(s);
+        rank[s] = (int32_t)cnt[p]++;
+        if (p == n_up) up[cu++] = s;
+        if (p == n_dn) dn[cd++] = s;
+    }
+    m->ns = ns; m->nb = nb; m->bi = bi; m->bj = bj; m->bt = bt;
+    m->U = U; m->Up = Up; m->J = J; m->Jp = Jp; m->V = V; m->n_up = n_up; m->n_dn = n_dn;
+    m->D_dn = cd; m->rank = rank;
+    *rank_out = rank; *up_out = up; *dn_out = dn; *Du = cu; *Dd = cd;
+    return 0;
+}
+
+/* H of the sector in CSR (rows sorted by column, duplicates merged, exact
+ * zeros dropped).  Call with rowptr/col/val NULL for the nnz (returned), then
+ * with arrays of [dim+1], [nnz], [nnz]. */
+int64_t oracle_hubbard2_csr(int ns, int nb, const int32_t *bi, const int32_t *bj, const double *bt,
+                            double U, double Up, double J, double Jp, double V, int n_up, int n_dn,
+                            int64_t *rowptr, int32_t *col, double *val)
+{
+    h2_model m;
+    int32_t *rank; uint32_t *up, *dn; int64_t Du, Dd;
+    int st = h2_setup(&m, ns, nb, bi, bj, bt, U, Up, J, Jp, V, n_up, n_dn, &rank, &up, &dn, &Du, &Dd);
+    if (st) return st;
+    const int cap = 1 + 16 * nb + 6 * ns;
+    int32_t *rc = malloc(sizeof(int32_t) * cap);
+    double *rv = malloc(sizeof(double) * cap);
+    if (!rc || !rv) { free(rc); free(rv); free(rank); free(up); free(dn); return -3; }
+    const int M = 2 * ns;
+    int64_t nnz = 0;
+    if (rowptr) rowptr[0] = 0;
+    for (int64_t iu = 0; iu < Du; ++iu)
+        for (int64_t id = 0; id < Dd; ++id) {
+            const uint64_t occ = (uint64_t)up[iu] | ((uint64_t)dn[id] << M);
+            int c = h2_apply_state(&m, occ, rc, rv);
+            for (int x1 = 1; x1 < c; ++x1) {   /* insertion sort by column */
+                int32_t c0 = rc[x1]; double v0 = rv[x1]; int y = x1 - 1;
+                while (y >= 0 && rc[y] > c0) { rc[y + 1] = rc[y]; rv[y + 1] = rv[y]; --y; }
+                rc[y + 1] = c0; rv[y + 1] = v0;
+            }
+            int k = 0;
+            for (int x1 = 0; x1 < c; ++x1) {
+                if (k > 0 && rc[k - 1] == rc[x1]) rv[k - 1] += rv[x1];
+                else { rc[k] = rc[x1]; rv[k] = rv[x1]; ++k; }
+            }
+            for (int x1 = 0; x1 < k; ++x1) {
+                if (rv[x1] == 0.0) continue;
+                if (col) { col[nnz] = rc[x1]; val[nnz] = rv[x1]; }
+                ++nnz;
+            }
+            if (rowptr) rowptr[iu * Dd + id + 1] = nnz;
+        }
+    free(rc); free(rv); free(rank); free(up); free(dn);
+    return nnz;
+}
+
+/* y[r] = (H x)[rows[r]] for sampled rows of a sector too large for CSR: each
+ * row from the terms of H applied to its basis state (H is real symmetric, so
+ * row s holds the coefficients of H|s>).  x, y complex (re, im) pairs. */
+int oracle_hubbard2_rows(int ns, int nb, const int32_t *bi, const int32_t *bj, const double *bt,
+                         double U, double Up, double J, double Jp, double V, int n_up, int n_dn,
+                         int64_t nrows, const int64_t *rows, const double *x, double *y)
+{
+    h2_model m;
+    int32_t *rank; uint32_t *up, *dn; int64_t Du, Dd;
+    int st = h2_setup(&m, ns, nb, bi, bj, bt, U, Up, J, Jp, V, n_up, n_dn, &rank, &up, &dn, &Du, &Dd);
+    if (st) return st;
+    const int M = 2 * ns;
+    int bad = 0;
+#pragma omp parallel
+    {
+        const int cap = 1 + 16 * nb + 6 * ns;
+        int32_t *rc = malloc(sizeof(int32_t) * cap);
+        double *rv = malloc(sizeof(double) * cap);
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t r = 0; r < nrows; ++r) {
+            const int64_t s = rows[r];
+            if (!rc || !rv || s < 0 || s >= Du * Dd) { bad = 1; continue; }
+            const uint64_t occ = (uint64_t)up[s / Dd] | ((uint64_t)dn[s % Dd] << M);
+            const int c = h2_apply_state(&m, occ, rc, rv);
+            double re = 0.0, im = 0.0;
+            for (int k = 0; k < c; ++k) { re += rv[k] * x[2 * (size_t)rc[k]]; im += rv[k] * x[2 * (size_t)rc[k] + 1]; }
+            y[2 * r] = re; y[2 * r + 1] = im;
+        }
+        free(rc); free(rv);
+    }
+    free(rank); free(up); free(dn);
+    return bad ? -1 : 0;
+}

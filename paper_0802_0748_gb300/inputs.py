@@ -17,6 +17,10 @@ for them with the same structure):
                     single-precision copy of H is exact.
 * Hubbard ring parameters for the matrix-free extended Hubbard model of
   Sec. IV.B (the basis itself is built by each consumer).
+* ``sqrt8_cluster`` and ``eg_model`` -- the doubly degenerate (two-orbital)
+  extended Hubbard model on the sqrt(8) x sqrt(8) square-lattice cluster of
+  Sec. IV.B, with synthetic hopping and interaction values (the paper's own
+  parameter set is in a reference that is not available).
 
 All randomness comes from numpy's PCG64 (``np.random.default_rng(seed)``).
 """
@@ -30,6 +34,7 @@ import numpy as np
 __all__ = [
     "CSR", "chain_csr", "anderson_csr", "spectral_bounds", "random_unit_complex",
     "to_fp32_exact", "Workload", "workload", "cluster_sizes", "ANDERSON64_BOUNDS", "BATCH32_BOUNDS",
+    "sqrt8_cluster", "eg_model",
 ]
 
 # Spectral bounds (ARPACK, tol 1e-4) of the seed-2 64^3 x 4 Anderson matrix and
@@ -170,6 +175,50 @@ def cluster_sizes(nsys: int = 32, lmin: int = 14, lmax: int = 50, seed: int = 31
     return rng.integers(lmin, lmax + 1, size=nsys)
 
 
+def sqrt8_cluster() -> tuple[list[tuple[int, int]], list[int]]:
+    """The 8-site sqrt(8) x sqrt(8) cluster of the square lattice with periodic
+    boundary conditions: lattice points (x, y) modulo the vectors (2, 2) and
+    (2, -2), represented by 0 <= x < 4, 0 <= y < 2 (site = x + 4 y).  Returns
+    the 16 nearest-neighbour bonds (i, j) (each site to its +x and +y
+    neighbour) and the direction of each bond (0 = x, 1 = y)."""
+    def site(x, y):
+        while y >= 2:
+            x, y = x - 2, y - 2
+        while y < 0:
+            x, y = x + 2, y + 2
+        return (x % 4) + 4 * y
+    bonds, dirs = [], []
+    for y in range(2):
+        for x in range(4):
+            for d, (dx, dy) in enumerate(((1, 0), (0, 1))):
+                bonds.append((site(x, y), site(x + dx, y + dy)))
+                dirs.append(d)
+    return bonds, dirs
+
+
+# Synthetic values standing in for the two-orbital model's parameters: e_g-like
+# hoppings (orbital 0 ~ x^2-y^2, orbital 1 ~ 3z^2-r^2) whose inter-orbital
+# element changes sign between the x and y bonds, Kanamori on-site terms with
+# U' = U - 2 J and J' = J, and the inter-site Coulomb V.  Every value is a
+# dyadic rational, so H has the same entries in FP64 and FP32.
+EG_HOPPING = {0: ((-0.75, 0.4375), (0.4375, -0.25)), 1: ((-0.75, -0.4375), (-0.4375, -0.25))}
+EG_INTERACTION = {"U": 4.0, "Up": 2.5, "J": 0.75, "Jp": 0.75, "V": 1.0}
+
+
+def eg_model(bonds=None, dirs=None, **over) -> dict:
+    """The two-orbital extended Hubbard model on a bond list (default: the
+    sqrt(8) x sqrt(8) cluster) with the synthetic values above; keyword
+    arguments override U, Up, J, Jp, V."""
+    if bonds is None:
+        bonds, dirs = sqrt8_cluster()
+    n_sites = 1 + max(max(b) for b in bonds)
+    bond_t = [list(map(list, EG_HOPPING[d])) for d in dirs]
+    m = {"n_sites": n_sites, "bonds": [tuple(b) for b in bonds], "dirs": list(dirs), "bond_t": bond_t}
+    m.update(EG_INTERACTION)
+    m.update(over)
+    return m
+
+
 @dataclass
 class Workload:
     """One synthetic problem: H (CSR or Hubbard parameters), shifts, rhs, projections."""
@@ -212,6 +261,10 @@ def workload(name: str, scale: str = "full", bounds: tuple[float, float] | None 
       ``hubbard``   L=14 ring, 7 up 7 down, t=1, U=4, V=1, periodic; b seeded unit
                     complex, c = conj(b), 128 shifts linspace(-10, 20) + 0.05i
                     (small: L=8, 4 up 4 down).
+      ``hubbard2``  two-orbital extended Hubbard model on the sqrt(8) x sqrt(8)
+                    cluster, 6 up 6 down (64,128,064 states; medium 3/3:
+                    313,600; small 2/2: 14,400), eg_model values, b seeded unit
+                    complex, c = conj(b), 128 shifts linspace(-12, 48) + 0.1i.
     """
     if name == "chain":
         L = 4096 if scale == "full" else 256
@@ -257,4 +310,12 @@ def workload(name: str, scale: str = "full", bounds: tuple[float, float] | None 
         hub = dict(L=L, n_up=nup, n_dn=nup, t=1.0, U=4.0, V=1.0, periodic=True)
         return Workload(name, shifts, b[None, :], 1e-6, hubbard=hub,
                         proj_vec=np.conj(b)[None, :], meta={"seed": 5, **hub})
+    if name == "hubbard2":
+        n_el = {"full": 6, "medium": 3, "small": 2}[scale]
+        model = eg_model()
+        n = math.comb(16, n_el) ** 2
+        b = random_unit_complex(n, seed=6)
+        shifts = np.linspace(-12.0, 48.0, 128) + 0.1j
+        return Workload(name, shifts, b[None, :], 1e-8, hubbard=model, proj_vec=np.conj(b)[None, :],
+                        meta={"seed": 6, "n_up": n_el, "n_dn": n_el})
     raise ValueError(f"unknown workload {name!r}")

@@ -388,3 +388,85 @@ def test_vector_gradient_equals_dense_gradient(oracle_mod):
     gt = oracle_mod.grad_from_vectors(h.rowptr, h.col, Y, X, gbar)
     ref = dense.grad_dense(h.dense(), shifts, b, c, gbar)[rows, h.col]
     assert np.max(np.abs(gt - ref)) > 1e-3 * np.max(np.abs(ref))
+
+
+# ---------------------------------------------------------------- two-orbital model (Sec. IV.B)
+def _model2(bonds, dirs, seed=None, **over):
+    m = inputs.eg_model(bonds=bonds, dirs=dirs, **over)
+    if seed is not None:   # generic hoppings: no accidental symmetry hides a wrong sign or index
+        rng = np.random.default_rng(seed)
+        m["bond_t"] = rng.normal(size=(len(bonds), 2, 2)).tolist()
+    return m
+
+
+@pytest.mark.parametrize("nu,nd", [(1, 1), (2, 1), (2, 2), (3, 1), (1, 3)])
+def test_hubbard2_csr_equals_fock_construction(oracle_mod, nu, nd):
+    """Two sites, one bond, generic hoppings and interaction values: the sector
+    CSR built term by term from bit strings equals the Fock-space Kronecker
+    construction restricted to the sector."""
+    m = _model2([(0, 1)], [0], seed=3, U=3.1, Up=1.7, J=0.6, Jp=0.45, V=0.8)
+    Hf, _, _ = dense.fock_hubbard2(m)
+    ref = dense.fock_sector2(Hf, 2, nu, nd)
+    rp, c, v = oracle_mod.hubbard2_csr(m, nu, nd)
+    n = rp.size - 1
+    import scipy.sparse as sp
+    H = sp.csr_matrix((v, c, rp), shape=(n, n)).toarray()
+    assert np.max(np.abs(H - ref)) < 1e-13
+    assert np.max(np.abs(H - H.T)) == 0.0
+
+
+def test_hubbard2_atomic_kanamori_levels(oracle_mod):
+    """One site: the S_z = 0 two-electron levels are U' -+ J and U -+ J'; the
+    S_z = 1 state sits at U' - J (the same triplet)."""
+    m = {"n_sites": 1, "bonds": [], "bond_t": np.zeros((0, 2, 2)), "U": 4.0, "Up": 2.5, "J": 0.75, "Jp": 0.6,
+         "V": 1.0}
+    rp, c, v = oracle_mod.hubbard2_csr(m, 1, 1)
+    import scipy.sparse as sp
+    H = sp.csr_matrix((v, c, rp), shape=(4, 4)).toarray()
+    assert np.allclose(np.linalg.eigvalsh(H), dense.kanamori_two_electron_levels(4.0, 2.5, 0.75, 0.6), atol=1e-14)
+    rp2, c2, v2 = oracle_mod.hubbard2_csr(m, 2, 0)
+    assert rp2.size == 2 and np.allclose(v2, [2.5 - 0.75])
+
+
+def test_hubbard2_fock_model_is_spin_invariant():
+    """With U' = U - 2J and J' = J the Kanamori interaction is spin-rotation
+    invariant: H commutes with S^2 and S_z (a wrong sign of the spin-flip or
+    pair-hopping term breaks [H, S^2] = 0)."""
+    m = _model2([(0, 1)], [0], seed=5, U=3.0, Up=1.8, J=0.6, Jp=0.6, V=0.7)
+    H, c, _ = dense.fock_hubbard2(m)
+    S2, Sz = dense.fock_spin2(2, c)
+    assert np.max(np.abs(H @ S2 - S2 @ H)) < 1e-12
+    assert np.max(np.abs(H @ Sz - Sz @ H)) < 1e-12
+    # the same H with the spin-flip term (alone) of the opposite sign is not
+    cd = [x.T for x in c]
+    sf = sum(cd[2 * i + 0 + 4 * s] @ cd[2 * i + 1 + 4 * (1 - s)] @ c[2 * i + 0 + 4 * (1 - s)] @ c[2 * i + 1 + 4 * s]
+             for i in range(2) for s in range(2))
+    Hb = H - 2 * 0.6 * sf
+    assert np.max(np.abs(Hb @ S2 - S2 @ Hb)) > 1e-3
+
+
+def test_hubbard2_free_fermions_on_sqrt8_cluster(oracle_mod):
+    """Hopping alone on the sqrt(8) x sqrt(8) cluster: the sector spectrum is
+    every sum of occupied single-particle energies (2 up, 1 down)."""
+    m = inputs.eg_model(U=0.0, Up=0.0, J=0.0, Jp=0.0, V=0.0)
+    rp, c, v = oracle_mod.hubbard2_csr(m, 2, 1)
+    import scipy.sparse as sp
+    n = rp.size - 1
+    ev = np.linalg.eigvalsh(sp.csr_matrix((v, c, rp), shape=(n, n)).toarray())
+    assert np.allclose(ev, dense.free_fermion_spectrum2(m, 2, 1), atol=1e-12)
+
+
+def test_hubbard2_rows_equal_csr_product(oracle_mod):
+    """Sampled rows of H x computed state by state equal the CSR product
+    (sqrt(8) x sqrt(8), 2 up 2 down, 14,400 states); the 6/6 sector of the
+    paper has (16 C 6)^2 states."""
+    m = inputs.eg_model()
+    rp, c, v = oracle_mod.hubbard2_csr(m, 2, 2)
+    n = rp.size - 1
+    assert n == math.comb(16, 2) ** 2
+    x = inputs.random_unit_complex(n, 9)
+    import scipy.sparse as sp
+    y = sp.csr_matrix((v, c, rp), shape=(n, n)) @ x
+    rows = np.random.default_rng(1).choice(n, 300, replace=False)
+    assert np.max(np.abs(oracle_mod.hubbard2_rows(m, 2, 2, rows, x) - y[rows])) < 1e-14
+    assert oracle_mod.sector_dim(16, 6) ** 2 == 64128064
