@@ -158,6 +158,34 @@ int scocg_create_csr(scocg_handle *out, int64_t n, int64_t nnz, const int64_t *r
 int scocg_create_hubbard(scocg_handle *out, int L, int n_up, int n_dn, double t, double U,
                          double V, int periodic, const scocg_opts *opts, void *cuda_stream);
 
+/*
+ * scocg_create_hubbard2 -- matrix-free two-orbital (doubly degenerate)
+ * extended Hubbard model on a cluster, the many-electron problem of Sec. IV.B
+ * (the paper: N = 8 sites of the sqrt(8) x sqrt(8) square lattice with two
+ * orbitals each, N_e = 12, S_z = 0: 64,128,064 states):
+ *
+ *   H = sum_b sum_{a,a'} sum_s t^b_{aa'} (c+_{i a s} c_{j a' s} + c+_{j a' s} c_{i a s})  (bond b = (i, j))
+ *     + U sum_{i,a} n_{ia up} n_{ia dn} + U' sum_i n_{i0} n_{i1} - J sum_{i,s} n_{i0s} n_{i1s}
+ *     + J sum_{i,s} c+_{i0s} c+_{i1s'} c_{i0s'} c_{i1s}                          (s' = -s)
+ *     + J' sum_i (c+_{i0 up} c+_{i0 dn} c_{i1 dn} c_{i1 up} + h.c.) + V sum_b n_i n_j
+ *
+ *   n_sites <= 16; n_bonds <= 32, each site in at most 7 bonds;
+ *   bond_i, bond_j [n_bonds] host: the sites of each bond (i != j);
+ *   bond_t [n_bonds][2][2] host: t^b_{aa'};
+ *   n_up, n_dn electrons per spin (each spin sector below 2^23 states).
+ * Modes: within a spin 2 i + a (site i, orbital a); all up-spin modes first,
+ * then the down-spin ones (Jordan-Wigner order).  Basis index rank_up * D_dn +
+ * rank_dn with ranks as in scocg_create_hubbard over the 2 n_sites modes.
+ * The handle is a Hubbard handle: scocg_solve, scocg_apply,
+ * scocg_ground_state, scocg_krylov_sd accept it, and scocg_excite creates or
+ * annihilates mode m = 2 i + a (`site` = m) between two such handles.
+ * Returns SCOCG_ERR_INVALID for parameters outside these limits.
+ */
+int scocg_create_hubbard2(scocg_handle *out, int n_sites, int n_bonds, const int32_t *bond_i,
+                          const int32_t *bond_j, const double *bond_t, double U, double Up, double J,
+                          double Jp, double V, int n_up, int n_dn, const scocg_opts *opts,
+                          void *cuda_stream);
+
 /* Dimension N of the handle's H. */
 int scocg_dim(scocg_handle h, int64_t *n);
 

@@ -56,6 +56,21 @@ struct Hubbard {
     int32_t* d_hop_packed = nullptr;   // [2][Dmax][2L]: (target << 1) | (sign < 0), -1 = unused
     int Dmax = 0;
     double table_bytes = 0;
+    // model 1: two orbitals per site on a cluster (L = 2 ns modes per spin;
+    // t, U, V above unused).  Tables per spin at offset spin * (table stride).
+    int model = 0;                     // 0: one-orbital ring, 1: two-orbital cluster
+    int ns = 0, nb = 0, S2 = 0;        // sites, bonds, hop slots per rank
+    double Up = 0, J = 0, Jp = 0;
+    int32_t* d_hop2 = nullptr;         // [2][Dmax][S2]: (target << 8) | (amplitude << 1) | (sign < 0), -1 = unused
+    int32_t* d_orb2 = nullptr;         // [2][Dmax][ns]: (target << 1) | destination orbital, -1 = no move
+    uint32_t* d_nib2 = nullptr;        // [2][Dmax][2]: site occupations n_i and (A n)_i as nibbles
+    double* d_self2 = nullptr;         // [2][Dmax]: the diagonal terms of one spin alone
+    float2* d_self2f = nullptr;        // [2][Dmax]: the same as float pairs (hi, lo)
+    double* d_amp2 = nullptr;          // [nb][2][2] hoppings t_ab of each bond
+    float2* d_amp2f = nullptr;         // [nb][2][2] the same as float pairs
+    double* d_cross2 = nullptr;        // [3][kCross2]: U c, U' c, V c for small integer counts c
+    float2* d_cross2f = nullptr;       // the same as float pairs
+    int32_t* d_bonds2 = nullptr;       // [nb][2]
 };
 
 }  // namespace scocg
@@ -124,6 +139,13 @@ cudaError_t hubbard_hx(const Hubbard& hb, const double* x, double* y, const doub
                        double sigma, const int* skip, double* part, int grid, cudaStream_t st);
 template <typename R>
 cudaError_t hubbard_launch_solve(const SolveArgs<R>& a, const Hubbard& hb, int grid, cudaStream_t st);
+// the two-orbital model (hubbard2.cu), dispatched to from the functions above
+cudaError_t hubbard2_apply(const Hubbard& hb, int prec, double2 z, const void* x, void* y, cudaStream_t st);
+int hubbard2_max_ctas(const Hubbard& hb, int prec, int num_sms, size_t dyn_smem);
+cudaError_t hubbard2_hx(const Hubbard& hb, const double* x, double* y, const double* xprev, const double* beta,
+                        double sigma, const int* skip, double* part, int grid, cudaStream_t st);
+template <typename R>
+cudaError_t hubbard2_launch_solve(const SolveArgs<R>& a, const Hubbard& hb, int grid, cudaStream_t st);
 
 constexpr int kMaxFullShifts = 512;   // shifts per full-vector launch (dynamic shared memory)
 int solve_impl(scocg_ctx* h, const scocg_c128* shifts, int nshift, const void* rhs, int nrhs,

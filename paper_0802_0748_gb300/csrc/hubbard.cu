@@ -23,6 +23,7 @@
 #include "api_internal.h"
 #include "solver_kernel.cuh"
 #include "vector_ops.cuh"
+#include "hubbard_basis.cuh"
 
 #ifndef SCOCG_HOP_GROUP
 #define SCOCG_HOP_GROUP 4
@@ -33,32 +34,6 @@ namespace scocg {
 template <typename VV> struct Scal;
 template <> struct Scal<float2> { using T = float; };
 template <> struct Scal<double2> { using T = double; };
-
-__host__ __device__ inline int64_t binom(int n, int k) {
-    if (k < 0 || k > n) return 0;
-    int64_t r = 1;
-    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
-    return r;
-}
-
-__device__ inline int64_t rank_of(uint32_t s) {
-    int64_t r = 0;
-    int j = 0;
-    for (int pos = 0; pos < 32; ++pos)
-        if ((s >> pos) & 1u) { ++j; r += binom(pos, j); }
-    return r;
-}
-
-__device__ inline uint32_t unrank(int64_t r, int k, int L) {
-    uint32_t s = 0;
-    for (int j = k; j >= 1; --j) {
-        int p = j - 1;
-        while (p + 1 < L && binom(p + 1, j) <= r) ++p;
-        s |= 1u << p;
-        r -= binom(p, j);
-    }
-    return s;
-}
 
 // One thread per rank of one spin species.
 __global__ void k_hubbard_tables(int L, int k, int D, int ring, uint32_t* states, int32_t* target, int8_t* sign,
@@ -233,6 +208,7 @@ static ApplyHubbard<R> make_apply(const Hubbard& hb) {
 }
 
 int hubbard_max_ctas(const Hubbard& hb, int prec, int num_sms, size_t dyn_smem) {
+    if (hb.model == 1) return hubbard2_max_ctas(hb, prec, num_sms, dyn_smem);
     int nb = 0;
     cudaError_t e =
         prec == SCOCG_MIXED
@@ -249,6 +225,7 @@ int hubbard_max_ctas(const Hubbard& hb, int prec, int num_sms, size_t dyn_smem) 
 
 template <typename R>
 cudaError_t hubbard_launch_solve(const SolveArgs<R>& a, const Hubbard& hb, int grid, cudaStream_t st) {
+    if (hb.model == 1) return hubbard2_launch_solve<R>(a, hb, grid, st);
     using W = typename ValT<R>::T;
     ApplyHubbard<W> ap = make_apply<W>(hb);
     ap.dbg = a.dbg;
@@ -274,6 +251,7 @@ __global__ void __launch_bounds__(256) k_hub_apply(Apply ap, int64_t nunits, VV 
 }
 
 cudaError_t hubbard_apply(const Hubbard& hb, int prec, double2 z, const void* x, void* y, cudaStream_t st) {
+    if (hb.model == 1) return hubbard2_apply(hb, prec, z, x, y, st);
     const unsigned blocks = (unsigned)((hb.nunits * 32 + 255) / 256);
     if (prec == SCOCG_MIXED)
         k_hub_apply<float2><<<blocks, 256, 0, st>>>(make_apply<float>(hb), hb.nunits,
@@ -357,6 +335,7 @@ __global__ void __launch_bounds__(kVecBlock) k_hub_hx(ApplyHubbard<double> ap, i
 
 cudaError_t hubbard_hx(const Hubbard& hb, const double* x, double* y, const double* xprev, const double* beta,
                        double sigma, const int* skip, double* part, int grid, cudaStream_t st) {
+    if (hb.model == 1) return hubbard2_hx(hb, x, y, xprev, beta, sigma, skip, part, grid, st);
     k_hub_hx<<<grid, kVecBlock, 0, st>>>(make_apply<double>(hb), hb.nunits, x, y, xprev, beta, sigma, skip, part);
     return cudaGetLastError();
 }

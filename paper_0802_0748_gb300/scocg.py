@@ -28,7 +28,7 @@ EXPORTED = [
     "scocg_create_csr", "scocg_create_hubbard", "scocg_dim", "scocg_set_opts", "scocg_apply",
     "scocg_solve", "scocg_solve_full", "scocg_grad", "scocg_destroy", "scocg_strerror",
     "scocg_hubbard_tables", "scocg_solve_csr_noalloc", "scocg_solve_multi", "scocg_multi_release",
-    "scocg_density", "scocg_ground_state", "scocg_excite", "scocg_krylov_sd",
+    "scocg_density", "scocg_ground_state", "scocg_excite", "scocg_krylov_sd", "scocg_create_hubbard2",
 ]
 
 
@@ -94,6 +94,8 @@ def lib() -> ctypes.CDLL:
         D = ctypes.c_double
         L.scocg_create_csr.argtypes = [ctypes.POINTER(P), I64, I64, P, P, P, I, ctypes.POINTER(Opts), P]
         L.scocg_create_hubbard.argtypes = [ctypes.POINTER(P), I, I, I, D, D, D, I, ctypes.POINTER(Opts), P]
+        L.scocg_create_hubbard2.argtypes = [ctypes.POINTER(P), I, I, P, P, P, D, D, D, D, D, I, I,
+                                            ctypes.POINTER(Opts), P]
         L.scocg_dim.argtypes = [P, ctypes.POINTER(I64)]
         L.scocg_set_opts.argtypes = [P, ctypes.POINTER(Opts)]
         L.scocg_apply.argtypes = [P, c128, P, P, I]
@@ -219,6 +221,29 @@ def scocg_create_hubbard(L, n_up, n_dn, t, U, V, periodic=True, opts: SolveOptio
     _check(code, "scocg_create_hubbard")
     h = Handle(out, stream)
     h.L = L
+    h.sector = (int(n_up), int(n_dn))
+    return h
+
+
+def scocg_create_hubbard2(model: dict, n_up: int, n_dn: int, opts: SolveOptions | None = None,
+                          stream=None) -> Handle:
+    """scocg_create_hubbard2: matrix-free two-orbital extended Hubbard model
+    (Sec. IV.B).  model: dict with n_sites, bonds [(i, j)], bond_t [nb][2][2],
+    U, Up, J, Jp, V."""
+    out = ctypes.c_void_p()
+    o = (opts or SolveOptions()).c()
+    bi = np.ascontiguousarray([b[0] for b in model["bonds"]], dtype=np.int32)
+    bj = np.ascontiguousarray([b[1] for b in model["bonds"]], dtype=np.int32)
+    bt = np.ascontiguousarray(model["bond_t"], dtype=np.float64).reshape(-1, 2, 2)
+    if bt.shape[0] != bi.size:
+        raise ValueError("bond_t must hold one 2x2 block per bond")
+    code = lib().scocg_create_hubbard2(ctypes.byref(out), int(model["n_sites"]), int(bi.size), bi.ctypes.data,
+                                       bj.ctypes.data, bt.ctypes.data, float(model["U"]), float(model["Up"]),
+                                       float(model["J"]), float(model["Jp"]), float(model["V"]), int(n_up), int(n_dn),
+                                       ctypes.byref(o), _stream_ptr(stream))
+    _check(code, "scocg_create_hubbard2")
+    h = Handle(out, stream)
+    h.L = 2 * int(model["n_sites"])
     h.sector = (int(n_up), int(n_dn))
     return h
 
