@@ -119,7 +119,7 @@ void scocg_ctx::free_all() {
     void* ptrs[] = {d_rowptr, d_col, d_val64, d_val32, d_unit_off, d_bcol, d_bval64, d_bval32, d_bval32c, d_ctrl,
                     hub.d_states, hub.d_hop_target, hub.d_hop_sign, hub.d_hop_packed, hub.d_hop2, hub.d_orb2,
                     hub.d_nib2, hub.d_self2, hub.d_self2f, hub.d_amp2, hub.d_amp2f, hub.d_cross2, hub.d_cross2f,
-                    hub.d_bonds2};
+                    hub.d_bonds2, hub.d_diagf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     ws.release();

@@ -54,6 +54,7 @@ struct Hubbard {
     int32_t* d_hop_target = nullptr;   // [2][Dmax][2L]
     int8_t* d_hop_sign = nullptr;      // [2][Dmax][2L]
     int32_t* d_hop_packed = nullptr;   // [2][Dmax][2L]: (target << 1) | (sign < 0), -1 = unused
+    float2* d_diagf = nullptr;         // [(L+1)(4L+1)]: U cu + V cv as float pairs (hi, lo)
     int Dmax = 0;
     double table_bytes = 0;
     // model 1: two orbitals per site on a cluster (L = 2 ns modes per spin;
@@ -67,7 +68,7 @@ struct Hubbard {
     double* d_self2 = nullptr;         // [2][Dmax]: the diagonal terms of one spin alone
     float2* d_self2f = nullptr;        // [2][Dmax]: the same as float pairs (hi, lo)
     double* d_amp2 = nullptr;          // [nb][2][2] hoppings t_ab of each bond
-    float2* d_amp2f = nullptr;         // [nb][2][2] the same as float pairs
+    float2* d_amp2f = nullptr;         // [nb][2][2][2] the same with each sign, as (hi, hi, lo, lo) float4s
     double* d_cross2 = nullptr;        // [3][kCross2]: U c, U' c, V c for small integer counts c
     float2* d_cross2f = nullptr;       // the same as float pairs
     int32_t* d_bonds2 = nullptr;       // [nb][2]

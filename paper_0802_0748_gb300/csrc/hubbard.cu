@@ -25,6 +25,9 @@
 #include "vector_ops.cuh"
 #include "hubbard_basis.cuh"
 
+#ifndef SCOCG_RING_TWO_PASS
+#define SCOCG_RING_TWO_PASS 0
+#endif
 #ifndef SCOCG_HOP_GROUP
 #define SCOCG_HOP_GROUP 4
 #endif
@@ -78,6 +81,8 @@ struct ApplyHubbard {
     const int32_t* hop_dn;     // packed, [D_dn][S]
     int S, D_up, D_dn, L, ring;
     double t, U, V;
+    const float2* diagf;     // U cu + V cv as float pairs, index cu * (4 L + 1) + cv
+    float t_hi, t_lo;        // t as a float pair
     int64_t n;
     unsigned long long* dbg;
 
@@ -104,7 +109,7 @@ struct ApplyHubbard {
             }
             float4 xv[kHopGroup];
 #pragma unroll
-            for (int q = 0; q < kHopGroup; ++q) xv[q] = e[q] >= 0 ? base[(int64_t)(e[q] >> 1) * stride] : vzero<float4>();
+            for (int q = 0; q < kHopGroup; ++q) xv[q] = base[(int64_t)(max(e[q], 0) >> 1) * stride];   // entry 0 when ended
 #pragma unroll
             for (int q = 0; q < kHopGroup; ++q) {
                 if (e[q] >= 0) {
@@ -137,14 +142,122 @@ struct ApplyHubbard {
         hop_acc_df(hop_dn + (size_t)d * S, S, x + (size_t)u * D_dn, 1, D_dn, dbg, h, l);
         hop_acc_df(hop_up + (size_t)u * S, S, x + d, D_dn, D_up, dbg, h, l);
         pk_norm(h, l);
-        const float4 dg = df_from(c2(U * (double)cu + V * (double)cv, 0.0));
-        const dfs zr = df_add(cre(zs), df_neg(cre(dg)));
+        const float2 dg = diagf[cu * (4 * L + 1) + cv];
+        const dfs zr = df_add(cre(zs), dfs{-dg.x, -dg.y});
         const float4 acc = vcfma(cpack(zr, cim(zs)), x[row], vzero<float4>());   // (z_s - diag) x_row
         float2 ah = hi2(acc), al = lo2(acc);
-        const float4 tp = df_from(c2(t, 0.0));   // - H's hopping part: + t sum sign x
-        pk_acc_prod(ah, al, make_float2(tp.x, tp.x), make_float2(tp.z, tp.z), h, l);
+        // - H's hopping part: + t sum sign x
+        pk_acc_prod(ah, al, make_float2(t_hi, t_hi), make_float2(t_lo, t_lo), h, l);
         pk_norm(ah, al);
         w = pk4(ah, al);
+        return true;
+    }
+
+    // ---- two-pass form (phase A runs pass 1 over all units, a grid barrier,
+    // then pass 2; off for the ring, where one pass measured faster: 622 vs
+    // 686 us per iteration at 14 sites, while the two-orbital model gains).  Pass 1 visits units row-major
+    // (unit = u * tiles + tile: the CTAs share the rows x[u][:] of the down
+    // hops) and stores q = (z_s - diag) x + t (down-hop sum) + beta q_old;
+    // pass 2 visits them tile-major (unit = tile * D_up + u: the CTAs share the
+    // column tiles x[:][tile] of the up hops) and adds t (up-hop sum).
+    static constexpr bool kTwoPass = SCOCG_RING_TWO_PASS;
+    __device__ __forceinline__ bool rc_rows(int64_t unit, int lane, int& u, int& d) const {
+        const int tiles = (D_dn + 31) / 32;
+        u = (int)(unit / tiles);
+        d = (int)(unit % tiles) * 32 + lane;
+        return d < D_dn;
+    }
+    __device__ __forceinline__ bool rc_tiles(int64_t unit, int lane, int& u, int& d) const {
+        u = (int)(unit % D_up);
+        d = (int)(unit / D_up) * 32 + lane;
+        return d < D_dn;
+    }
+    __device__ __forceinline__ int diag_index(int u, int d) const {
+        const uint32_t su = st_up[u], sd = st_dn[d];
+        const uint32_t pu = partner(su), pd = partner(sd);
+        const int cu = __popc(su & sd);
+        const int cv = __popc(su & pu) + __popc(sd & pd) + __popc(su & pd) + __popc(sd & pu);
+        return cu * (4 * L + 1) + cv;
+    }
+    __device__ __forceinline__ double diag_of(int u, int d) const {
+        const uint32_t su = st_up[u], sd = st_dn[d];
+        const uint32_t pu = partner(su), pd = partner(sd);
+        const int cu = __popc(su & sd);
+        const int cv = __popc(su & pu) + __popc(sd & pd) + __popc(su & pd) + __popc(sd & pu);
+        return U * (double)cu + V * (double)cv;
+    }
+
+    __device__ __forceinline__ void pass1(int64_t unit, int lane, float4 zs, float4 bp, const float4* x,
+                                          float4* q) const {
+        int u, d;
+        if (!rc_rows(unit, lane, u, d)) return;
+        const int64_t row = (int64_t)u * D_dn + d;
+        float2 h = make_float2(0.f, 0.f), l = make_float2(0.f, 0.f);
+        hop_acc_df(hop_dn + (size_t)d * S, S, x + (size_t)u * D_dn, 1, D_dn, dbg, h, l);
+        pk_norm(h, l);
+        const float2 dg = diagf[diag_index(u, d)];
+        const dfs zr = df_add(cre(zs), dfs{-dg.x, -dg.y});
+        const float4 acc = vcfma(cpack(zr, cim(zs)), x[row], vzero<float4>());
+        float2 ah = hi2(acc), al = lo2(acc);
+        pk_acc_prod(ah, al, make_float2(t_hi, t_hi), make_float2(t_lo, t_lo), h, l);
+        pk_norm(ah, al);
+        q[row] = vcfma(bp, q[row], pk4(ah, al));
+    }
+    __device__ __forceinline__ bool pass2(int64_t unit, int lane, const float4* x, float4* q, int64_t& row,
+                                          float4& qn) const {
+        int u, d;
+        if (!rc_tiles(unit, lane, u, d)) return false;
+        row = (int64_t)u * D_dn + d;
+        float2 h = make_float2(0.f, 0.f), l = make_float2(0.f, 0.f);
+        hop_acc_df(hop_up + (size_t)u * S, S, x + d, D_dn, D_up, dbg, h, l);
+        pk_norm(h, l);
+        const float4 q1 = q[row];
+        float2 ah = hi2(q1), al = lo2(q1);
+        pk_acc_prod(ah, al, make_float2(t_hi, t_hi), make_float2(t_lo, t_lo), h, l);
+        pk_norm(ah, al);
+        qn = pk4(ah, al);
+        q[row] = qn;
+        return true;
+    }
+    // FP64 and complex64 vectors
+    template <typename VV>
+    __device__ __forceinline__ VV hop_sum_v(const int32_t* tab, const VV* base, int64_t stride, int64_t lim) const {
+        using T = typename Scal<VV>::T;
+        VV acc;
+        acc.x = 0; acc.y = 0;
+        for (int j = 0; j < S; ++j) {
+            const int e = tab[j];
+            if (e < 0) break;
+            if (!chk(dbg, 20, e >> 1, lim)) continue;
+            const VV xv = base[(int64_t)(e >> 1) * stride];
+            const T c = (e & 1) ? -(T)t : (T)t;
+            acc.x += c * xv.x; acc.y += c * xv.y;
+        }
+        return acc;
+    }
+    template <typename VV>
+    __device__ __forceinline__ void pass1(int64_t unit, int lane, VV zs, VV bp, const VV* x, VV* q) const {
+        using T = typename Scal<VV>::T;
+        int u, d;
+        if (!rc_rows(unit, lane, u, d)) return;
+        const int64_t row = (int64_t)u * D_dn + d;
+        const VV hs = hop_sum_v(hop_dn + (size_t)d * S, x + (size_t)u * D_dn, 1, D_dn);
+        const T zr = zs.x - (T)diag_of(u, d);
+        const VV xr = x[row];
+        VV w;
+        w.x = zr * xr.x - zs.y * xr.y + hs.x;
+        w.y = zr * xr.y + zs.y * xr.x + hs.y;
+        q[row] = vcfma(bp, q[row], w);
+    }
+    template <typename VV>
+    __device__ __forceinline__ bool pass2(int64_t unit, int lane, const VV* x, VV* q, int64_t& row, VV& qn) const {
+        int u, d;
+        if (!rc_tiles(unit, lane, u, d)) return false;
+        row = (int64_t)u * D_dn + d;
+        const VV hs = hop_sum_v(hop_up + (size_t)u * S, x + d, D_dn, D_up);
+        qn = q[row];
+        qn.x += hs.x; qn.y += hs.y;
+        q[row] = qn;
         return true;
     }
 
@@ -202,6 +315,9 @@ static ApplyHubbard<R> make_apply(const Hubbard& hb) {
     ap.D_up = hb.D_up; ap.D_dn = hb.D_dn; ap.L = hb.L;
     ap.ring = hb.periodic && hb.L >= 3;
     ap.t = hb.t; ap.U = hb.U; ap.V = hb.V;
+    ap.diagf = hb.d_diagf;
+    ap.t_hi = (float)hb.t;
+    ap.t_lo = (float)(hb.t - (double)ap.t_hi);
     ap.n = (int64_t)hb.D_up * hb.D_dn;
     ap.dbg = nullptr;
     return ap;
@@ -404,6 +520,19 @@ extern "C" int scocg_create_hubbard(scocg_handle* out, int L, int n_up, int n_dn
                                                                  hb.d_hop_target + sp * tab, hb.d_hop_sign + sp * tab,
                                                                  hb.d_hop_packed + sp * tab);
         e = cudaGetLastError();
+    }
+    {   // the diagonal U cu + V cv for every count pair, as float pairs
+        const int ncv = 4 * L + 1;
+        std::vector<float2> dg((size_t)(L + 1) * ncv);
+        for (int cu = 0; cu <= L; ++cu)
+            for (int cv = 0; cv < ncv; ++cv) {
+                const double v = U * (double)cu + V * (double)cv;
+                const float hi = (float)v;
+                dg[(size_t)cu * ncv + cv] = make_float2(hi, (float)(v - (double)hi));
+            }
+        if (e == cudaSuccess) e = cudaMalloc(&hb.d_diagf, sizeof(float2) * dg.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(hb.d_diagf, dg.data(), sizeof(float2) * dg.size(), cudaMemcpyHostToDevice, h->stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     hb.table_bytes = (double)(hb.D_up + hb.D_dn) * (4.0 + 4.0 * S);

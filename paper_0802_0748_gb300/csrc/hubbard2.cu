@@ -40,7 +40,13 @@ namespace scocg {
 constexpr int kMaxSites2 = 16;       // 2 ns <= 32 modes per spin
 constexpr int kMaxBonds2 = 32;       // amplitude index b*4 + a*2 + a' < 128 (7 bits)
 constexpr int kCross2 = 257;         // counts 0..256 of the cross-spin diagonal tables (8 per bond at most)
-constexpr int kHop2Group = 4;        // hop entries read (and gathered) together
+#ifndef SCOCG_H2_GROUP
+#define SCOCG_H2_GROUP 4
+#endif
+constexpr int kHop2Group = SCOCG_H2_GROUP;   // hop entries read (and gathered) together
+#ifndef SCOCG_H2_UMAJOR
+#define SCOCG_H2_UMAJOR 0
+#endif
 
 __device__ __forceinline__ int parity_sign(int c) { return (c & 1) ? -1 : 1; }
 
@@ -66,12 +72,12 @@ __global__ void k_hubbard2_tables(int ns, int nb, int k, int D, const int32_t* b
                     const uint32_t s1 = s & ~(1u << src);
                     const int sg = parity_sign(__popc(s & ((1u << src) - 1u)) + __popc(s1 & ((1u << dst) - 1u)));
                     const int t = (int)rank_of(s1 | (1u << dst));
-                    if (cnt < S2) hop[(size_t)r * S2 + cnt] = (t << 8) | (amp << 1) | (sg < 0 ? 1 : 0);
+                    if (cnt < S2) hop[(size_t)cnt * D + r] = (t << 8) | (amp << 1) | (sg < 0 ? 1 : 0);
                     ++cnt;
                 }
             }
     }
-    for (int c = cnt; c < S2; ++c) hop[(size_t)r * S2 + c] = -1;
+    for (int c = cnt; c < S2; ++c) hop[(size_t)c * D + r] = -1;
     uint32_t ni = 0, ani = 0;
     double sv = 0.0;
     int same = 0;
@@ -82,7 +88,7 @@ __global__ void k_hubbard2_tables(int ns, int nb, int k, int D, const int32_t* b
             const int dst = o == 1u ? 1 : 0;
             mv = (int32_t)(rank_of(s ^ (3u << (2 * i))) << 1) | dst;
         }
-        orb[(size_t)r * ns + i] = mv;
+        orb[(size_t)i * D + r] = mv;
         ni |= (uint32_t)__popc(o) << (4 * i);
         same += o == 3u;
     }
@@ -108,9 +114,9 @@ struct ApplyHubbard2 {
     const uint32_t* st_up;
     const uint32_t* st_dn;
     const int32_t* hop_up;
-    const int32_t* hop_dn;     // [D][S2]
+    const int32_t* hop_dn;     // [S2][D] (slot-major: a warp's 32 ranks read one line per slot)
     const int32_t* orb_up;
-    const int32_t* orb_dn;     // [D][ns]
+    const int32_t* orb_dn;     // [ns][D]
     const uint32_t* nib_up;
     const uint32_t* nib_dn;    // [D][2]
     const double* self_up;
@@ -118,13 +124,29 @@ struct ApplyHubbard2 {
     const float2* selff_up;
     const float2* selff_dn;
     const double* amp;         // [4 nb]
-    const float2* ampf;
+    const float4* ampf;        // [4 nb][2]: the signed amplitude (sign t) as (hi, hi, lo, lo)
     const double* cross;       // [3][kCross2]: U c, U' c, V c
     const float2* crossf;
     int S2, ns, D_up, D_dn;
     double J, Jp;
+    float Jh, Jl, Ph, Pl;      // -J and -J' as float pairs (hi, lo)
     int64_t n;
     unsigned long long* dbg;
+
+    // Row (u, d) of (unit, lane).  Units are visited by all CTAs together in
+    // unit order; up-major (unit = u * tiles + tile) keeps the rows x[u][:] of
+    // the down hops and the joint moves' rows in cache, tile-major (unit =
+    // tile * D_up + u) the column tiles x[:][tile] of the up hops.
+    __device__ __forceinline__ void unit_rc(int64_t unit, int lane, int& u, int& d) const {
+#if SCOCG_H2_UMAJOR
+        const int tiles = (D_dn + 31) / 32;
+        u = (int)(unit / tiles);
+        d = (int)(unit % tiles) * 32 + lane;
+#else
+        u = (int)(unit % D_up);
+        d = (int)(unit / D_up) * 32 + lane;
+#endif
+    }
 
     // the cross-spin diagonal counts of row (u, d)
     __device__ __forceinline__ void counts(uint32_t su, uint32_t sd, int u, int d, int& cu, int& cp, int& cv) const {
@@ -143,47 +165,36 @@ struct ApplyHubbard2 {
     // parts packed; the joint moves are summed by coefficient (J or J') and
     // multiplied once; the diagonal from the spins' own terms and the
     // cross-spin tables, as float pairs.
-    __device__ __forceinline__ void hops_df(const int32_t* tab, const float4* base, int64_t stride, int64_t lim,
-                                            float2& h, float2& l) const {
+    __device__ __forceinline__ void hops_df(const int32_t* tab, int64_t tstride, const float4* base, int64_t stride,
+                                            int64_t lim, float2& h, float2& l) const {
         for (int j0 = 0; j0 < S2; j0 += kHop2Group) {
             int e[kHop2Group];
 #pragma unroll
             for (int q = 0; q < kHop2Group; ++q) {
-                e[q] = j0 + q < S2 ? tab[j0 + q] : -1;
+                e[q] = j0 + q < S2 ? tab[(int64_t)(j0 + q) * tstride] : -1;
                 if (e[q] >= 0 && !chk(dbg, 22, e[q] >> 8, lim)) e[q] = -1;
             }
+            // every load is issued (an ended list reads entry 0) and only the
+            // valid entries are added
             float4 xv[kHop2Group];
 #pragma unroll
-            for (int q = 0; q < kHop2Group; ++q) xv[q] = e[q] >= 0 ? base[(int64_t)(e[q] >> 8) * stride] : vzero<float4>();
+            for (int q = 0; q < kHop2Group; ++q) xv[q] = base[(int64_t)(max(e[q], 0) >> 8) * stride];
 #pragma unroll
             for (int q = 0; q < kHop2Group; ++q) {
                 if (e[q] >= 0) {
-                    const float2 t = ampf[(e[q] >> 1) & 127];
-                    const float th = (e[q] & 1) ? -t.x : t.x, tl = (e[q] & 1) ? -t.y : t.y;
-                    pk_acc_prod(h, l, make_float2(th, th), make_float2(tl, tl), hi2(xv[q]), lo2(xv[q]));
+                    const float4 t = ampf[e[q] & 255];
+                    pk_acc_prod(h, l, make_float2(t.x, t.y), make_float2(t.z, t.w), hi2(xv[q]), lo2(xv[q]));
                 }
             }
             if (e[kHop2Group - 1] < 0) break;
         }
     }
 
-    __device__ __forceinline__ bool operator()(int64_t unit, int lane, float4 zs, const float4* x, int64_t& row,
-                                               float4& w) const {
-        const int u = (int)(unit % D_up);
-        const int d = (int)(unit / D_up) * 32 + lane;
-        if (d >= D_dn) return false;
-        row = (int64_t)u * D_dn + d;
-        const uint32_t su = st_up[u], sd = st_dn[d];
-        int cu, cp, cv;
-        counts(su, sd, u, d, cu, cp, cv);
-        // hops: h + l = (H's hopping part) x = sum t sign x over the hop lists
-        float2 h = make_float2(0.f, 0.f), l = make_float2(0.f, 0.f);
-        hops_df(hop_dn + (size_t)d * S2, x + (size_t)u * D_dn, 1, D_dn, h, l);
-        hops_df(hop_up + (size_t)u * S2, x + d, D_dn, D_up, h, l);
-        // joint moves, summed separately for J and J'
-        float2 hj = make_float2(0.f, 0.f), lj = hj, hp = hj, lp = hj;
+    // joint moves (spin flip: J, pair hopping: J'), summed separately
+    __device__ __forceinline__ void joint_df(int u, int d, const float4* x, float2& hj, float2& lj, float2& hp,
+                                             float2& lp) const {
         for (int i = 0; i < ns; ++i) {
-            const int32_t mu = orb_up[(size_t)u * ns + i], md = orb_dn[(size_t)d * ns + i];
+            const int32_t mu = orb_up[(size_t)i * D_up + u], md = orb_dn[(size_t)i * D_dn + d];
             if (mu < 0 || md < 0) continue;
             const int tu = mu >> 1, td = md >> 1;
             if (!chk(dbg, 23, tu, D_up) || !chk(dbg, 24, td, D_dn)) continue;
@@ -199,34 +210,165 @@ struct ApplyHubbard2 {
         }
         pk_norm(hj, lj);
         pk_norm(hp, lp);
-        // diagonal: self terms of both spins plus the cross-spin tables
+    }
+    // w = (z_s - diag) x_row - (hops h + l) - J (hj + lj) - J' (hp + lp)
+    __device__ __forceinline__ float4 combine_df(int u, int d, int cu, int cp, int cv, float4 zs, float4 xr,
+                                                 float2 h, float2 l, float2 hj, float2 lj, float2 hp,
+                                                 float2 lp) const {
+        pk_norm(h, l);
         const float2 d0 = selff_up[u], d1 = selff_dn[d];
         const float2 c0 = crossf[min(cu, kCross2 - 1)], c1 = crossf[kCross2 + min(cp, kCross2 - 1)],
                      c2v = crossf[2 * kCross2 + min(cv, kCross2 - 1)];
-        dfs dg = df_add(df_add(dfs{d0.x, d0.y}, dfs{d1.x, d1.y}), df_add(dfs{c0.x, c0.y}, df_add(dfs{c1.x, c1.y}, dfs{c2v.x, c2v.y})));
+        const dfs dg = df_add(df_add(dfs{d0.x, d0.y}, dfs{d1.x, d1.y}),
+                              df_add(dfs{c0.x, c0.y}, df_add(dfs{c1.x, c1.y}, dfs{c2v.x, c2v.y})));
         const dfs zr = df_add(cre(zs), df_neg(dg));
-        const float4 acc = vcfma(cpack(zr, cim(zs)), x[row], vzero<float4>());   // (z_s - diag) x_row
+        const float4 acc = vcfma(cpack(zr, cim(zs)), xr, vzero<float4>());
         float2 ah = hi2(acc), al = lo2(acc);
-        // w = (z_s - diag) x - (hops) - J (spin flips) - J' (pair hops)
         float2 s, e;
         pk_two_sum(ah, pk_neg(h), s, e);
         ah = s;
         al = pk_add(al, pk_sub(e, l));
-        const float Jh = (float)J, Jl = (float)(J - (double)Jh), Ph = (float)Jp, Pl = (float)(Jp - (double)Ph);
-        pk_acc_prod(ah, al, make_float2(-Jh, -Jh), make_float2(-Jl, -Jl), hj, lj);
-        pk_acc_prod(ah, al, make_float2(-Ph, -Ph), make_float2(-Pl, -Pl), hp, lp);
+        pk_acc_prod(ah, al, make_float2(Jh, Jh), make_float2(Jl, Jl), hj, lj);
+        pk_acc_prod(ah, al, make_float2(Ph, Ph), make_float2(Pl, Pl), hp, lp);
         pk_norm(ah, al);
-        w = pk4(ah, al);
+        return pk4(ah, al);
+    }
+
+    __device__ __forceinline__ bool operator()(int64_t unit, int lane, float4 zs, const float4* x, int64_t& row,
+                                               float4& w) const {
+        int u, d;
+        unit_rc(unit, lane, u, d);
+        if (d >= D_dn) return false;
+        row = (int64_t)u * D_dn + d;
+        const uint32_t su = st_up[u], sd = st_dn[d];
+        int cu, cp, cv;
+        counts(su, sd, u, d, cu, cp, cv);
+        // hops: h + l = (H's hopping part) x = sum t sign x over the hop lists
+        float2 h = make_float2(0.f, 0.f), l = make_float2(0.f, 0.f);
+        hops_df(hop_dn + d, D_dn, x + (size_t)u * D_dn, 1, D_dn, h, l);
+        hops_df(hop_up + u, D_up, x + d, D_dn, D_up, h, l);
+        float2 hj = make_float2(0.f, 0.f), lj = hj, hp = hj, lp = hj;
+        joint_df(u, d, x, hj, lj, hp, lp);
+        w = combine_df(u, d, cu, cp, cv, zs, x[row], h, l, hj, lj, hp, lp);
         return true;
     }
 
+    // ---- two-pass form used by the persistent solve: pass 1 over the units
+    // row-major (the CTAs share the rows x[u][:] of the down hops and the few
+    // rows of the joint moves) stores q = (z_s - diag) x - (down hops and
+    // joint moves) + beta q_old; pass 2 tile-major (the CTAs share the column
+    // tiles x[:][tile] of the up hops) subtracts the up hops.
+    static constexpr bool kTwoPass = true;
+    __device__ __forceinline__ bool rc_rows(int64_t unit, int lane, int& u, int& d) const {
+        const int tiles = (D_dn + 31) / 32;
+        u = (int)(unit / tiles);
+        d = (int)(unit % tiles) * 32 + lane;
+        return d < D_dn;
+    }
+    __device__ __forceinline__ bool rc_tiles(int64_t unit, int lane, int& u, int& d) const {
+        u = (int)(unit % D_up);
+        d = (int)(unit / D_up) * 32 + lane;
+        return d < D_dn;
+    }
+    __device__ __forceinline__ float4 pass1_w(int u, int d, float4 zs, const float4* x) const {
+        const int64_t row = (int64_t)u * D_dn + d;
+        const uint32_t su = st_up[u], sd = st_dn[d];
+        int cu, cp, cv;
+        counts(su, sd, u, d, cu, cp, cv);
+        float2 h = make_float2(0.f, 0.f), l = make_float2(0.f, 0.f);
+        hops_df(hop_dn + d, D_dn, x + (size_t)u * D_dn, 1, D_dn, h, l);
+        float2 hj = make_float2(0.f, 0.f), lj = hj, hp = hj, lp = hj;
+        joint_df(u, d, x, hj, lj, hp, lp);
+        return combine_df(u, d, cu, cp, cv, zs, x[row], h, l, hj, lj, hp, lp);
+    }
+    __device__ __forceinline__ void pass1(int64_t unit, int lane, float4 zs, float4 bp, const float4* x,
+                                          float4* q) const {
+        int u, d;
+        if (!rc_rows(unit, lane, u, d)) return;
+        const int64_t row = (int64_t)u * D_dn + d;
+        q[row] = vcfma(bp, q[row], pass1_w(u, d, zs, x));
+    }
+    __device__ __forceinline__ bool pass2(int64_t unit, int lane, const float4* x, float4* q, int64_t& row,
+                                          float4& qn) const {
+        int u, d;
+        if (!rc_tiles(unit, lane, u, d)) return false;
+        row = (int64_t)u * D_dn + d;
+        float2 h = make_float2(0.f, 0.f), l = make_float2(0.f, 0.f);
+        hops_df(hop_up + u, D_up, x + d, D_dn, D_up, h, l);
+        pk_norm(h, l);
+        const float4 q1 = q[row];
+        float2 s, e;
+        pk_two_sum(hi2(q1), pk_neg(h), s, e);
+        e = pk_add(e, pk_sub(lo2(q1), l));
+        pk_norm(s, e);
+        qn = pk4(s, e);
+        q[row] = qn;
+        return true;
+    }
     // FP64 (double2) and complex64 (float2) vectors
+    template <typename VV>
+    __device__ __forceinline__ VV hops_v(const int32_t* tab, int64_t ts, const VV* base, int64_t stride,
+                                         int64_t lim) const {
+        using T = decltype(base->x);
+        VV acc;
+        acc.x = 0; acc.y = 0;
+        for (int j = 0; j < S2; ++j) {
+            const int e = tab[(int64_t)j * ts];
+            if (e < 0) break;
+            if (!chk(dbg, 22, e >> 8, lim)) continue;
+            const VV xv = base[(int64_t)(e >> 8) * stride];
+            const T t = (T)amp[(e >> 1) & 127];
+            const T c = (e & 1) ? -t : t;   // H's element
+            acc.x += c * xv.x; acc.y += c * xv.y;
+        }
+        return acc;
+    }
+    template <typename VV>
+    __device__ __forceinline__ void pass1(int64_t unit, int lane, VV zs, VV bp, const VV* x, VV* q) const {
+        using T = decltype(zs.x);
+        int u, d;
+        if (!rc_rows(unit, lane, u, d)) return;
+        const int64_t row = (int64_t)u * D_dn + d;
+        const uint32_t su = st_up[u], sd = st_dn[d];
+        int cu, cp, cv;
+        counts(su, sd, u, d, cu, cp, cv);
+        const T diag = (T)(self_up[u] + self_dn[d] + cross[min(cu, kCross2 - 1)] +
+                           cross[kCross2 + min(cp, kCross2 - 1)] + cross[2 * kCross2 + min(cv, kCross2 - 1)]);
+        const VV hs = hops_v(hop_dn + d, D_dn, x + (size_t)u * D_dn, 1, D_dn);
+        VV acc;
+        const VV xr = x[row];
+        const T zr = zs.x - diag;
+        acc.x = zr * xr.x - zs.y * xr.y - hs.x;
+        acc.y = zr * xr.y + zs.y * xr.x - hs.y;
+        for (int i = 0; i < ns; ++i) {
+            const int32_t mu = orb_up[(size_t)i * D_up + u], md = orb_dn[(size_t)i * D_dn + d];
+            if (mu < 0 || md < 0) continue;
+            const int tu = mu >> 1, td = md >> 1;
+            if (!chk(dbg, 23, tu, D_up) || !chk(dbg, 24, td, D_dn)) continue;
+            const VV xv = x[(size_t)tu * D_dn + td];
+            const T c = -(T)((mu & 1) != (md & 1) ? J : Jp);
+            acc.x += c * xv.x; acc.y += c * xv.y;
+        }
+        q[row] = vcfma(bp, q[row], acc);
+    }
+    template <typename VV>
+    __device__ __forceinline__ bool pass2(int64_t unit, int lane, const VV* x, VV* q, int64_t& row, VV& qn) const {
+        int u, d;
+        if (!rc_tiles(unit, lane, u, d)) return false;
+        row = (int64_t)u * D_dn + d;
+        const VV hs = hops_v(hop_up + u, D_up, x + d, D_dn, D_up);
+        qn = q[row];
+        qn.x -= hs.x; qn.y -= hs.y;
+        q[row] = qn;
+        return true;
+    }
+
     template <typename VV>
     __device__ __forceinline__ bool operator()(int64_t unit, int lane, VV zs, const VV* x, int64_t& row,
                                                VV& w) const {
         using T = decltype(zs.x);
-        const int u = (int)(unit % D_up);
-        const int d = (int)(unit / D_up) * 32 + lane;
+        int u, d;
+        unit_rc(unit, lane, u, d);
         if (d >= D_dn) return false;
         row = (int64_t)u * D_dn + d;
         const uint32_t su = st_up[u], sd = st_dn[d];
@@ -242,11 +384,12 @@ struct ApplyHubbard2 {
             acc.y = zr * xr.y + zs.y * xr.x;
         }
         for (int sp = 0; sp < 2; ++sp) {
-            const int32_t* tab = sp ? hop_up + (size_t)u * S2 : hop_dn + (size_t)d * S2;
+            const int32_t* tab = sp ? hop_up + u : hop_dn + d;
+            const int64_t ts = sp ? D_up : D_dn;
             const VV* base = sp ? x + d : x + (size_t)u * D_dn;
             const int64_t stride = sp ? D_dn : 1, lim = sp ? D_up : D_dn;
             for (int j = 0; j < S2; ++j) {
-                const int e = tab[j];
+                const int e = tab[(int64_t)j * ts];
                 if (e < 0) break;
                 if (!chk(dbg, 22, e >> 8, lim)) continue;
                 const VV xv = base[(int64_t)(e >> 8) * stride];
@@ -256,7 +399,7 @@ struct ApplyHubbard2 {
             }
         }
         for (int i = 0; i < ns; ++i) {
-            const int32_t mu = orb_up[(size_t)u * ns + i], md = orb_dn[(size_t)d * ns + i];
+            const int32_t mu = orb_up[(size_t)i * D_up + u], md = orb_dn[(size_t)i * D_dn + d];
             if (mu < 0 || md < 0) continue;
             const int tu = mu >> 1, td = md >> 1;
             if (!chk(dbg, 23, tu, D_up) || !chk(dbg, 24, td, D_dn)) continue;
@@ -286,11 +429,13 @@ static ApplyHubbard2<R> make_apply2(const Hubbard& hb) {
     ap.selff_up = hb.d_self2f;
     ap.selff_dn = hb.d_self2f + D;
     ap.amp = hb.d_amp2;
-    ap.ampf = hb.d_amp2f;
+    ap.ampf = reinterpret_cast<const float4*>(hb.d_amp2f);
     ap.cross = hb.d_cross2;
     ap.crossf = hb.d_cross2f;
     ap.S2 = hb.S2; ap.ns = hb.ns; ap.D_up = hb.D_up; ap.D_dn = hb.D_dn;
     ap.J = hb.J; ap.Jp = hb.Jp;
+    ap.Jh = (float)(-hb.J); ap.Jl = (float)(-hb.J - (double)ap.Jh);
+    ap.Ph = (float)(-hb.Jp); ap.Pl = (float)(-hb.Jp - (double)ap.Ph);
     ap.n = (int64_t)hb.D_up * hb.D_dn;
     ap.dbg = nullptr;
     return ap;
@@ -364,8 +509,8 @@ __global__ void __launch_bounds__(kVecBlock) k_hub2_hx(ApplyHubbard2<double> ap,
     const double bp = (xprev && beta) ? *beta : 0.0;
     double acc = 0.0;
     for (int64_t unit = w0; unit < nunits; unit += nw) {
-        const int u = (int)(unit % ap.D_up);
-        const int d = (int)(unit / ap.D_up) * 32 + lane;
+        int u, d;
+        ap.unit_rc(unit, lane, u, d);
         if (d >= ap.D_dn) continue;
         const int64_t row = (int64_t)u * ap.D_dn + d;
         const uint32_t su = ap.st_up[u], sd = ap.st_dn[d];
@@ -376,18 +521,19 @@ __global__ void __launch_bounds__(kVecBlock) k_hub2_hx(ApplyHubbard2<double> ap,
         const double xi = x[row];
         double hx = 0.0;
         for (int sp = 0; sp < 2; ++sp) {
-            const int32_t* tab = sp ? ap.hop_up + (size_t)u * ap.S2 : ap.hop_dn + (size_t)d * ap.S2;
+            const int32_t* tab = sp ? ap.hop_up + u : ap.hop_dn + d;
+            const int64_t ts = sp ? ap.D_up : ap.D_dn;
             const double* base = sp ? x + d : x + (size_t)u * ap.D_dn;
             const int64_t stride = sp ? ap.D_dn : 1;
             for (int j = 0; j < ap.S2; ++j) {
-                const int e = tab[j];
+                const int e = tab[(int64_t)j * ts];
                 if (e < 0) break;
                 const double t = ap.amp[(e >> 1) & 127];
                 hx = fma((e & 1) ? -t : t, base[(int64_t)(e >> 8) * stride], hx);
             }
         }
         for (int i = 0; i < ap.ns; ++i) {
-            const int32_t mu = ap.orb_up[(size_t)u * ap.ns + i], md = ap.orb_dn[(size_t)d * ap.ns + i];
+            const int32_t mu = ap.orb_up[(size_t)i * ap.D_up + u], md = ap.orb_dn[(size_t)i * ap.D_dn + d];
             if (mu < 0 || md < 0) continue;
             hx = fma((mu & 1) != (md & 1) ? ap.J : ap.Jp, x[(size_t)(mu >> 1) * ap.D_dn + (md >> 1)], hx);
         }
@@ -453,15 +599,17 @@ extern "C" int scocg_create_hubbard2(scocg_handle* out, int n_sites, int n_bonds
     cudaStream_t s = h->stream;
     std::vector<int32_t> bonds(2 * std::max(n_bonds, 1), 0);
     std::vector<double> amp(4 * std::max(n_bonds, 1), 0.0);
-    std::vector<float2> ampf(amp.size());
+    std::vector<float4> ampf(2 * amp.size());
     for (int b = 0; b < n_bonds; ++b) {
         bonds[2 * b] = bond_i[b]; bonds[2 * b + 1] = bond_j[b];
         for (int q = 0; q < 4; ++q) amp[4 * b + q] = bond_t[4 * b + q];
     }
-    for (size_t q = 0; q < amp.size(); ++q) {
-        const float hi = (float)amp[q];
-        ampf[q] = make_float2(hi, (float)(amp[q] - (double)hi));
-    }
+    for (size_t q = 0; q < amp.size(); ++q)   // entry 2 q + sign bit: the amplitude times its sign
+        for (int sg = 0; sg < 2; ++sg) {
+            const double v = sg ? -amp[q] : amp[q];
+            const float hi = (float)v, lo = (float)(v - (double)hi);
+            ampf[2 * q + sg] = make_float4(hi, hi, lo, lo);
+        }
     std::vector<double> cross(3 * kCross2);
     std::vector<float2> crossf(3 * kCross2);
     for (int c = 0; c < kCross2; ++c) {
@@ -478,12 +626,12 @@ extern "C" int scocg_create_hubbard2(scocg_handle* out, int n_sites, int n_bonds
     if (e == cudaSuccess) e = cudaMalloc(&hb.d_self2, sizeof(double) * 2 * D);
     if (e == cudaSuccess) e = cudaMalloc(&hb.d_self2f, sizeof(float2) * 2 * D);
     if (e == cudaSuccess) e = cudaMalloc(&hb.d_amp2, sizeof(double) * amp.size());
-    if (e == cudaSuccess) e = cudaMalloc(&hb.d_amp2f, sizeof(float2) * amp.size());
+    if (e == cudaSuccess) e = cudaMalloc(&hb.d_amp2f, sizeof(float4) * ampf.size());
     if (e == cudaSuccess) e = cudaMalloc(&hb.d_cross2, sizeof(double) * cross.size());
     if (e == cudaSuccess) e = cudaMalloc(&hb.d_cross2f, sizeof(float2) * cross.size());
     if (e == cudaSuccess) e = cudaMalloc(&hb.d_bonds2, sizeof(int32_t) * bonds.size());
     if (e == cudaSuccess) e = cudaMemcpyAsync(hb.d_amp2, amp.data(), sizeof(double) * amp.size(), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hb.d_amp2f, ampf.data(), sizeof(float2) * amp.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hb.d_amp2f, ampf.data(), sizeof(float4) * ampf.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hb.d_cross2, cross.data(), sizeof(double) * cross.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hb.d_cross2f, crossf.data(), sizeof(float2) * cross.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hb.d_bonds2, bonds.data(), sizeof(int32_t) * bonds.size(), cudaMemcpyHostToDevice, s);

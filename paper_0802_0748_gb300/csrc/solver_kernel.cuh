@@ -225,6 +225,13 @@ __device__ __forceinline__ void shift_update(const SolveArgs<R>& a, int k, const
     else active = 1;
 }
 
+// Applies whose phase A runs in two passes (they declare kTwoPass and
+// provide pass1 / pass2, see ApplyHubbard).
+template <class A, class = void>
+struct HasTwoPass : std::false_type {};
+template <class A>
+struct HasTwoPass<A, std::void_t<decltype(A::kTwoPass)>> : std::integral_constant<bool, A::kTwoPass> {};
+
 // Decision word of the per-iteration checks: kGoOn continues, any other value
 // ends the solve with that status (SCOCG_OK is 0, so 0 cannot mean "go on").
 constexpr int kGoOn = 0x7fffffff;
@@ -364,13 +371,24 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
             // when the rounds do not come out even, one unit fewer
             const int wi = c_here ? (warp + kWarps - 1) % kWarps : warp;
             const int64_t a_first = Apply::kMap == kMapStrided ? (int64_t)cta + (int64_t)G * wi : ubeg + wi;
-            for (int64_t u = a_first; u < u_end; u += u_step) {
-                int64_t row;
-                V w;
-                if (ap(u, lane, zs, (const V*)a.r, row, w)) {
-                    const V qn = vcfma(bp, a.q[row], w);
-                    a.q[row] = qn;
-                    acc_bil(rq[0], rq[1], a.r[row], qn);
+            if constexpr (HasTwoPass<Apply>::value) {
+                // two passes over the units in two orders, a grid barrier between
+                for (int64_t u = a_first; u < u_end; u += u_step) ap.pass1(u, lane, zs, bp, (const V*)a.r, a.q);
+                if (!grid_barrier(a.sync, epoch)) return;
+                for (int64_t u = a_first; u < u_end; u += u_step) {
+                    int64_t row;
+                    V qn;
+                    if (ap.pass2(u, lane, (const V*)a.r, a.q, row, qn)) acc_bil(rq[0], rq[1], a.r[row], qn);
+                }
+            } else {
+                for (int64_t u = a_first; u < u_end; u += u_step) {
+                    int64_t row;
+                    V w;
+                    if (ap(u, lane, zs, (const V*)a.r, row, w)) {
+                        const V qn = vcfma(bp, a.q[row], w);
+                        a.q[row] = qn;
+                        acc_bil(rq[0], rq[1], a.r[row], qn);
+                    }
                 }
             }
             block_sum_n<2>(rq, s.scratch, s_part);
