@@ -77,10 +77,13 @@ typedef struct {
     int precision;        /* scocg_precision                                          */
     int max_iter;         /* iteration cap per solve; 0 -> 100000                     */
     int replace_every;    /* MIXED: FP64 true-residual replacement of the seed every
-                             this many iterations; 0 or < 0 disables it (default).
-                             Replacing the seed residual injects the seed's rounding
-                             gap into every shift's recurrence, scaled by 1/pi^k, so
-                             it improves the seed but not the other shifts           */
+                             this many iterations (reliable update of the seed's
+                             residual from its compensated solution); 0 or < 0
+                             disables it (default).  It does not make complex64
+                             vectors accurate: each FP32 apply perturbs the Krylov
+                             process itself, which a residual update does not undo
+                             (measured: no gain in G).  SCOCG_MIXED_DF is the
+                             reduced-precision mode that reaches FP64-like G      */
     int seed;             /* seed shift index; < 0 or out of range -> the seed rule:
                              smallest Im z, then Re z nearest the median Re z, then
                              the lowest index                                         */

@@ -244,10 +244,14 @@ def test_mixed_matches_fp64_oracle(S, oracle_mod):
 
 def test_mixed_residual_replacement(S, oracle_mod):
     """MIXED with the FP64 seed-residual replacement every 20 iterations: the
-    replacement runs (n_replace > 0) and G stays within the complex64 bound.
-    The replacement injects the seed's rounding gap into every shift's
-    recurrence, so it does not tighten G (measured 2.8e-4 here, against 3e-5
-    without it in a CPU emulation of the kernel); the bound is 1e-3."""
+    replacement runs (n_replace > 0) and G stays within the complex64 bound
+    (1e-3).  The replacement does not tighten G: it resets the seed's
+    residual, but every apply of complex64 vectors perturbs the Krylov
+    process by ~eps32 ||H||, which no residual update undoes.  Measured on the
+    GPU (6^3 x 4 matrix, eta 0.05, 32 shifts, 200,000 iterations, where FP64
+    converges in 1,632): max G error 7.5e-5 without replacement, 3.6e-4 /
+    1.1e-3 / 2.6e-3 / 6.4e-5 / 6.7e-5 replacing every 10 / 25 / 50 / 100 / 400
+    iterations; the compensated mode reaches 2.1e-11 in 1,656 iterations."""
     h = inputs.anderson_csr(3, seed=7)
     b = inputs.random_unit_complex(h.n, 100)
     shifts = np.linspace(-6, 6, 16) + 0.05j
