@@ -28,6 +28,9 @@
 namespace scocg {
 
 constexpr int kMaxProjB = 4;   // unit projections per right-hand side of a block (multi-rhs) solve
+#ifndef SCOCG_BSR4_GROUP
+#define SCOCG_BSR4_GROUP 4     // slots of the blocked apply whose loads are issued together
+#endif
 constexpr int kPartC = 10;   // active, best |pi|, arg, bad, pi_prev, pi_cur, alpha_k of arg
 
 struct ShiftState {          // device arrays, [K] or [K][M]
@@ -178,11 +181,12 @@ struct ApplyBSR4 {
         int s0 = unit_off[unit], s1 = unit_off[unit + 1];
         if (!chk(dbg, 4, s1, nslots + 1) || !chk(dbg, 4, s0, s1 + 1)) s0 = s1 = 0;
         VV acc = vzero<VV>();
-        for (int s = s0; s < s1; s += 4) {            // four slots in flight; the last group predicated
-            int cb[4];
-            R v[4][4];
+        constexpr int kG = SCOCG_BSR4_GROUP;
+        for (int s = s0; s < s1; s += kG) {           // kG slots in flight; the last group predicated
+            int cb[kG];
+            R v[kG][4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < kG; ++j) {
                 if (s + j < s1) {
                     cb[j] = ld_stream(bcol + (size_t)(s + j) * 8 + br);
                     load_row(bval + ((size_t)(s + j) * 8 + br) * 16 + rr * 4, v[j]);
@@ -191,7 +195,7 @@ struct ApplyBSR4 {
                 }
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) block_fma(acc, cb[j], v[j], x);
+            for (int j = 0; j < kG; ++j) block_fma(acc, cb[j], v[j], x);
         }
         if (row < n) {
             w = vsub(vcfma(zs, x[row], vzero<VV>()), acc);
