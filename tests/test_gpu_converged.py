@@ -97,7 +97,7 @@ def test_anderson64_converged_vs_oracle(S):
         finally:
             S.scocg_destroy(hh)
         assert info["status"] == 0, (prec, info["status"], info["iters"])
-        out[prec] = G.cpu().numpy()[0]
+        out[prec] = G.cpu().numpy()[0, 0]
     assert relerr(out[0][sub], ref) < 2e-8
     assert relerr(out[2][sub], ref) < DF_BOUND
 
@@ -120,7 +120,7 @@ def test_hubbard14_converged_vs_oracle(S):
         finally:
             S.scocg_destroy(hh)
         assert info["status"] == 0, (prec, info["status"])
-        out[prec] = G.cpu().numpy()[0]
+        out[prec] = G.cpu().numpy()[0, 0]
     assert relerr(out[0][sub], ref) < FP64_BOUND
     assert relerr(out[2][sub], ref) < DF_BOUND
     assert relerr(out[2], out[0]) < DF_BOUND
