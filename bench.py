@@ -84,7 +84,7 @@ from paper_0802_0748_gb300.inputs import ANDERSON64_BOUNDS as BOUNDS, BATCH32_BO
 # capture (dram__bytes_read.sum + dram__bytes_write.sum over a 60-iteration
 # launch on this workload, divided by 60; the command is in profiles/); valid
 # only for the kernel sources with this digest.
-TRAFFIC = {"digest": "af586c71491254fd", "df": (7.622577e9 + 33.650688e6) / 60}
+TRAFFIC = {"digest": "95398101030b0042", "df": (7.645879e9 + 88.885248e6) / 60}
 
 
 # The sources of the persistent solve kernel and its launch (the kernel the
@@ -573,6 +573,42 @@ def leg_ground(scocg, dev, stream, hbm):
             "spectrum_shift_iter_per_s": sinfo["shift_iters"] / (ms_s * 1e-3)}
 
 
+def profile_case(name: str, max_iter: int):
+    """One compensated solve (a single launch of the persistent kernel) of a
+    bench workload, capped at max_iter iterations, for an ncu capture:
+    ``anderson`` the headline matrix and shifts, ``hubbard`` the 14-site ring,
+    ``hubbard2-5`` the two-orbital sqrt(8) x sqrt(8) model with 5 up / 5 down
+    electrons (19,079,424 states, a smaller device footprint than the paper's
+    6/6 sector for the replayed capture)."""
+    import math
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0802_0748_gb300 import inputs, scocg
+    opts = scocg.SolveOptions(precision=scocg.MIXED_DF, max_iter=max_iter)
+    if name == "anderson":
+        wl = inputs.workload("anderson", "full", bounds=BOUNDS)
+        h = scocg.scocg_create_csr(wl.csr.rowptr, wl.csr.col, wl.csr.val, opts=opts)
+        shifts, b = wl.shifts, wl.rhs[0]
+    elif name == "hubbard":
+        wl = inputs.workload("hubbard", "full")
+        p = wl.hubbard
+        h = scocg.scocg_create_hubbard(p["L"], p["n_up"], p["n_dn"], p["t"], p["U"], p["V"], p["periodic"], opts=opts)
+        shifts, b = wl.shifts, wl.rhs[0]
+    else:
+        n = math.comb(16, 5) ** 2
+        h = scocg.scocg_create_hubbard2(inputs.eg_model(), 5, 5, opts=opts)
+        shifts, b = np.linspace(-12.0, 48.0, 128) + 0.1j, inputs.random_unit_complex(n, 6)
+    bd = torch.from_numpy(b).cuda()
+    cd = torch.from_numpy(np.conj(b)[None, :]).cuda()
+    G, info = scocg.scocg_solve(h, shifts, bd, proj_vec=cd, tol=TOL)
+    torch.cuda.synchronize()
+    scocg.scocg_destroy(h)
+    print(json.dumps({"profile_case": name, "status": info["status"], "iters": info["iters"],
+                      "us_per_iter": info["seconds"] / max(info["iters"], 1) * 1e6}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -585,7 +621,13 @@ def main():
     ap.add_argument("--max-iter", type=int, default=0, help="cap on seed iterations (0 = to convergence)")
     ap.add_argument("--legs", default="batch,multi,chain,adjoint,hubbard,hubbard2,density,krylov,ground",
                     help="comma list of the other workloads, each timed once beside the headline")
+    ap.add_argument("--profile-case", default="", choices=["", "anderson", "hubbard", "hubbard2-5"],
+                    help="run one compensated solve of that workload (--max-iter iterations) and exit: "
+                         "the launch the committed ncu summaries capture")
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case(args.profile_case, args.max_iter or 60)
+        return
 
     from paper_0802_0748_gb300 import inputs
     wl = inputs.workload("anderson", "full", bounds=BOUNDS)
