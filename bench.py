@@ -573,9 +573,10 @@ def leg_ground(scocg, dev, stream, hbm):
             "spectrum_shift_iter_per_s": sinfo["shift_iters"] / (ms_s * 1e-3)}
 
 
-def profile_case(name: str, max_iter: int):
-    """One compensated solve (a single launch of the persistent kernel) of a
-    bench workload, capped at max_iter iterations, for an ncu capture:
+def profile_case(name: str, max_iter: int, precision: int):
+    """One solve (a single launch of the persistent kernel) of a bench
+    workload in the given precision, capped at max_iter iterations, for an ncu
+    capture:
     ``anderson`` the headline matrix and shifts, ``hubbard`` the 14-site ring,
     ``hubbard2-5`` the two-orbital sqrt(8) x sqrt(8) model with 5 up / 5 down
     electrons (19,079,424 states, a smaller device footprint than the paper's
@@ -586,7 +587,7 @@ def profile_case(name: str, max_iter: int):
     import __graft_entry__
     __graft_entry__.build()
     from paper_0802_0748_gb300 import inputs, scocg
-    opts = scocg.SolveOptions(precision=scocg.MIXED_DF, max_iter=max_iter)
+    opts = scocg.SolveOptions(precision=precision, max_iter=max_iter)
     if name == "anderson":
         wl = inputs.workload("anderson", "full", bounds=BOUNDS)
         h = scocg.scocg_create_csr(wl.csr.rowptr, wl.csr.col, wl.csr.val, opts=opts)
@@ -622,11 +623,11 @@ def main():
     ap.add_argument("--legs", default="batch,multi,chain,adjoint,hubbard,hubbard2,density,krylov,ground",
                     help="comma list of the other workloads, each timed once beside the headline")
     ap.add_argument("--profile-case", default="", choices=["", "anderson", "hubbard", "hubbard2-5"],
-                    help="run one compensated solve of that workload (--max-iter iterations) and exit: "
+                    help="run one solve of that workload in --precision (--max-iter iterations) and exit: "
                          "the launch the committed ncu summaries capture")
     args = ap.parse_args()
     if args.profile_case:
-        profile_case(args.profile_case, args.max_iter or 60)
+        profile_case(args.profile_case, args.max_iter or 60, PREC_NAMES[args.precision])
         return
 
     from paper_0802_0748_gb300 import inputs
