@@ -425,6 +425,8 @@ def scocg_ground_state(h: Handle, v0, m: int = 60, cg_steps: int = 0, max_cycles
     import torch
     if v0.dtype != torch.float64 or not v0.is_cuda:
         raise TypeError("v0 must be a CUDA float64 tensor")
+    if v0.numel() != scocg_dim(h):
+        raise ValueError("v0 must have the handle's dimension")
     v0 = v0.reshape(-1).contiguous()
     psi = torch.empty_like(v0)
     E = ctypes.c_double()
@@ -446,6 +448,9 @@ def scocg_krylov_sd(h: Handle, b, nu: int, shifts, proj_idx=None, proj_vec=None)
     import torch
     if b.dtype != torch.float64 or not b.is_cuda:
         raise TypeError("b must be a CUDA float64 tensor")
+    n = scocg_dim(h)
+    if b.numel() != n:
+        raise ValueError("b must have the handle's dimension")
     b = b.reshape(-1).contiguous()
     z, zp = _shifts(shifts)
     K = z.size
@@ -459,6 +464,8 @@ def scocg_krylov_sd(h: Handle, b, nu: int, shifts, proj_idx=None, proj_vec=None)
         keep = (proj_vec if proj_vec.dim() == 2 else proj_vec.reshape(1, -1)).contiguous()
         if keep.dtype != torch.float64 or not keep.is_cuda:
             raise TypeError("proj_vec must be a CUDA float64 tensor")
+        if keep.shape[1] != n:
+            raise ValueError("proj_vec rows must have the handle's dimension")
         M = keep.shape[0]
         pvec_p = _dev(keep)
     G = torch.empty((M, K), dtype=torch.complex128, device=b.device)
@@ -481,6 +488,8 @@ def scocg_excite(h_from: Handle, h_to: Handle, site: int, spin: int, create: boo
         raise TypeError("psi must be a CUDA float64 tensor")
     n = ctypes.c_int64()
     _check(lib().scocg_dim(h_to.ptr, ctypes.byref(n)), "scocg_dim")
+    if psi.numel() != scocg_dim(h_from):
+        raise ValueError("psi must have the source sector's dimension")
     out = torch.empty(n.value, dtype=torch.complex128, device=psi.device)
     psi = psi.reshape(-1).contiguous()
     _check(lib().scocg_excite(h_from.ptr, h_to.ptr, int(site), int(spin), int(bool(create)), _dev(psi), _dev(out)),

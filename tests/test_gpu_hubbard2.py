@@ -193,3 +193,101 @@ def test_invalid_models(S):
         S.scocg_create_hubbard2(star, 1, 1)
     with pytest.raises(S.ScocgError):
         S.scocg_create_hubbard2(m, 17, 0)
+
+
+def test_spectra_end_to_end_small_sector(S, oracle_mod):
+    """The Sec. IV.B pipeline on the sqrt(8) x sqrt(8) cluster, 2 up 1 down
+    (1,920 states): GPU ground state (E against dense eigh of the oracle's
+    CSR, residual through the oracle's CSR), c and c+ of every mode and spin
+    bit-exact against the oracle's Jordan-Wigner operator applied to the same
+    psi, the sum rules sum_m ||c_{m s} psi||^2 = n_s and ||c_m psi||^2 +
+    ||c+_m psi||^2 = 1, and the ionization and affinity spectra of mode 0 up
+    (FP64 and compensated) against the oracle's Lehmann sum and shifted COCG
+    on the target sectors' CSR."""
+    import scipy.sparse as sp
+    from oracle import ground
+    m = inputs.eg_model()
+    nu, nd, M = 2, 1, 16
+    rp, c, v = oracle_mod.hubbard2_csr(m, nu, nd)
+    n = rp.size - 1
+    H0 = sp.csr_matrix((v, c, rp), shape=(n, n))
+    E = np.linalg.eigvalsh(H0.toarray())
+    h0 = S.scocg_create_hubbard2(m, nu, nd)
+    targets = {}
+    try:
+        e0, psi, info = S.scocg_ground_state(h0, cuda(inputs.random_unit_real(n, 21)), m=60, cg_steps=30, tol=1e-11)
+        assert info["status"] == 0 and abs(e0 - E[0]) < 1e-10 * max(1.0, abs(E[0]))
+        p = psi.cpu().numpy()
+        assert np.linalg.norm(H0 @ p - e0 * p) <= info["residual"] * (1 + 1e-6) + 1e-13
+        norms = {}
+        for spin in (0, 1):
+            for create in (False, True):
+                d = 1 if create else -1
+                key = (nu + d, nd) if spin == 0 else (nu, nd + d)
+                targets[key] = S.scocg_create_hubbard2(m, *key)
+                for mode in range(M):
+                    b = S.scocg_excite(h0, targets[key], mode, spin, create, psi).cpu().numpy()
+                    ref = ground.fermion_op(M, nu, nd, mode, spin, create, p)
+                    assert np.all(b.imag == 0)
+                    assert np.array_equal(b.real, ref), (mode, spin, create)
+                    norms[mode, spin, create] = float(ref @ ref)
+        for spin, ns in ((0, nu), (1, nd)):
+            assert abs(sum(norms[mode, spin, False] for mode in range(M)) - ns) < 1e-12
+            for mode in range(M):
+                assert abs(norms[mode, spin, False] + norms[mode, spin, True] - 1.0) < 1e-12
+        w = np.linspace(-4.0, 24.0, 24)
+        eta = 0.1
+        for create in (False, True):
+            key = (nu + 1, nd) if create else (nu - 1, nd)
+            b = S.scocg_excite(h0, targets[key], 0, 0, create, psi)
+            bn = b.cpu().numpy().real
+            z = (e0 + w + 1j * eta) if create else (e0 - w - 1j * eta)
+            trp, tc, tv = oracle_mod.hubbard2_csr(m, *key)
+            ref = oracle_mod.shifted_cocg(trp, tc, tv, z, bn.astype(np.complex128),
+                                          proj_vec=bn[None, :].astype(np.complex128), tol=1e-12).G[0]
+            if trp.size - 1 <= 2000:
+                nt = trp.size - 1
+                lehm = ground.lehmann_green(sp.csr_matrix((tv, tc, trp), shape=(nt, nt)), bn, z)
+                assert np.max(np.abs(lehm - ref)) < 1e-10 * np.max(np.abs(ref))
+            for prec, tol, bound in ((0, 1e-12, 1e-9), (2, 1e-10, 1e-7)):
+                S.scocg_set_opts(targets[key], S.SolveOptions(precision=prec))
+                G, sinfo = S.scocg_solve(targets[key], z, b, proj_vec=b, tol=tol)
+                assert sinfo["status"] == 0
+                g = G.cpu().numpy()[0, 0]
+                assert np.max(np.abs(g - ref)) < bound * np.max(np.abs(ref)), (create, prec)
+    finally:
+        S.scocg_destroy(h0)
+        for t in targets.values():
+            S.scocg_destroy(t)
+
+
+def test_full_sector_ground_state_sampled(S, oracle_mod):
+    """The paper's 6 up 6 down sector (64,128,064 states): after the
+    ground-state cycles, 256 sampled rows of H psi - E psi, computed one by one
+    by the oracle, are each below the reported residual, psi has unit norm,
+    and 512 sampled entries of c_{5 up} psi (mode 5 = site 2, orbital 1, into
+    5 up 6 down) equal the oracle's one-by-one operator bit for bit."""
+    from oracle import ground
+    m = inputs.eg_model()
+    h = S.scocg_create_hubbard2(m, 6, 6)
+    h1 = S.scocg_create_hubbard2(m, 5, 6)
+    try:
+        n = S.scocg_dim(h)
+        e0, psi, info = S.scocg_ground_state(h, cuda(inputs.random_unit_real(n, 8)), m=60, cg_steps=30,
+                                             max_cycles=3, tol=1e-8)
+        assert info["status"] in (0, 1)
+        res = info["residual"]
+        assert np.isfinite(e0) and res < 1e-2
+        p = psi.cpu().numpy()
+        assert abs(np.linalg.norm(p) - 1.0) < 1e-12
+        rows = np.random.default_rng(9).choice(n, 256, replace=False)
+        hp = oracle_mod.hubbard2_rows(m, 6, 6, rows, p)
+        assert np.all(np.abs(hp - e0 * p[rows]) <= res * (1 + 1e-6) + 1e-13)
+        b = S.scocg_excite(h, h1, 5, 0, False, psi).cpu().numpy()
+        tgt = np.random.default_rng(10).choice(b.size, 512, replace=False)
+        ref = ground.fermion_op_at(16, 6, 6, 5, 0, False, p, tgt)
+        assert np.array_equal(b.real[tgt], ref)
+    finally:
+        S.scocg_destroy(h)
+        S.scocg_destroy(h1)
+        torch.cuda.empty_cache()
