@@ -498,56 +498,75 @@ cudaError_t hubbard2_apply(const Hubbard& hb, int prec, double2 z, const void* x
 }
 
 // Real FP64 operator of the ground-state iteration, y = (H - sigma) x - beta
-// x_prev with the block's partial of x^T y (same contract as the ring's).
-__global__ void __launch_bounds__(kVecBlock) k_hub2_hx(ApplyHubbard2<double> ap, int64_t nunits, const double* x,
-                                                       double* y, const double* xprev, const double* beta,
-                                                       double sigma, const int* skip, double* part) {
+// x_prev with the block's partial of x^T y (same contract as the ring's), in
+// the two passes of the solve's phase A: pass 1 visits the units row-major
+// (the CTAs share the rows x[u][:] of the down hops and the joint moves),
+// pass 2 tile-major (the CTAs share the column tiles x[:][tile] of the up
+// hops) and forms the partials.
+__device__ __forceinline__ double hop_sum_real(const double* amp, int S2, const int32_t* tab, int64_t ts,
+                                               const double* base, int64_t stride) {
+    double hx = 0.0;
+    for (int j = 0; j < S2; ++j) {
+        const int e = tab[(int64_t)j * ts];
+        if (e < 0) break;
+        const double t = amp[(e >> 1) & 127];
+        hx = fma((e & 1) ? -t : t, base[(int64_t)(e >> 8) * stride], hx);
+    }
+    return hx;
+}
+
+__global__ void __launch_bounds__(kVecBlock) k_hub2_hx1(ApplyHubbard2<double> ap, int64_t nunits, const double* x,
+                                                        double* y, const double* xprev, const double* beta,
+                                                        double sigma, const int* skip) {
     if (skip && *skip) return;
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (blockIdx.x * (int64_t)kVecBlock + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * kVecBlock) >> 5;
     const double bp = (xprev && beta) ? *beta : 0.0;
-    double acc = 0.0;
     for (int64_t unit = w0; unit < nunits; unit += nw) {
         int u, d;
-        ap.unit_rc(unit, lane, u, d);
-        if (d >= ap.D_dn) continue;
+        if (!ap.rc_rows(unit, lane, u, d)) continue;
         const int64_t row = (int64_t)u * ap.D_dn + d;
         const uint32_t su = ap.st_up[u], sd = ap.st_dn[d];
         int cu, cp, cv;
         ap.counts(su, sd, u, d, cu, cp, cv);
         const double diag = ap.self_up[u] + ap.self_dn[d] + ap.cross[min(cu, kCross2 - 1)] +
                             ap.cross[kCross2 + min(cp, kCross2 - 1)] + ap.cross[2 * kCross2 + min(cv, kCross2 - 1)];
-        const double xi = x[row];
-        double hx = 0.0;
-        for (int sp = 0; sp < 2; ++sp) {
-            const int32_t* tab = sp ? ap.hop_up + u : ap.hop_dn + d;
-            const int64_t ts = sp ? ap.D_up : ap.D_dn;
-            const double* base = sp ? x + d : x + (size_t)u * ap.D_dn;
-            const int64_t stride = sp ? ap.D_dn : 1;
-            for (int j = 0; j < ap.S2; ++j) {
-                const int e = tab[(int64_t)j * ts];
-                if (e < 0) break;
-                const double t = ap.amp[(e >> 1) & 127];
-                hx = fma((e & 1) ? -t : t, base[(int64_t)(e >> 8) * stride], hx);
-            }
-        }
+        double hx = hop_sum_real(ap.amp, ap.S2, ap.hop_dn + d, ap.D_dn, x + (size_t)u * ap.D_dn, 1);
         for (int i = 0; i < ap.ns; ++i) {
             const int32_t mu = ap.orb_up[(size_t)i * ap.D_up + u], md = ap.orb_dn[(size_t)i * ap.D_dn + d];
             if (mu < 0 || md < 0) continue;
             hx = fma((mu & 1) != (md & 1) ? ap.J : ap.Jp, x[(size_t)(mu >> 1) * ap.D_dn + (md >> 1)], hx);
         }
-        double yi = fma(diag - sigma, xi, hx);
+        double yi = fma(diag - sigma, x[row], hx);
         if (xprev) yi = fma(-bp, xprev[row], yi);
         y[row] = yi;
-        acc = fma(xi, yi, acc);
+    }
+}
+
+__global__ void __launch_bounds__(kVecBlock, 4) k_hub2_hx2(ApplyHubbard2<double> ap, int64_t nunits, const double* x,
+                                                        double* y, const int* skip, double* part) {
+    if (skip && *skip) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)kVecBlock + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * kVecBlock) >> 5;
+    double acc = 0.0;
+    for (int64_t unit = w0; unit < nunits; unit += nw) {
+        int u, d;
+        if (!ap.rc_tiles(unit, lane, u, d)) continue;
+        const int64_t row = (int64_t)u * ap.D_dn + d;
+        const double yi = y[row] + hop_sum_real(ap.amp, ap.S2, ap.hop_up + u, ap.D_up, x + d, ap.D_dn);
+        y[row] = yi;
+        acc = fma(x[row], yi, acc);
     }
     block_partial(acc, part);
 }
 
 cudaError_t hubbard2_hx(const Hubbard& hb, const double* x, double* y, const double* xprev, const double* beta,
                         double sigma, const int* skip, double* part, int grid, cudaStream_t st) {
-    k_hub2_hx<<<grid, kVecBlock, 0, st>>>(make_apply2<double>(hb), hb.nunits, x, y, xprev, beta, sigma, skip, part);
+    const ApplyHubbard2<double> ap = make_apply2<double>(hb);
+    k_hub2_hx1<<<grid, kVecBlock, 0, st>>>(ap, hb.nunits, x, y, xprev, beta, sigma, skip);
+    k_hub2_hx2<<<grid, kVecBlock, 0, st>>>(ap, hb.nunits, x, y, skip, part);
     return cudaGetLastError();
 }
 
