@@ -35,6 +35,7 @@
 #ifndef SCOCG_H
 #define SCOCG_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -228,6 +229,53 @@ int scocg_apply(scocg_handle h, scocg_c128 z, const void *x, void *y, int precis
 int scocg_solve(scocg_handle h, const scocg_c128 *shifts, int nshift, const void *rhs, int nrhs,
                 const int64_t *proj_idx, const void *proj_vec, int nproj, double tol,
                 scocg_c128 *G_out, scocg_info *info);
+
+/*
+ * scocg_solve_resume -- continue the handle's last scocg_solve from where it
+ * stopped at max_iter (status SCOCG_NOT_CONVERGED), reusing what was already
+ * computed as the seed switch of Sec. III.C does when it carries on with a
+ * new seed: the seed vectors r_n and q_n, every shift's recurrence values
+ * (pi^k, projected p^k and x^k, freeze state) and the FP64 seed scalars stay
+ * in the handle's device workspace, and the continued solve starts from them
+ * instead of r_0 = b.
+ * The seed iteration count carries on (scocg_set_opts with a larger max_iter
+ * caps the total); shifts frozen at the earlier tol stay frozen, the others
+ * run to this call's tol.  With the same grid the continued solve equals an
+ * uninterrupted one bit for bit.
+ *   arguments as scocg_solve with nrhs = 1; shifts (bit for bit), the
+ *   projection kind, the unit indices, nproj and the handle's precision must
+ *   be those of the stopped solve, and rhs / proj_vec the same data (the
+ *   dense projections are read again every iteration)
+ * Only one right-hand side solved by the persistent kernel can be continued
+ * (not block mode, not scocg_solve_full); any other solve on the handle
+ * discards the state.  Returns SCOCG_ERR_INVALID when there is no state to
+ * continue or the inputs differ; otherwise as scocg_solve (a continuation
+ * that stops at max_iter again can itself be continued).  info->shift_iters
+ * and info->seconds count this call's work, info->iters the total.
+ */
+int scocg_solve_resume(scocg_handle h, const scocg_c128 *shifts, int nshift, const void *rhs,
+                       const int64_t *proj_idx, const void *proj_vec, int nproj, double tol,
+                       scocg_c128 *G_out, scocg_info *info);
+
+/*
+ * Checkpoint of the continuation state on the host (so that a solve can be
+ * continued by another process or after the handle was destroyed):
+ *   scocg_state_size  bytes of the state of the handle's last stopped solve
+ *                     (SCOCG_ERR_INVALID, *bytes = 0, when there is none)
+ *   scocg_state_save  copies it into the caller's host buffer (>= that size)
+ *   scocg_state_load  makes the buffer the handle's continuation state; the
+ *                     next scocg_solve_resume continues from it.  The handle
+ *                     must hold the same H (N, nnz and the handle kind are
+ *                     checked, the values are not) and have the saved
+ *                     precision; SCOCG_ERR_INVALID otherwise.
+ * The buffer holds a header, the shifts, the unit projection indices and the
+ * device bytes of r_n, q_n (and for SCOCG_MIXED the seed direction and the
+ * compensated solution), the per-shift recurrence arrays and the seed
+ * scalars.  It is tied to this library's build (no format guarantee).
+ */
+int scocg_state_size(scocg_handle h, size_t *bytes);
+int scocg_state_save(scocg_handle h, void *buf, size_t bytes);
+int scocg_state_load(scocg_handle h, const void *buf, size_t bytes);
 
 /*
  * scocg_solve_full -- the same solve for one right-hand side, but every shift's

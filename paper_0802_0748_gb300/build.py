@@ -13,7 +13,7 @@ ROOT = PKG.parent
 CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = BUILD / "libscocg.so"
-SOURCES = ["api.cu", "layout.cu", "solver.cu", "hubbard.cu", "adjoint.cu", "noalloc.cu", "multi.cu", "block.cu",
+SOURCES = ["api.cu", "layout.cu", "solver.cu", "solver_resume.cu", "hubbard.cu", "adjoint.cu", "noalloc.cu", "multi.cu", "block.cu",
            "density.cu", "ground.cu", "hubbard2.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", str(ROOT / "include")]

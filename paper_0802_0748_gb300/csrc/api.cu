@@ -48,6 +48,22 @@ cudaError_t Workspace::reserve(size_t bytes) {
     return cudaSuccess;
 }
 
+cudaError_t Workspace::reserve_keep(size_t bytes, size_t keep, cudaStream_t s) {
+    off = 0;
+    if (bytes <= cap) return cudaSuccess;
+    void* nb = nullptr;
+    cudaError_t e = cudaMalloc(&nb, bytes);
+    if (e != cudaSuccess) return e;
+    if (base && keep > 0) e = cudaMemcpyAsync(nb, base, std::min(keep, cap), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { cudaFree(nb); return e; }
+    if (base) cudaFree(base);
+    if (gen) *gen = next_generation();
+    base = nb;
+    cap = bytes;
+    return cudaSuccess;
+}
+
 void Workspace::release() {
     if (base) cudaFree(base);
     base = nullptr; cap = 0; off = 0;
@@ -297,10 +313,12 @@ static int solve_one_rhs(scocg_ctx* h, const double2* d_z, int K, int seed, cons
                          int grid, ShiftState S, double* partA, double* partB, double* partC, int strideB,
                          typename Vec<R>::T* r, typename Vec<R>::T* q, typename Vec<R>::T* pseed,
                          typename Vec<R>::T* xhi, typename Vec<R>::T* xlo, double2* xd, const Layout& L,
-                         double2* Xf = nullptr, double2* Pf = nullptr) {
+                         ResumeState* rstate, int resume, double2* Xf = nullptr, double2* Pf = nullptr) {
     SolveArgs<R> a{};
     a.Xf = Xf;
     a.Pf = Pf;
+    a.rstate = rstate;
+    a.resume = resume;
     a.n = h->n;
     a.rows_per_unit = h->kind == HandleKind::kHubbard ? 32 : rows_per_unit(L.kind);
     a.nunits = h->kind == HandleKind::kHubbard ? h->hub.nunits : (h->n + a.rows_per_unit - 1) / a.rows_per_unit;
@@ -396,8 +414,6 @@ __global__ void k_to_df(int64_t n, const double2* in, float4* out) {
     if (i < n) out[i] = df_from(in[i]);
 }
 
-int algorithmic_bytes_note(void) { return 0; }
-
 }  // namespace scocg
 
 extern "C" int scocg_solve(scocg_handle h, const scocg_c128* shifts, int nshift, const void* rhs, int nrhs,
@@ -408,12 +424,90 @@ extern "C" int scocg_solve(scocg_handle h, const scocg_c128* shifts, int nshift,
                       h->opts.precision, nullptr, nullptr);
 }
 
+extern "C" int scocg_solve_resume(scocg_handle h, const scocg_c128* shifts, int nshift, const void* rhs,
+                                  const int64_t* proj_idx, const void* proj_vec, int nproj, double tol,
+                                  scocg_c128* G_out, scocg_info* info) {
+    if (!h) return SCOCG_ERR_INVALID;
+    return solve_impl(h, shifts, nshift, rhs, 1, proj_idx, proj_vec, nproj, tol, G_out, info, h->opts.precision,
+                      nullptr, nullptr, true);
+}
+
+namespace {
+// Header of a saved continuation state; the shifts, the unit projection
+// indices and the workspace bytes follow it.
+struct StateHeader {
+    uint64_t magic;
+    int32_t version, prec, K, M, dense, kind;
+    int64_t n, nnz;          // of the handle's H (a partial check that the loading handle holds the same H)
+    uint64_t state_bytes;
+};
+constexpr uint64_t kStateMagic = 0x31747367636f6373ull;   // "scocgst1" little-endian
+
+size_t state_total(const scocg_ctx* h) {
+    return sizeof(StateHeader) + sizeof(scocg_c128) * (size_t)h->rs.K + sizeof(int64_t) * (size_t)h->rs.M +
+           h->rs.state_bytes;
+}
+}  // namespace
+
+extern "C" int scocg_state_size(scocg_handle h, size_t* bytes) {
+    if (!h || !bytes) return SCOCG_ERR_INVALID;
+    *bytes = 0;
+    if (!h->rs.ok) return SCOCG_ERR_INVALID;
+    *bytes = state_total(h);
+    return SCOCG_OK;
+}
+
+extern "C" int scocg_state_save(scocg_handle h, void* buf, size_t bytes) {
+    if (!h || !buf || !h->rs.ok || bytes < state_total(h)) return SCOCG_ERR_INVALID;
+    StateHeader hd{kStateMagic, 1, h->rs.prec, h->rs.K, h->rs.M, h->rs.dense ? 1 : 0, (int32_t)h->kind, h->n,
+                   h->nnz, h->rs.state_bytes};
+    char* p = static_cast<char*>(buf);
+    std::memcpy(p, &hd, sizeof(hd));
+    p += sizeof(hd);
+    std::memcpy(p, h->rs.z.data(), sizeof(scocg_c128) * (size_t)hd.K);
+    p += sizeof(scocg_c128) * (size_t)hd.K;
+    std::memcpy(p, h->rs.cidx.data(), sizeof(int64_t) * (size_t)hd.M);
+    p += sizeof(int64_t) * (size_t)hd.M;
+    cudaError_t e = cudaMemcpyAsync(p, h->ws.base, h->rs.state_bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return cuda_status(e);
+}
+
+extern "C" int scocg_state_load(scocg_handle h, const void* buf, size_t bytes) {
+    if (!h || !buf || bytes < sizeof(StateHeader)) return SCOCG_ERR_INVALID;
+    StateHeader hd;
+    std::memcpy(&hd, buf, sizeof(hd));
+    if (hd.magic != kStateMagic || hd.version != 1 || hd.n != h->n || hd.nnz != h->nnz ||
+        hd.kind != (int32_t)h->kind || hd.K < 1 || hd.K > 4096 || hd.M < 1 ||
+        hd.M > kMaxProj || (hd.prec != SCOCG_FP64 && hd.prec != SCOCG_MIXED && hd.prec != SCOCG_MIXED_DF))
+        return SCOCG_ERR_INVALID;
+    const size_t need = sizeof(hd) + sizeof(scocg_c128) * (size_t)hd.K + sizeof(int64_t) * (size_t)hd.M +
+                        hd.state_bytes;
+    if (bytes < need) return SCOCG_ERR_INVALID;
+    const char* p = static_cast<const char*>(buf) + sizeof(hd);
+    h->rs.ok = false;
+    cudaError_t e = h->ws.reserve(hd.state_bytes);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->ws.base, p + sizeof(scocg_c128) * (size_t)hd.K + sizeof(int64_t) * (size_t)hd.M,
+                            hd.state_bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    h->rs.prec = hd.prec; h->rs.K = hd.K; h->rs.M = hd.M; h->rs.dense = hd.dense != 0;
+    const scocg_c128* z = reinterpret_cast<const scocg_c128*>(p);
+    h->rs.z.assign(z, z + hd.K);
+    const int64_t* ci = reinterpret_cast<const int64_t*>(p + sizeof(scocg_c128) * (size_t)hd.K);
+    h->rs.cidx.assign(ci, ci + hd.M);
+    h->rs.state_bytes = hd.state_bytes;
+    h->rs.ok = true;
+    return SCOCG_OK;
+}
+
 // The solve driver.  prec selects the vector precision; Xf/Pf (device
 // complex128 [nshift][N] each, FP64 only, one right-hand side) switch on the
 // full-vector mode that forms every shift's solution x_k.
 int scocg::solve_impl(scocg_ctx* h, const scocg_c128* shifts, int nshift, const void* rhs, int nrhs,
                       const int64_t* proj_idx, const void* proj_vec, int nproj, double tol, scocg_c128* G_out,
-                      scocg_info* info, int prec, double2* Xf, double2* Pf) {
+                      scocg_info* info, int prec, double2* Xf, double2* Pf, bool resume) {
     if (!h || !shifts || nshift < 1 || nshift > 4096 || !rhs || nrhs < 1 || nproj < 1 ||
         nproj > kMaxProj || !G_out || (proj_idx == nullptr) == (proj_vec == nullptr) || !(tol >= 0.0))
         return SCOCG_ERR_INVALID;
@@ -423,6 +517,17 @@ int scocg::solve_impl(scocg_ctx* h, const scocg_c128* shifts, int nshift, const 
         for (int64_t j = 0; j < (int64_t)nrhs * nproj; ++j)
             if (proj_idx[j] < 0 || proj_idx[j] >= h->n) return SCOCG_ERR_INVALID;
     if (Xf && (prec != SCOCG_FP64 || nrhs != 1 || nshift > kMaxFullShifts || !Pf)) return SCOCG_ERR_INVALID;
+    if (resume) {
+        // the same inputs as the stopped solve: precision, shifts (bit for
+        // bit), projection kind and unit indices, one right-hand side
+        const auto& rs = h->rs;
+        if (!rs.ok || Xf || nrhs != 1 || prec != rs.prec || nshift != rs.K || nproj != rs.M ||
+            (proj_vec != nullptr) != rs.dense ||
+            std::memcmp(shifts, rs.z.data(), sizeof(scocg_c128) * (size_t)nshift) != 0 ||
+            (proj_idx && std::memcmp(proj_idx, rs.cidx.data(), sizeof(int64_t) * (size_t)nproj) != 0))
+            return SCOCG_ERR_INVALID;
+    }
+    if (!resume) h->rs.ok = false;   // any other solve overwrites the state
     const size_t dyn_smem = Xf ? (size_t)nshift * kFullSmem : 0;
     const bool mixed = prec == SCOCG_MIXED;
     const bool dfm = prec == SCOCG_MIXED_DF;
@@ -470,6 +575,8 @@ int scocg::solve_impl(scocg_ctx* h, const scocg_c128* shifts, int nshift, const 
     int64_t* d_cidx = nullptr;
     double2* d_z = nullptr;
     ShiftState S{};
+    ResumeState* rstate = nullptr;
+    size_t state_end = 0;
     double *partA = nullptr, *partB = nullptr, *partC = nullptr;
     auto carve = [&](Carver& c) {
         r = c.take(vbytes);
@@ -491,16 +598,21 @@ int scocg::solve_impl(scocg_ctx* h, const scocg_c128* shifts, int nshift, const 
         S.frozen = (int*)c.take(sizeof(int) * K);
         S.iters = (int*)c.take(sizeof(int) * K);
         S.resid = (double*)c.take(sizeof(double) * K);
+        rstate = (ResumeState*)c.take(sizeof(ResumeState));
+        state_end = c.off;
         partA = (double*)c.take(sizeof(double) * grid * 4);
         partB = (double*)c.take(sizeof(double) * grid * strideB);
         partC = (double*)c.take(sizeof(double) * grid * kPartC);
     };
     Carver measure{nullptr, 0};
     carve(measure);
-    cudaError_t e = h->ws.reserve(measure.off);
+    // a continuation keeps the state bytes when the workspace grows (its
+    // partials may be sized for another grid)
+    cudaError_t e = resume ? h->ws.reserve_keep(measure.off, h->rs.state_bytes, s) : h->ws.reserve(measure.off);
     if (e != cudaSuccess) return cuda_status(e);
     Carver cut{static_cast<char*>(h->ws.base), 0};
     carve(cut);
+    if (resume && state_end != h->rs.state_bytes) return SCOCG_ERR_INVALID;
 
     e = cudaMemcpyAsync(d_z, shifts, sizeof(double2) * K, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && mixed && proj_vec) {
@@ -533,14 +645,17 @@ int scocg::solve_impl(scocg_ctx* h, const scocg_c128* shifts, int nshift, const 
         double2* G = reinterpret_cast<double2*>(G_out) + (size_t)j * M * K;
         cudaEventRecord(ev0, s);
         const int64_t* ci = proj_idx ? d_cidx : nullptr;
+        ResumeState* rsj = nrhs == 1 && !Xf ? rstate : nullptr;
+        const int res = resume ? 1 : 0;
         int st = mixed ? solve_one_rhs<float>(h, d_z, K, seed, b, ci, cv, M, tol, G, grid, S, partA, partB, partC,
                                               strideB, (float2*)r, (float2*)q, (float2*)ps, (float2*)xh,
-                                              (float2*)xl, xd, L)
+                                              (float2*)xl, xd, L, rsj, res)
                : dfm ? solve_one_rhs<DF>(h, d_z, K, seed, b, ci, cv, M, tol, G, grid, S, partA, partB, partC,
-                                         strideB, (float4*)r, (float4*)q, nullptr, nullptr, nullptr, nullptr, L)
+                                         strideB, (float4*)r, (float4*)q, nullptr, nullptr, nullptr, nullptr, L,
+                                         rsj, res)
                      : solve_one_rhs<double>(h, d_z, K, seed, b, ci, cv, M, tol, G, grid, S, partA, partB, partC,
                                              strideB, (double2*)r, (double2*)q, nullptr, nullptr, nullptr, nullptr, L,
-                                             Xf, Pf);
+                                             rsj, res, Xf, Pf);
         cudaEventRecord(ev1, s);
         if (st != SCOCG_OK) { worst = st; break; }
         Ctrl c;
@@ -573,6 +688,15 @@ int scocg::solve_impl(scocg_ctx* h, const scocg_c128* shifts, int nshift, const 
         }
     }
     cudaEventDestroy(ev0); cudaEventDestroy(ev1);
+    // a single-right-hand-side solve that stopped at max_iter can be continued
+    h->rs.ok = nrhs == 1 && !Xf && worst == SCOCG_NOT_CONVERGED;
+    if (h->rs.ok) {
+        h->rs.prec = prec; h->rs.K = K; h->rs.M = M; h->rs.dense = proj_vec != nullptr;
+        h->rs.z.assign(shifts, shifts + K);
+        h->rs.cidx.assign(M, 0);
+        if (proj_idx) h->rs.cidx.assign(proj_idx, proj_idx + M);
+        h->rs.state_bytes = state_end;
+    }
     if (info) {
         info->iters = iters;
         info->n_switch = nsw;

@@ -39,6 +39,8 @@ struct Workspace {
     size_t off = 0;
     unsigned long long* gen = nullptr;   // bumped on every (re)allocation
     cudaError_t reserve(size_t bytes);   // resets the carve offset
+    // the same, keeping the first `keep` bytes when the buffer has to grow
+    cudaError_t reserve_keep(size_t bytes, size_t keep, cudaStream_t s);
     void* get(size_t bytes);
     void release();
 };
@@ -112,6 +114,17 @@ struct scocg_ctx {
     scocg::Workspace ws;
     unsigned long long ws_gen = 0;   // changes whenever ws is (re)allocated or the handle is new
     std::vector<scocg::TuneEntry> tune;   // autotuner decisions of this handle
+    // the single-right-hand-side solve that stopped at max_iter and can be
+    // continued (scocg_solve_resume): its inputs and the workspace bytes
+    // [0, state_bytes) that hold its state
+    struct {
+        bool ok = false;
+        int prec = 0, K = 0, M = 0;
+        bool dense = false;
+        std::vector<scocg_c128> z;
+        std::vector<int64_t> cidx;
+        size_t state_bytes = 0;
+    } rs;
 
     void free_all();
     scocg::Layout layout(bool prefer_csr) const;
@@ -151,7 +164,7 @@ cudaError_t hubbard2_launch_solve(const SolveArgs<R>& a, const Hubbard& hb, int 
 constexpr int kMaxFullShifts = 512;   // shifts per full-vector launch (dynamic shared memory)
 int solve_impl(scocg_ctx* h, const scocg_c128* shifts, int nshift, const void* rhs, int nrhs,
                const int64_t* proj_idx, const void* proj_vec, int nproj, double tol, scocg_c128* G_out,
-               scocg_info* info, int prec, double2* Xf, double2* Pf);
+               scocg_info* info, int prec, double2* Xf, double2* Pf, bool resume = false);
 
 // multi-system plans (multi.cu)
 void multi_forget(scocg_ctx* h);

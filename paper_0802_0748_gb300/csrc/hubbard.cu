@@ -161,6 +161,13 @@ struct ApplyHubbard {
     // pass 2 visits them tile-major (unit = tile * D_up + u: the CTAs share the
     // column tiles x[:][tile] of the up hops) and adds t (up-hop sum).
     static constexpr bool kTwoPass = SCOCG_RING_TWO_PASS;
+    // the row whose term (unit, lane) adds to the r^T q partial of phase A
+    // (the tile-major order of the one-pass apply and of pass 2)
+    __device__ __forceinline__ bool row_of(int64_t unit, int lane, int64_t& row) const {
+        const int u = (int)(unit % D_up), d = (int)(unit / D_up) * 32 + lane;
+        row = (int64_t)u * D_dn + d;
+        return d < D_dn;
+    }
     __device__ __forceinline__ bool rc_rows(int64_t unit, int lane, int& u, int& d) const {
         const int tiles = (D_dn + 31) / 32;
         u = (int)(unit / tiles);
@@ -347,11 +354,12 @@ cudaError_t hubbard_launch_solve(const SolveArgs<R>& a, const Hubbard& hb, int g
     ap.dbg = a.dbg;
     void* args[] = {(void*)&a, (void*)&ap};
     const size_t smem = a.Xf ? (size_t)a.K * kFullSmem : 0;
+    // a continuation of a stopped solve runs its own instantiation
+    const void* kern = a.resume ? (const void*)cocg_persistent<R, ApplyHubbard<W>, true>
+                                : (const void*)cocg_persistent<R, ApplyHubbard<W>, false>;
     if (smem > 0)   // above the 48 KB default together with the static part
-        cudaFuncSetAttribute((const void*)cocg_persistent<R, ApplyHubbard<W>>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return cudaLaunchCooperativeKernel((const void*)cocg_persistent<R, ApplyHubbard<W>>, dim3(grid), dim3(kBlock),
-                                       args, smem, st);
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kBlock), args, smem, st);
 }
 template cudaError_t hubbard_launch_solve<double>(const SolveArgs<double>&, const Hubbard&, int, cudaStream_t);
 template cudaError_t hubbard_launch_solve<float>(const SolveArgs<float>&, const Hubbard&, int, cudaStream_t);

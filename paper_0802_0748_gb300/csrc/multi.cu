@@ -198,6 +198,7 @@ int run_multi(int nsys, const scocg_handle* hs, const scocg_c128* const* shifts,
             };
             Carver measure{nullptr, 0};
             carve(measure);
+            h->rs.ok = false;   // the handle's continuation state is overwritten
             e = h->ws.reserve(measure.off);
             if (e != cudaSuccess) break;
             Carver cut{static_cast<char*>(h->ws.base), 0};

@@ -2,29 +2,9 @@
 // (precision, H layout) pair, plus a one-shot apply kernel y = (z - H) x.
 #include <type_traits>
 
-#include "solver_kernel.cuh"
-#include "solver_launch.h"
+#include "solver_dispatch.cuh"
 
 namespace scocg {
-
-// Dynamic shared memory above the 48 KB default (with the static part) needs
-// the kernel's opt-in; the full-vector mode asks for up to kMaxFullShifts x
-// kFullSmem bytes.
-template <typename R, class Apply>
-static void allow_dyn_smem(size_t smem) {
-    if (smem > 0)
-        cudaFuncSetAttribute((const void*)cocg_persistent<R, Apply>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-}
-
-template <typename R, class Apply>
-static cudaError_t coop_launch(const SolveArgs<R>& a, const Apply& ap, int grid, cudaStream_t st) {
-    void* args[] = {(void*)&a, (void*)&ap};
-    const size_t smem = a.Xf ? (size_t)a.K * kFullSmem : 0;
-    allow_dyn_smem<R, Apply>(smem);
-    return cudaLaunchCooperativeKernel((const void*)cocg_persistent<R, Apply>, dim3(grid), dim3(kBlock), args, smem,
-                                       st);
-}
 
 template <typename R, class Apply>
 static int occupancy_of(size_t smem) {
@@ -33,24 +13,6 @@ static int occupancy_of(size_t smem) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cocg_persistent<R, Apply>, kBlock, smem) != cudaSuccess)
         return 0;
     return nb;
-}
-
-// H values of each precision: FP64 for FP64 vectors, FP32 otherwise
-template <typename W>
-static const W* pick(const Layout& h, const double* d, const float* f);
-template <> const double* pick<double>(const Layout&, const double* d, const float*) { return d; }
-template <> const float* pick<float>(const Layout&, const double*, const float* f) { return f; }
-
-// The blocked apply of vector precision R on layout h (row lanes on row-major
-// blocks, or column lanes on the column-major copy for complex64 vectors).
-template <typename R>
-static typename BsrApply<R>::T make_bsr(const Layout& h, unsigned long long* dbg) {
-    using W = typename ValT<R>::T;
-    return typename BsrApply<R>::T{h.unit_off, h.bcol, pick<W>(h, h.bval64, h.bval32), h.n, h.nslots, dbg};
-}
-template <>
-ApplyBSR4C<float> make_bsr<float>(const Layout& h, unsigned long long* dbg) {
-    return ApplyBSR4C<float>{h.unit_off, h.bcol, h.bval32c, h.n, h.nslots, dbg};
 }
 
 template <typename R>
@@ -83,23 +45,7 @@ int rows_per_unit(LayoutKind k) {
 
 template <typename R>
 cudaError_t launch_solve(const SolveArgs<R>& a, const Layout& h, int grid, cudaStream_t st) {
-    using W = typename ValT<R>::T;
-    switch (h.kind) {
-        case LayoutKind::kBsr4: return coop_launch(a, make_bsr<R>(h, a.dbg), grid, st);
-        case LayoutKind::kCsr1: {
-            ApplyCSR<W, 1> ap{h.rowptr, h.col, pick<W>(h, h.val64, h.val32), h.n, h.nnz, a.dbg};
-            return coop_launch(a, ap, grid, st);
-        }
-        case LayoutKind::kCsr4: {
-            ApplyCSR<W, 4> ap{h.rowptr, h.col, pick<W>(h, h.val64, h.val32), h.n, h.nnz, a.dbg};
-            return coop_launch(a, ap, grid, st);
-        }
-        case LayoutKind::kCsr16: {
-            ApplyCSR<W, 16> ap{h.rowptr, h.col, pick<W>(h, h.val64, h.val32), h.n, h.nnz, a.dbg};
-            return coop_launch(a, ap, grid, st);
-        }
-    }
-    return cudaErrorInvalidValue;
+    return a.resume ? launch_solve_resume<R>(a, h, grid, st) : launch_layout<R, false>(a, h, grid, st);
 }
 template cudaError_t launch_solve<double>(const SolveArgs<double>&, const Layout&, int, cudaStream_t);
 template cudaError_t launch_solve<float>(const SolveArgs<float>&, const Layout&, int, cudaStream_t);

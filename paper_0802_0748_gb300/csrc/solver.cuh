@@ -46,6 +46,20 @@ struct ShiftState {          // device arrays, [K] or [K][M]
     double* resid;           // squared residual estimate (||r_k|| / ||b||)^2
 };
 
+// What a solve that stopped at max_iter leaves for a later launch to continue
+// from (scocg_solve_resume): it stops between the apply of iteration n and
+// its first reduction, so the workspace holds r_n, q_n and every shift's
+// recurrence after iteration n - 1; these are the seed scalars of that point.
+struct ResumeState {       // device, written by CTA 0
+    int valid;             // 1: the last solve stopped at max_iter
+    int n, seed, n_switch, n_replace, replace_on;
+    int rotated;           // the stopping apply visited its units in the rotated order
+    int pad;
+    double2 alpha_prev, beta_prev, rho, rho_prev, zs;
+    double rnorm, bnorm;
+    double2 cr_cur[kMaxProj];
+};
+
 struct SolveStats {          // device, written by CTA 0
     int status;
     int iters;
@@ -136,6 +150,11 @@ struct ApplyCSR {
         }
         return false;
     }
+    // the row whose term (unit, lane) adds to the apply's r^T q partial
+    __device__ __forceinline__ bool row_of(int64_t unit, int lane, int64_t& row) const {
+        row = unit * kRowsPerUnit + lane / LPR;
+        return row < n && lane % LPR == 0;
+    }
 };
 
 // 4x4-blocked sliced ELL: a unit is 8 block rows (32 rows); slot s of unit u
@@ -202,6 +221,11 @@ struct ApplyBSR4 {
             return true;
         }
         return false;
+    }
+    // the row whose term (unit, lane) adds to the apply's r^T q partial
+    __device__ __forceinline__ bool row_of(int64_t unit, int lane, int64_t& row) const {
+        row = unit * 32 + lane;
+        return row < n;
     }
 };
 
@@ -281,6 +305,11 @@ struct ApplyBSR4C {
         }
         return false;
     }
+    // the row whose term (unit, lane) adds to the apply's r^T q partial
+    __device__ __forceinline__ bool row_of(int64_t unit, int lane, int64_t& row) const {
+        row = unit * 32 + lane;
+        return row < n;
+    }
 };
 
 // The blocked apply of each vector precision: column lanes for complex64,
@@ -331,6 +360,10 @@ struct SolveArgs {
     // needs K * kFullSmem bytes of dynamic shared memory
     double2* Xf;
     double2* Pf;
+    // continuation: the state a solve stopped at max_iter leaves (written at
+    // exit when non-null), and resume = 1 to start from it instead of r_0 = b
+    ResumeState* rstate;
+    int resume;
 };
 constexpr int kFullSmem = 3 * 16 + 4;   // per shift: 1/pi_n, beta^k, alpha^k, active flag
 

@@ -236,9 +236,55 @@ struct HasTwoPass<A, std::void_t<decltype(A::kTwoPass)>> : std::integral_constan
 // ends the solve with that status (SCOCG_OK is 0, so 0 cannot mean "go on").
 constexpr int kGoOn = 0x7fffffff;
 
+// The first phase A of a solve continued from a ResumeState: the stopped
+// apply's r^T q partial again, from the stored r_n and q_n over the same rows
+// in the same order (so the continued solve matches an uninterrupted one bit
+// for bit), and the shift count as its deferred phase C left it.
+template <typename R, class Apply>
+__device__ __forceinline__ void resume_partials(const SolveArgs<R>& a, const Apply& ap, int G, int cta, int64_t ubeg,
+                                             int64_t u_end, int64_t u_step, bool active, SeedScalars& s,
+                                             double* s_part) {
+    using AT = typename Acc<R>::T;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool rot = a.rstate->rotated != 0;
+    const int wi = rot ? (warp + kWarps - 1) % kWarps : warp;
+    const int64_t first = Apply::kMap == kMapStrided ? (int64_t)cta + (int64_t)G * wi : ubeg + wi;
+    AT rq[2] = {};
+    for (int64_t u = first; u < u_end; u += u_step) {
+        int64_t row;
+        if (ap.row_of(u, lane, row)) acc_bil(rq[0], rq[1], a.r[row], a.q[row]);
+    }
+    const int act = __syncthreads_count(active);
+    block_sum_n<2>(rq, s.scratch, s_part);
+    if (tid == 0) {
+        double* pa = a.partA + cta;
+        pa[0] = s_part[0]; pa[G] = s_part[1];
+        pa[2 * G] = (double)act;
+        pa[3 * G] = 0.0;
+    }
+    __syncthreads();
+}
+
+// Thread 0 of CTA 0 at the end of a solve: the state a later launch continues
+// from when the solve stopped at max_iter (right after the apply of iteration
+// n).  Out of line, so that the solve loop's code is the same with or without it.
+static __device__ __noinline__ void save_resume_state(ResumeState* rs, const SeedScalars& s, int status, int M,
+                                               bool rotated) {
+    rs->valid = status == SCOCG_NOT_CONVERGED;
+    rs->n = s.n; rs->seed = s.seed; rs->n_switch = s.n_switch; rs->n_replace = s.n_replace;
+    rs->replace_on = s.replace_on;
+    rs->rotated = rotated;
+    rs->alpha_prev = s.alpha_prev; rs->beta_prev = s.beta_prev; rs->rho = s.rho; rs->rho_prev = s.rho_prev;
+    rs->zs = s.zs; rs->rnorm = s.rnorm; rs->bnorm = s.bnorm;
+    for (int m = 0; m < M; ++m) rs->cr_cur[m] = s.cr_cur[m];
+}
+
 // The whole solve of one system, run by its G co-resident CTAs (this one is
 // number cta among them).
-template <typename R, class Apply>
+// kResume: the instantiation that continues a stopped solve (a.resume = 1):
+// its init takes the stored state and its first phase A only forms the
+// stopped apply's partials again.
+template <typename R, class Apply, bool kResume = false>
 __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap, const int G, const int cta) {
     using V = typename Vec<R>::T;
     using AT = typename Acc<R>::T;
@@ -290,7 +336,29 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
 #endif
 
     // ------------------------------------------------------------ init: r_0 = b, q_{-1} = 0
-    {
+    // (or, continuing a solve stopped at max_iter, the stored state)
+    if constexpr (kResume) {
+        if (tid == 0) {
+            const ResumeState& rs = *a.rstate;
+            s.rho = rs.rho; s.rho_prev = rs.rho_prev;
+            s.alpha_prev = rs.alpha_prev; s.beta_prev = rs.beta_prev;
+            s.bnorm = rs.bnorm; s.rnorm = rs.rnorm;
+            s.seed = rs.seed; s.zs = rs.zs;
+            s_vs[0] = Vec<R>::make(s.zs);
+            s_vs[1] = Vec<R>::make(s.beta_prev);
+            s.n = rs.n;
+            s.active = a.K;
+            s.replace_on = rs.replace_on; s.n_switch = rs.n_switch; s.n_replace = rs.n_replace;
+            s.shift_iters = 0;
+        }
+        if (tid < M) s.cr_cur[tid] = a.rstate->cr_cur[tid];
+        // s_flag[4] (seed converged) decides whether the next apply takes a
+        // deferred shift update and visits its units rotated: restored so
+        // that a stop right after this pass records the stopped one's order
+        if (tid < 5) s_flag[tid] = tid == 4 ? (a.rstate->rotated ? 0 : 1) : 0;
+        __syncthreads();
+        resume_partials(a, ap, G, cta, ubeg, u_end, u_step, owns && !a.S.frozen[k_own], s, s_part);
+    } else {
         double nb = 0.0;
         for (int64_t i = rbeg + tid; i < rend; i += kBlock) {
             const double2 bi = a.b[i];
@@ -349,12 +417,13 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
     }
 
     // ------------------------------------------------------------ iterations
+    bool skip_a = kResume;                    // the continued solve's first phase A ran before it stopped
     while (!done) {
         SCOCG_TRACE(1);
         SCOCG_MARK(7);
         // ---- phase A: q_n = (z_s - H) r_n + beta_{n-1} q_{n-1}; partial r_n^T q_n
         // (with a deferred phase C of iteration n-1 in warp 0)
-        {
+        if (!skip_a) {
             const V zs = s_vs[0];
             const V bp = s_vs[1];
             AT rq[2] = {};
@@ -400,6 +469,7 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
                 pa[3 * G] = (double)s_flag[1];   // a pi^k of this CTA became zero or non-finite
             }
         }
+        skip_a = false;
         SCOCG_TRACE(2);
         SCOCG_MARK(0);
         if (!grid_barrier(a.sync, epoch, a.debug_inject == 1 && cta == 0 && s.n == 3)) return;
@@ -718,6 +788,9 @@ __device__ __forceinline__ void cocg_body(const SolveArgs<R>& a, const Apply& ap
         for (int m = 0; m < M; ++m) a.G[(size_t)m * a.K + k_own] = a.S.X[(size_t)k_own * M + m];
     }
     if (cta == 0 && tid == 0) {
+        // the stopping apply took the deferred shift update (and rotated its
+        // units) when the iteration before had not converged the seed
+        if (a.rstate) save_resume_state(a.rstate, s, status, M, defer_ok && s_flag[4] == 0);
         a.stats->iters = s.n;
         a.stats->n_switch = s.n_switch;
         a.stats->seed = s.seed;
@@ -740,9 +813,9 @@ template <typename R> struct MinBlocks { static constexpr int value = 2; };
 template <> struct MinBlocks<double> { static constexpr int value = 1; };
 template <> struct MinBlocks<DF> { static constexpr int value = SCOCG_DF_CTAS_PER_SM; };
 
-template <typename R, class Apply>
+template <typename R, class Apply, bool kResume = false>
 __global__ void __launch_bounds__(kBlock, MinBlocks<R>::value) cocg_persistent(SolveArgs<R> a, Apply ap) {
-    cocg_body(a, ap, (int)gridDim.x, (int)blockIdx.x);
+    cocg_body<R, Apply, kResume>(a, ap, (int)gridDim.x, (int)blockIdx.x);
 }
 
 // Several independent solves in one launch: CTAs [cta_off[s], cta_off[s+1])

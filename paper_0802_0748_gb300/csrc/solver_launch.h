@@ -34,6 +34,9 @@ int max_coresident_ctas(const Layout& h, int precision, int num_sms, size_t dyn_
 
 template <typename R>
 cudaError_t launch_solve(const SolveArgs<R>& a, const Layout& h, int grid, cudaStream_t st);
+// the continuation kernels (a.resume = 1), compiled in solver_resume.cu
+template <typename R>
+cudaError_t launch_solve_resume(const SolveArgs<R>& a, const Layout& h, int grid, cudaStream_t st);
 
 cudaError_t launch_apply(const Layout& h, int precision, double2 z, const void* x, void* y, cudaStream_t st);
 

@@ -29,6 +29,7 @@ EXPORTED = [
     "scocg_solve", "scocg_solve_full", "scocg_grad", "scocg_destroy", "scocg_strerror",
     "scocg_hubbard_tables", "scocg_solve_csr_noalloc", "scocg_solve_multi", "scocg_multi_release",
     "scocg_density", "scocg_ground_state", "scocg_excite", "scocg_krylov_sd", "scocg_create_hubbard2",
+    "scocg_solve_resume", "scocg_state_size", "scocg_state_save", "scocg_state_load",
 ]
 
 
@@ -100,6 +101,10 @@ def lib() -> ctypes.CDLL:
         L.scocg_set_opts.argtypes = [P, ctypes.POINTER(Opts)]
         L.scocg_apply.argtypes = [P, c128, P, P, I]
         L.scocg_solve.argtypes = [P, P, I, P, I, P, P, I, D, P, ctypes.POINTER(Info)]
+        L.scocg_solve_resume.argtypes = [P, P, I, P, P, P, I, D, P, ctypes.POINTER(Info)]
+        L.scocg_state_size.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+        L.scocg_state_save.argtypes = [P, P, ctypes.c_size_t]
+        L.scocg_state_load.argtypes = [P, P, ctypes.c_size_t]
         L.scocg_solve_full.argtypes = [P, P, I, P, D, P, ctypes.POINTER(Info)]
         L.scocg_grad.argtypes = [P, P, I, P, I, P, P, I, D, P, P, ctypes.POINTER(Info)]
         L.scocg_density.argtypes = [P, D, D, D, D, D, I, P, I, P, P, I, D, P, ctypes.POINTER(Info)]
@@ -299,6 +304,39 @@ def scocg_solve(h: Handle, shifts, rhs, proj_idx=None, proj_vec=None, tol: float
 
     rhs: CUDA complex128 [nrhs][N] (or [N]); proj_idx: host int [nrhs][nproj]
     (or [nproj], shared); proj_vec: CUDA complex128 [nproj][N]."""
+    return _solve(h, shifts, rhs, proj_idx, proj_vec, tol, resume=False)
+
+
+def scocg_solve_resume(h: Handle, shifts, rhs, proj_idx=None, proj_vec=None, tol: float = 1e-10):
+    """scocg_solve_resume: continues the handle's last solve, stopped at
+    max_iter, with the same arguments (one right-hand side); returns what
+    scocg_solve returns."""
+    return _solve(h, shifts, rhs, proj_idx, proj_vec, tol, resume=True)
+
+
+def scocg_state_size(h: Handle) -> int:
+    """Bytes of the handle's continuation state (0 when there is none)."""
+    n = ctypes.c_size_t(0)
+    lib().scocg_state_size(h.ptr, ctypes.byref(n))
+    return int(n.value)
+
+
+def scocg_state_save(h: Handle) -> np.ndarray:
+    """The continuation state of the handle's last stopped solve as a host uint8 array."""
+    n = ctypes.c_size_t(0)
+    _check(lib().scocg_state_size(h.ptr, ctypes.byref(n)), "scocg_state_size")
+    buf = np.empty(n.value, dtype=np.uint8)
+    _check(lib().scocg_state_save(h.ptr, buf.ctypes.data, buf.size), "scocg_state_save")
+    return buf
+
+
+def scocg_state_load(h: Handle, buf) -> None:
+    """Makes a saved state the handle's continuation state (scocg_solve_resume continues it)."""
+    b = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(lib().scocg_state_load(h.ptr, b.ctypes.data, b.size), "scocg_state_load")
+
+
+def _solve(h: Handle, shifts, rhs, proj_idx, proj_vec, tol, resume: bool):
     import torch
     z, zp = _shifts(shifts)
     K = z.size
@@ -326,9 +364,16 @@ def scocg_solve(h: Handle, shifts, rhs, proj_idx=None, proj_vec=None, tol: float
         pvec_p = _dev(pv)
     G = torch.zeros((nrhs, M, K), dtype=torch.complex128, device=rhs.device)
     info, it, rs = _info_struct(nrhs, K)
-    code = lib().scocg_solve(h.ptr, zp, K, _dev(rhs), nrhs, pidx_p, pvec_p, M, float(tol), _dev(G),
-                             ctypes.byref(info))
-    _check(code, "scocg_solve")
+    if resume:
+        if nrhs != 1:
+            raise ValueError("scocg_solve_resume continues one right-hand side")
+        code = lib().scocg_solve_resume(h.ptr, zp, K, _dev(rhs), pidx_p, pvec_p, M, float(tol), _dev(G),
+                                        ctypes.byref(info))
+        _check(code, "scocg_solve_resume")
+    else:
+        code = lib().scocg_solve(h.ptr, zp, K, _dev(rhs), nrhs, pidx_p, pvec_p, M, float(tol), _dev(G),
+                                 ctypes.byref(info))
+        _check(code, "scocg_solve")
     return G, _info_dict(info, it, rs, nrhs, K, code)
 
 
