@@ -90,13 +90,13 @@ from paper_0802_0748_gb300.inputs import ANDERSON64_BOUNDS as BOUNDS, BATCH32_BO
 # capture (dram__bytes_read.sum + dram__bytes_write.sum over a 60-iteration
 # launch on this workload, divided by 60; the command is in profiles/); valid
 # only for the kernel sources with this digest.
-TRAFFIC = {"digest": "95398101030b0042", "df": (7.645879e9 + 88.885248e6) / 60}
+TRAFFIC = {"digest": "3fd81777f6ce8fcd", "df": (7.643657e9 + 96.041984e6) / 60}
 
 
 # The sources of the persistent solve kernel and its launch (the kernel the
 # roofline line describes); the traffic figure is valid only for this digest.
-KERNEL_SOURCES = ("common.cuh", "dfloat.cuh", "solver.cuh", "solver_kernel.cuh", "solver_launch.h", "solver.cu",
-                  "layout.cu")
+KERNEL_SOURCES = ("common.cuh", "dfloat.cuh", "solver.cuh", "solver_kernel.cuh", "solver_launch.h",
+                  "solver_dispatch.cuh", "solver.cu", "layout.cu")
 
 
 def kernel_digest() -> str:
@@ -676,7 +676,7 @@ def main():
     ap.add_argument("--compare", default="fp64,mixed", help="comma list of other precisions timed once beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--max-iter", type=int, default=0, help="cap on seed iterations (0 = to convergence)")
-    ap.add_argument("--legs", default="batch,multi,chain,adjoint,hubbard,hubbard2,density,krylov,ground",
+    ap.add_argument("--legs", default="batch,multi,chain,adjoint,hubbard,hubbard2,density,krylov,ground,spectra2",
                     help="comma list of the other workloads, each timed once beside the headline")
     ap.add_argument("--profile-case", default="", choices=["", "anderson", "hubbard", "hubbard2-5"],
                     help="run one solve of that workload in --precision (--max-iter iterations) and exit: "
