@@ -498,6 +498,16 @@ def leg_krylov(scocg, dev, stream, hbm):
         dev_s = sum(o[3]["seconds"] for o in outs)
         out["krsd"][str(nu)] = {"ms_per_site": ms / nsite, "median_rel_err": med, "max_rel_err": mx,
                                 "us_per_lanczos_step": dev_s / (nu * nsite) * 1e6}
+        # all sites in one launch (every read of H serves the 16 recursions)
+        Bm = torch.stack(bs)
+        (Gm, used, im), msm = timed(stream, lambda: scocg.scocg_krylov_sd_multi(h, Bm, nu, z, pidx))
+        Gm = Gm.cpu().numpy()[:, 0, :]
+        med_m, mx_m = err(Gm)
+        Gs = np.stack([o[0].cpu().numpy()[0] for o in outs])
+        out["krsd"][str(nu)]["multi"] = {
+            "ms_per_site": msm / nsite, "median_rel_err": med_m, "max_rel_err": mx_m,
+            "us_per_step_all_sites": im["seconds"] / nu * 1e6,
+            "max_rel_diff_vs_one_site_launches": float(np.max(np.abs(Gm - Gs)) / np.max(np.abs(Gs)))}
     # shifted COCG stopped early: the loosest residual whose G meets the accuracy KR-SD reaches at its largest nu
     target = out["krsd"]["1024"]["median_rel_err"]
     out["cocg_equal_accuracy"] = None
@@ -513,6 +523,9 @@ def leg_krylov(scocg, dev, stream, hbm):
     step_bytes = 12.0 * h_csr.nnz + 4.0 * (h_csr.n + 1) + 8 * 8.0 * h_csr.n
     k = out["krsd"]["1024"]
     out["krsd_hbm_frac_nu1024"] = step_bytes / (k["us_per_lanczos_step"] * 1e-6) / 1e9 / hbm
+    # the 16-site launch: H once and the [n][16] vectors' passes per step
+    step_bytes_m = 12.0 * h_csr.nnz + 4.0 * (h_csr.n + 1) + 8 * 8.0 * h_csr.n * nsite
+    out["krsd_multi_hbm_frac_nu1024"] = step_bytes_m / (k["multi"]["us_per_step_all_sites"] * 1e-6) / 1e9 / hbm
     return out
 
 

@@ -490,6 +490,31 @@ int scocg_krylov_sd(scocg_handle h, const double *b, int nu, const scocg_c128 *s
                     const int64_t *proj_idx, const double *proj_vec, int nproj, scocg_c128 *G_out,
                     double *ritz, double *weight, int *nu_used, double *seconds);
 
+/*
+ * scocg_krylov_sd_multi -- scocg_krylov_sd for several right-hand sides with
+ * unit projections (e.g. the local Green's functions G_jj of many sites):
+ * B[r] is right-hand side r, its projections e_{proj_idx[r][m]}.  On the
+ * 4x4-blocked layout (CSR handles whose pattern allows it) up to 32 of them
+ * run as one cooperative launch whose Lanczos vectors are [N][T] (T = 8, 16
+ * or 32 slots, the right-hand side fastest), so that every read of H serves
+ * T recursions, each with its own scalars and end; other handles run the
+ * single-right-hand-side recursion once per right-hand side.  Each slot does
+ * the same arithmetic as scocg_krylov_sd (its partial sums run in another
+ * order).
+ *   B            device double [nrhs][N] (each real and not zero)
+ *   proj_idx     host int64 [nrhs][nproj], 1 <= nproj <= 64
+ *   G_out        device complex128 [nrhs][nproj][nshift], written
+ *   nu_used      host int [nrhs] or NULL: Lanczos steps done per right-hand side
+ *   seconds      host double or NULL: device time
+ * nu and shifts as in scocg_krylov_sd.  Allocates about (5 T N + T (2 + nproj)
+ * nu + 6 nu^2) doubles of device memory per call.  Returns SCOCG_OK,
+ * SCOCG_ERR_INVALID (also when a right-hand side is zero), SCOCG_ERR_TIMEOUT,
+ * SCOCG_ERR_OOM or SCOCG_ERR_CUDA.
+ */
+int scocg_krylov_sd_multi(scocg_handle h, const double *B, int nrhs, int nu, const scocg_c128 *shifts,
+                          int nshift, const int64_t *proj_idx, int nproj, scocg_c128 *G_out, int *nu_used,
+                          double *seconds);
+
 /* Free the handle and everything it owns (NULL is ignored). */
 void scocg_destroy(scocg_handle h);
 

@@ -254,6 +254,196 @@ __global__ void __launch_bounds__(kVecBlock) k_krylov_lanczos(KrylovArgs a) {
 }
 
 
+// KR-SD's recursion for several right-hand sides at once (one per slot,
+// s < T): the vectors are [n][T] with the slot fastest, so that every read of
+// H's 4x4 blocks serves all T recursions, and each slot has its own scalars,
+// projections and end.  Lane = T * (block row within the warp step) + slot.
+// Per step the same operations as k_krylov_lanczos, slot by slot; a slot that
+// has ended (or holds no right-hand side) keeps running with zero vectors and
+// records nothing.  Waits are bounded (GridSync timeout).
+struct KrylovBlockArgs {
+    int64_t n, nunits;
+    const int* unit_off;
+    const int* bcol;
+    const double* bval;
+    const double* B;          // [n][T] the right-hand sides
+    double* V[2];
+    double* W[2];             // [n][T]
+    int nu, M, nslot;         // steps, unit projections per slot, slots in use
+    const int64_t* idx;       // [T][M]
+    double* P;                // [T][M][nu] c_m^T v_j
+    double* alpha;            // [T][nu]
+    double* beta;             // [T][nu]
+    double* bnorm;            // [T]
+    int* kdim;                // [T]
+    double* part_a;           // [T][G] partials of v_j^T w_j
+    double* part_b;           // [T][G] partials of ||b||^2, then of ||w_j||^2
+    GridSync sync;
+};
+
+// the CTA's partial of each slot's per-thread values into part[slot * G + cta]
+template <int T>
+__device__ __forceinline__ void slot_partial(double v, double (*s_w)[T], double* part, int G) {
+#pragma unroll
+    for (int o = T; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);   // the warp's lanes of one slot
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane < T) s_w[warp][lane] = v;
+    __syncthreads();
+    if (threadIdx.x < T) {
+        double t = 0.0;
+        for (int w = 0; w < kVecBlock / 32; ++w) t += s_w[w][threadIdx.x];
+        part[(size_t)threadIdx.x * G + blockIdx.x] = t;
+    }
+    __syncthreads();
+}
+
+// every CTA sums each slot's partials over the CTAs in the same order
+template <int T>
+__device__ __forceinline__ void slot_sums(const double* part, int G, double* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int t = warp; t < T; t += kVecBlock / 32) {
+        double acc = 0.0;
+        for (int c = lane; c < G; c += 32) acc += __ldcg(part + (size_t)t * G + c);
+        acc = warp_sum(acc);
+        if (lane == 0) out[t] = acc;
+    }
+    __syncthreads();
+}
+
+template <int T>
+__global__ void __launch_bounds__(kVecBlock) k_krylov_block(KrylovBlockArgs a) {
+    constexpr int RPW = 32 / T;              // block rows per warp step
+    constexpr int kW = kVecBlock / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sub = lane / T, cl = lane % T;
+    const int G = gridDim.x, cta = blockIdx.x;
+    __shared__ double s_w[kW][T];
+    __shared__ double s_al[T], s_b2[T], s_bprev[T], s_inv[T], s_tn[T];
+    __shared__ int s_end[T];
+    unsigned long long epoch = 0;
+    const int64_t nbr = a.n / 4;
+    const int64_t bfirst = (int64_t)cta * nbr / G + warp * RPW + sub, bend = (int64_t)(cta + 1) * nbr / G;
+    constexpr int64_t bstep = (int64_t)kW * RPW;
+    const double* wprev = a.B;
+    // ||b_s||
+    double acc = 0.0;
+    for (int64_t B = bfirst; B < bend; B += bstep)
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+            const double x = wprev[((size_t)B * 4 + rr) * T + cl];
+            acc = fma(x, x, acc);
+        }
+    slot_partial<T>(acc, s_w, a.part_b, G);
+    if (!grid_barrier(a.sync, epoch)) return;
+    slot_sums<T>(a.part_b, G, s_b2);
+    if (threadIdx.x < T) {
+        const int t = threadIdx.x;
+        const double bn = sqrt(s_b2[t]);
+        s_end[t] = t >= a.nslot || !(bn > 0.0);
+        s_bprev[t] = bn;
+        s_inv[t] = s_end[t] ? 0.0 : 1.0 / bn;
+        s_tn[t] = 0.0;
+        if (cta == 0) {
+            a.bnorm[t] = bn;
+            a.kdim[t] = 0;
+        }
+    }
+    __syncthreads();
+    for (int j = 0; j < a.nu; ++j) {
+        double* vcur = a.V[j & 1];
+        const double* vprev = a.V[(j + 1) & 1];
+        double* wcur = a.W[j & 1];
+        if (cta == 0)
+            for (int p = threadIdx.x; p < T * a.M; p += kVecBlock) {
+                const int t = p / a.M;
+                if (!s_end[t]) a.P[(size_t)p * a.nu + j] = wprev[(size_t)a.idx[p] * T + t] * s_inv[t];
+            }
+        const double inv = s_inv[cl], bprev = s_bprev[cl];
+        acc = 0.0;
+        for (int64_t B = bfirst; B < bend; B += bstep) {
+            double hs[4] = {0.0, 0.0, 0.0, 0.0};
+            const int64_t u = B >> 3;
+            const int br = (int)(B & 7);
+            const int s0 = a.unit_off[u], s1 = a.unit_off[u + 1];
+            for (int sl = s0; sl < s1; ++sl) {
+                const int cb = ld_stream(a.bcol + (size_t)sl * 8 + br);
+                if (cb < 0) continue;
+                double xv[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) xv[q] = wprev[((size_t)cb * 4 + q) * T + cl];
+                // the block's 16 values (row-major) as eight 16-byte loads
+                const double2* hb = reinterpret_cast<const double2*>(a.bval + ((size_t)sl * 8 + br) * 16);
+#pragma unroll
+                for (int rr = 0; rr < 4; ++rr) {
+                    const double2 h01 = ld_stream(hb + 2 * rr), h23 = ld_stream(hb + 2 * rr + 1);
+                    hs[rr] = fma(h01.x, xv[0], hs[rr]);
+                    hs[rr] = fma(h01.y, xv[1], hs[rr]);
+                    hs[rr] = fma(h23.x, xv[2], hs[rr]);
+                    hs[rr] = fma(h23.y, xv[3], hs[rr]);
+                }
+            }
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr) {
+                const size_t o = ((size_t)B * 4 + rr) * T + cl;
+                const double vi = wprev[o] * inv;
+                double wi = hs[rr] * inv;
+                if (j > 0) wi = fma(-bprev, vprev[o], wi);
+                vcur[o] = vi;
+                wcur[o] = wi;
+                acc = fma(vi, wi, acc);
+            }
+        }
+        slot_partial<T>(acc, s_w, a.part_a, G);
+        if (!grid_barrier(a.sync, epoch)) return;
+        slot_sums<T>(a.part_a, G, s_al);
+        const double al = s_al[cl];
+        acc = 0.0;
+        for (int64_t B = bfirst; B < bend; B += bstep)
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr) {
+                const size_t o = ((size_t)B * 4 + rr) * T + cl;
+                const double wi = fma(-al, vcur[o], wcur[o]);
+                wcur[o] = wi;
+                acc = fma(wi, wi, acc);
+            }
+        slot_partial<T>(acc, s_w, a.part_b, G);
+        if (!grid_barrier(a.sync, epoch)) return;
+        slot_sums<T>(a.part_b, G, s_b2);
+        if (threadIdx.x < T) {
+            const int t = threadIdx.x;
+            const double be = sqrt(s_b2[t]);
+            bool end = s_end[t] != 0;
+            if (!end) {
+                s_tn[t] = fmax(s_tn[t], fabs(s_al[t]) + be + (j > 0 ? s_bprev[t] : 0.0));
+                end = (j + 1 == a.nu) || !(be > 1e-12 * s_tn[t]);
+                if (cta == 0) {
+                    a.alpha[(size_t)t * a.nu + j] = s_al[t];
+                    a.beta[(size_t)t * a.nu + j] = be;
+                    if (end) a.kdim[t] = j + 1;
+                }
+            }
+            s_end[t] = end;
+            s_bprev[t] = be;
+            s_inv[t] = end ? 0.0 : 1.0 / be;
+        }
+        __syncthreads();
+        bool live = false;
+#pragma unroll
+        for (int t = 0; t < T; ++t) live = live || !s_end[t];
+        if (!live) break;
+        wprev = wcur;
+    }
+}
+
+// x [nslot][n] -> y [n][T] (slot fastest), zero in the slots past nslot
+__global__ void k_to_slots(int64_t n, int T, int nslot, const double* x, double* y) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n * T) return;
+    const int64_t row = i / T;
+    const int t = (int)(i % T);
+    y[i] = t < nslot ? x[(size_t)t * n + row] : 0.0;
+}
+
 // partial of x^T x
 __global__ void __launch_bounds__(kVecBlock) k_norm_part(int64_t n, const double* x, double* part) {
     double acc = 0.0;
@@ -572,8 +762,25 @@ __global__ void __launch_bounds__(kVecBlock) k_proj_fin(const double* part, int 
 // issue an FP64 warp instruction in a quarter of the time of 32 on this
 // GPU's narrow FP64 pipe, which more than pays for the extra rounds.
 constexpr int kMsLanes = 8;
-__global__ void k_tri_evals(const int* kdim, const double* alpha, const double* beta, double* ev, double* scale_out) {
+// The post-processing kernels below also serve several recursions at once:
+// recursion y = blockIdx.y finds its arrays `stride` elements after the
+// previous one's (all strides 0 with one recursion).
+struct TriStride {
+    int64_t tri;     // alpha, beta, ev: nu
+    int64_t scale;   // the scale value
+    int64_t S;       // eigenvectors: nu * nu
+    int64_t work;    // 5 nu * nu
+    int64_t PW;      // projections and weights: nproj * nu
+    int64_t G;       // nproj * nshift
+    int64_t bn;      // ||b||
+};
+
+__global__ void k_tri_evals(const int* kdim, const double* alpha, const double* beta, double* ev, double* scale_out,
+                            TriStride ys) {
     __shared__ double s_a[kMaxLanczos], s_b2[kMaxLanczos];
+    const int y = blockIdx.y;
+    kdim += y; alpha += y * ys.tri; beta += y * ys.tri; ev += y * ys.tri;
+    if (scale_out) scale_out += y * ys.scale;
     const int k = *kdim;
     const int lane = threadIdx.x;
     const int q = blockIdx.x;
@@ -615,7 +822,10 @@ __global__ void k_tri_evals(const int* kdim, const double* alpha, const double* 
 // independent, one thread each (the thread of the cluster's first
 // eigenvalue); `work` holds 5 k doubles per thread.
 __global__ void k_tri_evecs(const int* kdim, const double* alpha, const double* beta, const double* ev,
-                            const double* scale_p, double* S, double* work) {
+                            const double* scale_p, double* S, double* work, TriStride ys) {
+    const int y = blockIdx.y;
+    kdim += y; alpha += y * ys.tri; beta += y * ys.tri; ev += y * ys.tri;
+    scale_p += y * ys.scale; S += y * ys.S; work += y * ys.work;
     const int k = *kdim;
     const int q0 = blockIdx.x * blockDim.x + threadIdx.x;
     if (q0 >= k) return;
@@ -686,7 +896,9 @@ __global__ void k_tri_evecs(const int* kdim, const double* alpha, const double* 
 
 // weight[m][q] = (c_m^T w_q)(w_q^T b) = (sum_j S[q][j] P[m][j]) ||b|| S[q][0]; one thread per (m, q)
 __global__ void k_krylov_weight(const int* kdim, int M, int nu, const double* S, const double* P,
-                                const double* bnorm, double* W) {
+                                const double* bnorm, double* W, TriStride ys) {
+    const int y = blockIdx.y;
+    kdim += y; S += y * ys.S; P += y * ys.PW; bnorm += y * ys.bn; W += y * ys.PW;
     const int k = *kdim;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= M * k) return;
@@ -700,7 +912,9 @@ __global__ void k_krylov_weight(const int* kdim, int M, int nu, const double* S,
 
 // G[m][kk] = sum_q weight[m][q] / (z_kk - e_q); one thread per (m, kk)
 __global__ void k_krylov_g(const int* kdim, int M, int nu, int K, const double* ev, const double* W,
-                           const double2* z, double2* G) {
+                           const double2* z, double2* G, TriStride ys) {
+    const int y = blockIdx.y;
+    kdim += y; ev += y * ys.tri; W += y * ys.PW; G += y * ys.G;
     const int k = *kdim;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= M * K) return;
@@ -1039,10 +1253,11 @@ extern "C" int scocg_krylov_sd(scocg_handle h, const double* b, int nu, const sc
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && status == SCOCG_OK) {
-        k_tri_evals<<<nu, 32, 0, st>>>(kdim, alpha, beta, ev, scal + 1);
-        k_tri_evecs<<<(nu + 7) / 8, 8, 0, st>>>(kdim, alpha, beta, ev, scal + 1, S, work);
-        k_krylov_weight<<<(M * nu + 127) / 128, 128, 0, st>>>(kdim, M, nu, S, P, scal, W);
-        k_krylov_g<<<(M * K + 127) / 128, 128, 0, st>>>(kdim, M, nu, K, ev, W, d_z, (double2*)G_out);
+        const TriStride one{};
+        k_tri_evals<<<nu, 32, 0, st>>>(kdim, alpha, beta, ev, scal + 1, one);
+        k_tri_evecs<<<(nu + 7) / 8, 8, 0, st>>>(kdim, alpha, beta, ev, scal + 1, S, work, one);
+        k_krylov_weight<<<(M * nu + 127) / 128, 128, 0, st>>>(kdim, M, nu, S, P, scal, W, one);
+        k_krylov_g<<<(M * K + 127) / 128, 128, 0, st>>>(kdim, M, nu, K, ev, W, d_z, (double2*)G_out, one);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaEventRecord(e1, st);
         if (e == cudaSuccess && ritz) e = cudaMemcpyAsync(ritz, ev, sizeof(double) * nu, cudaMemcpyDeviceToDevice, st);
@@ -1060,6 +1275,169 @@ extern "C" int scocg_krylov_sd(scocg_handle h, const double* b, int nu, const sc
             if (seconds) *seconds = ms * 1e-3;
         }
     }
+    if (e != cudaSuccess) cudaStreamSynchronize(st);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(base);
+    if (e != cudaSuccess) return cuda_status(e);
+    return status;
+}
+
+// ---------------------------------------------------------------- several right-hand sides
+#ifndef SCOCG_KRSD_CTAS_PER_SM
+#define SCOCG_KRSD_CTAS_PER_SM 2
+#endif
+namespace scocg {
+namespace {
+template <int T>
+int krylov_block_grid(const scocg_ctx* h) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_krylov_block<T>, kVecBlock, 0) != cudaSuccess || nb < 1) {
+        cudaGetLastError();
+        return 0;
+    }
+    // up to SCOCG_KRSD_CTAS_PER_SM CTAs per SM (two: 39.5 ms for 200 steps of
+    // 16 recursions on the 32^3 x 4 matrix, against 45.0 with four and 48.2
+    // with eight), at most one warp step of block rows per warp
+    const int64_t steps = (h->nunits_bsr * 8 + (kVecBlock / 32) * (32 / T) - 1) / ((kVecBlock / 32) * (32 / T));
+    int g = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::min(nb, SCOCG_KRSD_CTAS_PER_SM) * h->num_sms,
+                                                          steps));
+    if (h->opts.grid > 0) g = std::min(g, h->opts.grid);
+    return g;
+}
+
+template <int T>
+cudaError_t launch_krylov_block(const KrylovBlockArgs& ka, int grid, cudaStream_t st) {
+    void* args[] = {(void*)&ka};
+    return cudaLaunchCooperativeKernel((const void*)k_krylov_block<T>, dim3(grid), dim3(kVecBlock), args, 0, st);
+}
+}  // namespace
+}  // namespace scocg
+
+extern "C" int scocg_krylov_sd_multi(scocg_handle h, const double* B, int nrhs, int nu, const scocg_c128* shifts,
+                                     int nshift, const int64_t* proj_idx, int nproj, scocg_c128* G_out,
+                                     int* nu_used, double* seconds) {
+    if (!h || !B || nrhs < 1 || nu < 1 || nu > kMaxLanczos || !shifts || nshift < 1 || nshift > (1 << 20) ||
+        !proj_idx || nproj < 1 || nproj > 64 || !G_out)
+        return SCOCG_ERR_INVALID;
+    const int64_t n = h->n;
+    const int M = nproj, K = nshift;
+    for (int k = 0; k < K; ++k)
+        if (!std::isfinite(shifts[k].re) || !std::isfinite(shifts[k].im)) return SCOCG_ERR_INVALID;
+    for (int64_t j = 0; j < (int64_t)nrhs * M; ++j)
+        if (proj_idx[j] < 0 || proj_idx[j] >= n) return SCOCG_ERR_INVALID;
+    if (!use_bsr(h)) {
+        // other layouts: the one-right-hand-side recursion per right-hand side
+        double total = 0.0;
+        for (int r = 0; r < nrhs; ++r) {
+            int used = 0;
+            double sec = 0.0;
+            const int st = scocg_krylov_sd(h, B + (size_t)r * n, nu, shifts, K, proj_idx + (size_t)r * M, nullptr,
+                                           M, G_out + (size_t)r * M * K, nullptr, nullptr, &used, &sec);
+            if (st != SCOCG_OK) return st;
+            if (nu_used) nu_used[r] = used;
+            total += sec;
+        }
+        if (seconds) *seconds = total;
+        return SCOCG_OK;
+    }
+    const int T = nrhs <= 8 ? 8 : (nrhs <= 16 ? 16 : 32);
+    const int Gp = T == 8 ? krylov_block_grid<8>(h) : T == 16 ? krylov_block_grid<16>(h) : krylov_block_grid<32>(h);
+    if (Gp < 1) return SCOCG_ERR_CUDA;
+    Carver cv{nullptr, 0};
+    double *X0 = nullptr, *vb[4] = {nullptr, nullptr, nullptr, nullptr}, *P = nullptr, *alpha = nullptr,
+           *beta = nullptr, *bnorm = nullptr, *pa = nullptr, *pb = nullptr, *S = nullptr, *work = nullptr,
+           *ev = nullptr, *W = nullptr, *scal = nullptr;
+    int* kdim = nullptr;
+    int64_t* d_idx = nullptr;
+    double2* d_z = nullptr;
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+            void* base = nullptr;
+            if (cudaMalloc(&base, cv.off) != cudaSuccess) { cudaGetLastError(); return SCOCG_ERR_OOM; }
+            cv = Carver{static_cast<char*>(base), 0};
+        }
+        X0 = (double*)cv.take(sizeof(double) * (size_t)n * T);
+        for (int v = 0; v < 4; ++v) vb[v] = (double*)cv.take(sizeof(double) * (size_t)n * T);
+        P = (double*)cv.take(sizeof(double) * (size_t)T * M * nu);
+        alpha = (double*)cv.take(sizeof(double) * (size_t)T * nu);
+        beta = (double*)cv.take(sizeof(double) * (size_t)T * nu);
+        bnorm = (double*)cv.take(sizeof(double) * T);
+        kdim = (int*)cv.take(sizeof(int) * T);
+        pa = (double*)cv.take(sizeof(double) * (size_t)T * Gp);
+        pb = (double*)cv.take(sizeof(double) * (size_t)T * Gp);
+        d_idx = (int64_t*)cv.take(sizeof(int64_t) * (size_t)T * M);
+        d_z = (double2*)cv.take(sizeof(double2) * K);
+        // post-processing scratch, per slot
+        S = (double*)cv.take(sizeof(double) * (size_t)T * nu * nu);
+        work = (double*)cv.take(sizeof(double) * 5 * (size_t)T * nu * nu);
+        ev = (double*)cv.take(sizeof(double) * (size_t)T * nu);
+        W = (double*)cv.take(sizeof(double) * (size_t)T * M * nu);
+        scal = (double*)cv.take(sizeof(double) * 4 * T);
+    }
+    char* base = cv.base;
+    cudaStream_t st = h->stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_z, shifts, sizeof(double2) * K, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    int status = SCOCG_OK;
+    std::vector<int> kd(T);
+    std::vector<double> bn(T);
+    std::vector<int64_t> idx_tile((size_t)T * M);
+    for (int r0 = 0; r0 < nrhs && e == cudaSuccess && status == SCOCG_OK; r0 += T) {
+        const int ns = std::min(T, nrhs - r0);
+        for (int t = 0; t < T; ++t)
+            for (int m = 0; m < M; ++m) idx_tile[(size_t)t * M + m] = t < ns ? proj_idx[(size_t)(r0 + t) * M + m] : 0;
+        e = cudaMemcpyAsync(d_idx, idx_tile.data(), sizeof(int64_t) * idx_tile.size(), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) {
+            k_to_slots<<<(unsigned)((n * T + 255) / 256), 256, 0, st>>>(n, T, ns, B + (size_t)r0 * n, X0);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemsetAsync(P, 0, sizeof(double) * (size_t)T * M * nu, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->d_ctrl, 0, sizeof(Ctrl), st);
+        if (e != cudaSuccess) break;
+        KrylovBlockArgs ka;
+        ka.n = n; ka.nunits = h->nunits_bsr;
+        ka.unit_off = h->d_unit_off; ka.bcol = h->d_bcol; ka.bval = h->d_bval64;
+        ka.B = X0;
+        ka.V[0] = vb[0]; ka.V[1] = vb[1]; ka.W[0] = vb[2]; ka.W[1] = vb[3];
+        ka.nu = nu; ka.M = M; ka.nslot = ns;
+        ka.idx = d_idx; ka.P = P; ka.alpha = alpha; ka.beta = beta; ka.bnorm = bnorm; ka.kdim = kdim;
+        ka.part_a = pa; ka.part_b = pb;
+        ka.sync.count = &h->d_ctrl->count;
+        ka.sync.status = &h->d_ctrl->status;
+        ka.sync.timeout_ns = (uint64_t)(h->opts.timeout_ms * 1e6);
+        ka.sync.nctas = Gp;
+        e = T == 8 ? launch_krylov_block<8>(ka, Gp, st)
+            : T == 16 ? launch_krylov_block<16>(ka, Gp, st) : launch_krylov_block<32>(ka, Gp, st);
+        int bar = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(kd.data(), kdim, sizeof(int) * T, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(bn.data(), bnorm, sizeof(double) * T, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&bar, &h->d_ctrl->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) break;
+        if (bar < 0) { status = bar; break; }   // a grid barrier gave up (SCOCG_ERR_TIMEOUT)
+        for (int t = 0; t < ns; ++t)
+            if (!(bn[t] > 0.0)) status = SCOCG_ERR_INVALID;   // b = 0
+        if (status != SCOCG_OK) break;
+        // the tridiagonal eigenproblems, weights and G of all ns recursions together
+        const TriStride ys{nu, 4, (int64_t)nu * nu, 5LL * nu * nu, (int64_t)M * nu, (int64_t)M * K, 1};
+        k_tri_evals<<<dim3(nu, ns), 32, 0, st>>>(kdim, alpha, beta, ev, scal + 1, ys);
+        k_tri_evecs<<<dim3((nu + 7) / 8, ns), 8, 0, st>>>(kdim, alpha, beta, ev, scal + 1, S, work, ys);
+        k_krylov_weight<<<dim3((M * nu + 127) / 128, ns), 128, 0, st>>>(kdim, M, nu, S, P, bnorm, W, ys);
+        k_krylov_g<<<dim3((M * K + 127) / 128, ns), 128, 0, st>>>(kdim, M, nu, K, ev, W, d_z,
+                                                                 (double2*)(G_out + (size_t)r0 * M * K), ys);
+        e = cudaGetLastError();
+        for (int t = 0; t < ns; ++t)
+            if (nu_used) nu_used[r0 + t] = kd[t];
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && seconds) *seconds = ms * 1e-3;
     if (e != cudaSuccess) cudaStreamSynchronize(st);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);

@@ -29,7 +29,7 @@ EXPORTED = [
     "scocg_solve", "scocg_solve_full", "scocg_grad", "scocg_destroy", "scocg_strerror",
     "scocg_hubbard_tables", "scocg_solve_csr_noalloc", "scocg_solve_multi", "scocg_multi_release",
     "scocg_density", "scocg_ground_state", "scocg_excite", "scocg_krylov_sd", "scocg_create_hubbard2",
-    "scocg_solve_resume", "scocg_state_size", "scocg_state_save", "scocg_state_load",
+    "scocg_solve_resume", "scocg_state_size", "scocg_state_save", "scocg_state_load", "scocg_krylov_sd_multi",
 ]
 
 
@@ -111,6 +111,7 @@ def lib() -> ctypes.CDLL:
         L.scocg_ground_state.argtypes = [P, P, P, I, I, I, D, ctypes.POINTER(D), ctypes.POINTER(GroundInfo)]
         L.scocg_excite.argtypes = [P, P, I, I, I, P, P]
         L.scocg_krylov_sd.argtypes = [P, P, I, P, I, P, P, I, P, P, P, ctypes.POINTER(I), ctypes.POINTER(D)]
+        L.scocg_krylov_sd_multi.argtypes = [P, P, I, I, P, I, P, I, P, P, ctypes.POINTER(D)]
         L.scocg_destroy.argtypes = [P]
         L.scocg_destroy.restype = None
         L.scocg_strerror.argtypes = [I]
@@ -482,6 +483,36 @@ def scocg_ground_state(h: Handle, v0, m: int = 60, cg_steps: int = 0, max_cycles
     return E.value, psi, {"status": code, "cycles": info.cycles, "lanczos_steps": int(info.lanczos_steps),
                           "cg_steps": int(info.cg_steps), "residual": info.residual, "seconds": info.seconds,
                           "bytes_per_step": info.bytes_per_step}
+
+
+def scocg_krylov_sd_multi(h: Handle, B, nu: int, shifts, proj_idx):
+    """scocg_krylov_sd_multi: returns (G [nrhs][nproj][nshift] CUDA complex128,
+    nu_used int array [nrhs], info dict).
+
+    B: CUDA float64 [nrhs][N]; proj_idx: host int [nrhs][nproj] unit projections."""
+    import torch
+    n = scocg_dim(h)
+    B = B if B.dim() == 2 else B.reshape(1, -1)
+    _need(B.contiguous(), torch.float64, None, "B")
+    B = B.contiguous()
+    if B.shape[1] != n:
+        raise ValueError("B rows must have the handle's dimension")
+    nrhs = B.shape[0]
+    pidx = np.ascontiguousarray(np.asarray(proj_idx, dtype=np.int64))
+    if pidx.ndim == 1:
+        pidx = np.ascontiguousarray(np.broadcast_to(pidx, (nrhs, pidx.size)))
+    if pidx.shape[0] != nrhs:
+        raise ValueError("proj_idx needs one row per right-hand side")
+    M = pidx.shape[1]
+    z, zp = _shifts(shifts)
+    K = z.size
+    G = torch.empty((nrhs, M, K), dtype=torch.complex128, device=B.device)
+    used = np.zeros(nrhs, dtype=np.int32)
+    sec = ctypes.c_double()
+    code = lib().scocg_krylov_sd_multi(h.ptr, _dev(B), nrhs, int(nu), zp, K, pidx.ctypes.data, M, _dev(G),
+                                       used.ctypes.data, ctypes.byref(sec))
+    _check(code, "scocg_krylov_sd_multi")
+    return G, used, {"status": code, "seconds": sec.value}
 
 
 def scocg_krylov_sd(h: Handle, b, nu: int, shifts, proj_idx=None, proj_vec=None):

@@ -179,3 +179,117 @@ def test_invalid_arguments(S):
             S.scocg_krylov_sd(h, torch.zeros_like(b), 10, [0.1j], proj_idx=[0])
     finally:
         S.scocg_destroy(h)
+
+
+def krsd_single(S, h, B, nu, z, pidx):
+    out, used = [], []
+    for r in range(B.shape[0]):
+        G, ritz, w, info = S.scocg_krylov_sd(h, dev(B[r]), nu, z, proj_idx=pidx[r])
+        out.append(G.cpu().numpy())
+        used.append(info["nu_used"])
+    return np.stack(out), np.asarray(used)
+
+
+@pytest.mark.parametrize("nrhs", [5, 12, 19, 40])
+def test_multi_equals_single_and_oracle(S, nrhs):
+    """Several right-hand sides in one launch (T = 8, 16, 32 slots; 40 = a
+    full tile and a ragged one) on the 8^3 x 4 matrix, nu = 30 (before
+    orthogonality is lost): every right-hand side's G equals the
+    one-right-hand-side recursion's and, for three of them, the oracle's."""
+    from oracle import ground
+    h_csr = inputs.anderson_csr(8, seed=9)
+    n = h_csr.n
+    rng = np.random.default_rng(nrhs)
+    sites = rng.choice(n, nrhs, replace=False)
+    B = np.zeros((nrhs, n))
+    B[np.arange(nrhs), sites] = 1.0
+    B[::3] = np.stack([inputs.random_unit_real(n, 100 + r) for r in range(0, nrhs, 3)])
+    pidx = np.stack([sites, rng.choice(n, nrhs)], axis=1)
+    z = np.linspace(-7, 7, 21) + 0.05j
+    h = csr_handle(S, h_csr)
+    try:
+        Gm, used, info = S.scocg_krylov_sd_multi(h, dev(B), 30, z, pidx)
+        Gs, used_s = krsd_single(S, h, B, 30, z, pidx)
+    finally:
+        S.scocg_destroy(h)
+    Gm = Gm.cpu().numpy()
+    assert np.array_equal(used, used_s) and np.all(used == 30)
+    for r in range(nrhs):
+        assert np.max(np.abs(Gm[r] - Gs[r])) < 1e-10 * np.max(np.abs(Gs[r])), r
+    for r in (0, 1, nrhs - 1):
+        C = np.eye(n)[pidx[r]]
+        ref = ground.krylov_sd(h_csr.scipy(), B[r], 30, z, C)
+        assert np.max(np.abs(Gm[r] - ref.G)) < 1e-10 * np.max(np.abs(ref.G)), r
+
+
+def test_multi_slots_end_on_their_own(S):
+    """H the direct sum of a 3^3 x 4 matrix, a 4^3 x 4 matrix and one
+    isolated 4 x 4 block (108 + 256 + 4 rows): a right-hand side inside the
+    4 x 4 block spans 4 Krylov vectors, so its slot ends (beta vanishes)
+    after at most 4 steps while the others run on (nu = 600); every
+    right-hand side's G then equals its dense Green's function."""
+    import scipy.sparse as sp
+    from oracle import dense
+    a, b_ = inputs.anderson_csr(3, seed=4), inputs.anderson_csr(4, seed=6)
+    small = np.array([[0.5, 0.25, 0.0, -0.125], [0.25, -1.0, 0.375, 0.0],
+                      [0.0, 0.375, 1.5, 0.25], [-0.125, 0.0, 0.25, -0.5]])
+    Hs = sp.block_diag([a.scipy(), b_.scipy(), sp.csr_matrix(small)], format="csr")
+    Hs.sort_indices()
+    n = Hs.shape[0]
+    B = np.zeros((6, n))
+    B[0, 5] = B[1, 150] = 1.0
+    B[2, :108] = inputs.random_unit_real(108, 7)
+    B[3, 365] = 1.0
+    B[4] = inputs.random_unit_real(n, 9)
+    B[5, 364:] = [0.5, -0.5, 0.5, 0.5]
+    pidx = np.array([[5, 7], [150, 151], [0, 100], [365, 366], [3, 250], [364, 367]])
+    z = np.linspace(-6, 6, 13) + 0.2j
+    h = S.scocg_create_csr(Hs.indptr.astype(np.int64), Hs.indices.astype(np.int64), Hs.data)
+    try:
+        Gm, used, info = S.scocg_krylov_sd_multi(h, dev(B), 600, z, pidx)
+    finally:
+        S.scocg_destroy(h)
+    Gm = Gm.cpu().numpy()
+    assert used[3] <= 4 and used[5] <= 4
+    assert all(used[r] > 100 for r in (0, 1, 2, 4))
+    Hd = Hs.toarray()
+    for r in range(6):
+        ref = dense.green_dense(Hd, z, B[r].astype(np.complex128), np.eye(n)[pidx[r]].astype(np.complex128))
+        assert np.max(np.abs(Gm[r] - ref)) < 1e-9 * np.max(np.abs(ref)), r
+
+
+def test_multi_on_other_layouts_and_refusals(S):
+    """The plain CSR layout and a Hubbard handle run the one-right-hand-side
+    recursion per right-hand side (same G as calling it); a zero right-hand
+    side or an index out of range is refused."""
+    h_csr = inputs.anderson_csr(4, seed=5)
+    n = h_csr.n
+    B = np.stack([inputs.random_unit_real(n, 50), np.eye(n)[9]])
+    pidx = np.array([[1], [9]])
+    z = np.linspace(-7, 7, 9) + 0.1j
+    h = S.scocg_create_csr(h_csr.rowptr, h_csr.col, h_csr.val, opts=S.SolveOptions(layout=1))
+    try:
+        Gm, used, _ = S.scocg_krylov_sd_multi(h, dev(B), 25, z, pidx)
+        Gs, used_s = krsd_single(S, h, B, 25, z, pidx)
+        assert np.array_equal(Gm.cpu().numpy(), Gs) and np.array_equal(used, used_s)
+        with pytest.raises(S.ScocgError):
+            S.scocg_krylov_sd_multi(h, dev(np.zeros((1, n))), 10, z, [[0]])
+        with pytest.raises(S.ScocgError):
+            S.scocg_krylov_sd_multi(h, dev(B), 10, z, [[0], [n]])
+    finally:
+        S.scocg_destroy(h)
+    h = csr_handle(S, h_csr)
+    try:
+        with pytest.raises(S.ScocgError):
+            S.scocg_krylov_sd_multi(h, dev(np.stack([B[0], np.zeros(n)])), 10, z, pidx)
+    finally:
+        S.scocg_destroy(h)
+    hb = S.scocg_create_hubbard(6, 2, 2, 1.0, 4.0, 1.0, True)
+    try:
+        nh = S.scocg_dim(hb)
+        Bh = np.stack([inputs.random_unit_real(nh, 60), inputs.random_unit_real(nh, 61)])
+        Gm, used, _ = S.scocg_krylov_sd_multi(hb, dev(Bh), 20, z, [[3], [4]])
+        Gs, _ = krsd_single(S, hb, Bh, 20, z, [[3], [4]])
+        assert np.array_equal(Gm.cpu().numpy(), Gs)
+    finally:
+        S.scocg_destroy(hb)
