@@ -649,7 +649,10 @@ def profile_case(name: str, max_iter: int, precision: int):
     ``anderson`` the headline matrix and shifts, ``hubbard`` the 14-site ring,
     ``hubbard2-5`` the two-orbital sqrt(8) x sqrt(8) model with 5 up / 5 down
     electrons (19,079,424 states, a smaller device footprint than the paper's
-    6/6 sector for the replayed capture)."""
+    6/6 sector for the replayed capture); ``batch`` the 32^3 x 4 block solve
+    (256 unit right-hand sides in 32 slots, each capped at max_iter
+    iterations); ``krylov16`` KR-SD for 16 sites of the same matrix in one
+    launch (max_iter Lanczos steps, FP64)."""
     import math
     import numpy as np
     import torch
@@ -657,6 +660,28 @@ def profile_case(name: str, max_iter: int, precision: int):
     __graft_entry__.build()
     from paper_0802_0748_gb300 import inputs, scocg
     opts = scocg.SolveOptions(precision=precision, max_iter=max_iter)
+    if name in ("batch", "krylov16"):
+        wl = inputs.workload("batch", "full", bounds=BATCH_BOUNDS)
+        h = wl.csr
+        if name == "batch":
+            hh = scocg.scocg_create_csr(h.rowptr, h.col, h.val,
+                                        opts=scocg.SolveOptions(precision=precision, max_iter=max_iter, rhs_tile=32))
+            rhs = torch.from_numpy(wl.rhs).cuda()
+            G, info = scocg.scocg_solve(hh, wl.shifts, rhs, proj_idx=wl.proj_idx, tol=wl.tol)
+            out = {"block_iters": info["iters"], "us_per_block_iter": info["seconds"] / max(info["iters"], 1) * 1e6}
+        else:
+            hh = scocg.scocg_create_csr(h.rowptr, h.col, h.val)
+            sites = [int(x) for x in wl.proj_idx[:16, 0]]
+            B = torch.zeros((16, h.n), dtype=torch.float64, device="cuda")
+            for i, j in enumerate(sites):
+                B[i, j] = 1.0
+            G, used, info = scocg.scocg_krylov_sd_multi(hh, B, max_iter, np.linspace(-6.6, 7.0, 256) + 0.02j,
+                                                       np.array(sites)[:, None])
+            out = {"steps": int(used.max()), "us_per_step": info["seconds"] / max(int(used.max()), 1) * 1e6}
+        torch.cuda.synchronize()
+        scocg.scocg_destroy(hh)
+        print(json.dumps({"profile_case": name, **out}), flush=True)
+        return
     if name == "anderson":
         wl = inputs.workload("anderson", "full", bounds=BOUNDS)
         h = scocg.scocg_create_csr(wl.csr.rowptr, wl.csr.col, wl.csr.val, opts=opts)
@@ -691,7 +716,7 @@ def main():
     ap.add_argument("--max-iter", type=int, default=0, help="cap on seed iterations (0 = to convergence)")
     ap.add_argument("--legs", default="batch,multi,chain,adjoint,hubbard,hubbard2,density,krylov,ground,spectra2",
                     help="comma list of the other workloads, each timed once beside the headline")
-    ap.add_argument("--profile-case", default="", choices=["", "anderson", "hubbard", "hubbard2-5"],
+    ap.add_argument("--profile-case", default="", choices=["", "anderson", "hubbard", "hubbard2-5", "batch", "krylov16"],
                     help="run one solve of that workload in --precision (--max-iter iterations) and exit: "
                          "the launch the committed ncu summaries capture")
     args = ap.parse_args()
