@@ -489,6 +489,7 @@ def leg_krylov(scocg, dev, stream, hbm):
         return float(np.median(d)), float(d.max())
 
     scocg.scocg_krylov_sd(h, bs[0], 200, z, proj_idx=[sites[0]])            # warm-up
+    hdf = scocg.scocg_create_csr(h_csr.rowptr, h_csr.col, h_csr.val, opts=scocg.SolveOptions(precision=2))
     out = {"workload": f"G_jj at {nsite} sites of anderson-32^3x4 (131,072 rows), 256 energies + 0.02i, FP64",
            "cocg_converged": {"ms_per_site": ms_c / nsite, "tol": 1e-10, "iters": ci["iters"]}, "krsd": {}}
     for nu in (200, 400, 800, 1024):
@@ -508,6 +509,14 @@ def leg_krylov(scocg, dev, stream, hbm):
             "ms_per_site": msm / nsite, "median_rel_err": med_m, "max_rel_err": mx_m,
             "us_per_step_all_sites": im["seconds"] / nu * 1e6,
             "max_rel_diff_vs_one_site_launches": float(np.max(np.abs(Gm - Gs)) / np.max(np.abs(Gs)))}
+        # the same in compensated FP32 (SCOCG_MIXED_DF handle)
+        (Gd, used_d, idf), msd = timed(stream, lambda: scocg.scocg_krylov_sd_multi(hdf, Bm, nu, z, pidx))
+        Gd = Gd.cpu().numpy()[:, 0, :]
+        med_d, mx_d = err(Gd)
+        out["krsd"][str(nu)]["multi_df"] = {
+            "ms_per_site": msd / nsite, "median_rel_err": med_d, "max_rel_err": mx_d,
+            "us_per_step_all_sites": idf["seconds"] / nu * 1e6,
+            "max_rel_diff_vs_fp64_multi": float(np.max(np.abs(Gd - Gm)) / np.max(np.abs(Gm)))}
     # shifted COCG stopped early: the loosest residual whose G meets the accuracy KR-SD reaches at its largest nu
     target = out["krsd"]["1024"]["median_rel_err"]
     out["cocg_equal_accuracy"] = None
@@ -519,6 +528,7 @@ def leg_krylov(scocg, dev, stream, hbm):
                                           "max_rel_err": mx, "iters": ie["iters"]}
             break
     scocg.scocg_destroy(h)
+    scocg.scocg_destroy(hdf)
     out["krsd_hbm_frac_nu1024"] = None
     step_bytes = 12.0 * h_csr.nnz + 4.0 * (h_csr.n + 1) + 8 * 8.0 * h_csr.n
     k = out["krsd"]["1024"]
@@ -652,7 +662,7 @@ def profile_case(name: str, max_iter: int, precision: int):
     6/6 sector for the replayed capture); ``batch`` the 32^3 x 4 block solve
     (256 unit right-hand sides in 32 slots, each capped at max_iter
     iterations); ``krylov16`` KR-SD for 16 sites of the same matrix in one
-    launch (max_iter Lanczos steps, FP64)."""
+    launch (max_iter Lanczos steps; FP64, or compensated FP32 with df)."""
     import math
     import numpy as np
     import torch
@@ -670,7 +680,7 @@ def profile_case(name: str, max_iter: int, precision: int):
             G, info = scocg.scocg_solve(hh, wl.shifts, rhs, proj_idx=wl.proj_idx, tol=wl.tol)
             out = {"block_iters": info["iters"], "us_per_block_iter": info["seconds"] / max(info["iters"], 1) * 1e6}
         else:
-            hh = scocg.scocg_create_csr(h.rowptr, h.col, h.val)
+            hh = scocg.scocg_create_csr(h.rowptr, h.col, h.val, opts=scocg.SolveOptions(precision=precision))
             sites = [int(x) for x in wl.proj_idx[:16, 0]]
             B = torch.zeros((16, h.n), dtype=torch.float64, device="cuda")
             for i, j in enumerate(sites):

@@ -500,7 +500,10 @@ int scocg_krylov_sd(scocg_handle h, const double *b, int nu, const scocg_c128 *s
  * T recursions, each with its own scalars and end; other handles run the
  * single-right-hand-side recursion once per right-hand side.  Each slot does
  * the same arithmetic as scocg_krylov_sd (its partial sums run in another
- * order).
+ * order), in FP64, or for a handle with precision SCOCG_MIXED_DF in
+ * compensated FP32 (H's FP32 blocks, vector entries as float pairs hi + lo
+ * with error-free products and sums, FP64 step scalars), which runs on the
+ * FP32 pipe instead of the FP64 one.
  *   B            device double [nrhs][N] (each real and not zero)
  *   proj_idx     host int64 [nrhs][nproj], 1 <= nproj <= 64
  *   G_out        device complex128 [nrhs][nproj][nshift], written

@@ -435,6 +435,189 @@ __global__ void __launch_bounds__(kVecBlock) k_krylov_block(KrylovBlockArgs a) {
     }
 }
 
+// The same recursions with compensated FP32 arithmetic (SCOCG_MIXED_DF
+// handles): H's FP32 4x4 blocks, vector entries as float pairs hi + lo, the
+// products exact to the pair precision and the sums by TwoSum, so that the
+// recursion runs on the FP32 pipe (the FP64 one bounds the version above);
+// the step scalars stay FP64.  Two rows of a block row share each paired
+// FP32 instruction of the apply.
+__device__ __forceinline__ void pk_acc_fx(float2& ah, float2& al, float2 v, float xh, float xl) {
+    const float2 xh2 = make_float2(xh, xh);
+    const float2 p = pk_mul(v, xh2);
+    float2 e = pk_fma(v, xh2, pk_neg(p));
+    e = pk_fma(v, make_float2(xl, xl), e);
+    float2 s, t;
+    pk_two_sum(ah, p, s, t);
+    ah = s;
+    al = pk_add(al, pk_add(t, e));
+}
+__device__ __forceinline__ dfs df_of(double v) {
+    const float hi = (float)v;
+    return dfs{hi, (float)(v - (double)hi)};
+}
+__device__ __forceinline__ dfs df_ld(const float2* p) {
+    const float2 v = *p;
+    return dfs{v.x, v.y};
+}
+
+struct KrylovBlockDfArgs {
+    int64_t n, nunits;
+    const int* unit_off;
+    const int* bcol;
+    const float* bval;        // FP32 4x4 blocks, row-major
+    const float2* B;          // [n][T] (hi, lo)
+    float2* V[2];
+    float2* W[2];
+    int nu, M, nslot;
+    const int64_t* idx;
+    double* P;
+    double* alpha;
+    double* beta;
+    double* bnorm;
+    int* kdim;
+    double* part_a;
+    double* part_b;
+    GridSync sync;
+};
+
+template <int T>
+__global__ void __launch_bounds__(kVecBlock) k_krylov_block_df(KrylovBlockDfArgs a) {
+    constexpr int RPW = 32 / T;
+    constexpr int kW = kVecBlock / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sub = lane / T, cl = lane % T;
+    const int G = gridDim.x, cta = blockIdx.x;
+    __shared__ double s_w[kW][T];
+    __shared__ double s_al[T], s_b2[T], s_bprev[T], s_inv[T], s_tn[T];
+    __shared__ int s_end[T];
+    unsigned long long epoch = 0;
+    const int64_t nbr = a.n / 4;
+    const int64_t bfirst = (int64_t)cta * nbr / G + warp * RPW + sub, bend = (int64_t)(cta + 1) * nbr / G;
+    constexpr int64_t bstep = (int64_t)kW * RPW;
+    const float2* wprev = a.B;
+    dfs acc = {0.f, 0.f};
+    for (int64_t B = bfirst; B < bend; B += bstep)
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+            const dfs x = df_ld(wprev + ((size_t)B * 4 + rr) * T + cl);
+            df_acc_prod(acc, x, x);
+        }
+    slot_partial<T>(df_to(df_norm(acc.hi, acc.lo)), s_w, a.part_b, G);
+    if (!grid_barrier(a.sync, epoch)) return;
+    slot_sums<T>(a.part_b, G, s_b2);
+    if (threadIdx.x < T) {
+        const int t = threadIdx.x;
+        const double bn = sqrt(s_b2[t]);
+        s_end[t] = t >= a.nslot || !(bn > 0.0);
+        s_bprev[t] = bn;
+        s_inv[t] = s_end[t] ? 0.0 : 1.0 / bn;
+        s_tn[t] = 0.0;
+        if (cta == 0) {
+            a.bnorm[t] = bn;
+            a.kdim[t] = 0;
+        }
+    }
+    __syncthreads();
+    for (int j = 0; j < a.nu; ++j) {
+        float2* vcur = a.V[j & 1];
+        const float2* vprev = a.V[(j + 1) & 1];
+        float2* wcur = a.W[j & 1];
+        if (cta == 0)
+            for (int p = threadIdx.x; p < T * a.M; p += kVecBlock) {
+                const int t = p / a.M;
+                if (!s_end[t]) a.P[(size_t)p * a.nu + j] = df_to(df_ld(wprev + (size_t)a.idx[p] * T + t)) * s_inv[t];
+            }
+        const dfs inv = df_of(s_inv[cl]), nbprev = df_of(-s_bprev[cl]);
+        acc = dfs{0.f, 0.f};
+        for (int64_t B = bfirst; B < bend; B += bstep) {
+            float2 h01 = make_float2(0.f, 0.f), l01 = h01, h23 = h01, l23 = h01;   // rows (0, 1) and (2, 3)
+            const int64_t u = B >> 3;
+            const int br = (int)(B & 7);
+            const int s0 = a.unit_off[u], s1 = a.unit_off[u + 1];
+            for (int sl = s0; sl < s1; ++sl) {
+                const int cb = ld_stream(a.bcol + (size_t)sl * 8 + br);
+                if (cb < 0) continue;
+                float2 xv[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) xv[q] = wprev[((size_t)cb * 4 + q) * T + cl];
+                const float4* hb = reinterpret_cast<const float4*>(a.bval + ((size_t)sl * 8 + br) * 16);
+                const float4 r0 = ld_stream(hb), r1 = ld_stream(hb + 1), r2 = ld_stream(hb + 2), r3 = ld_stream(hb + 3);
+                pk_acc_fx(h01, l01, make_float2(r0.x, r1.x), xv[0].x, xv[0].y);
+                pk_acc_fx(h01, l01, make_float2(r0.y, r1.y), xv[1].x, xv[1].y);
+                pk_acc_fx(h01, l01, make_float2(r0.z, r1.z), xv[2].x, xv[2].y);
+                pk_acc_fx(h01, l01, make_float2(r0.w, r1.w), xv[3].x, xv[3].y);
+                pk_acc_fx(h23, l23, make_float2(r2.x, r3.x), xv[0].x, xv[0].y);
+                pk_acc_fx(h23, l23, make_float2(r2.y, r3.y), xv[1].x, xv[1].y);
+                pk_acc_fx(h23, l23, make_float2(r2.z, r3.z), xv[2].x, xv[2].y);
+                pk_acc_fx(h23, l23, make_float2(r2.w, r3.w), xv[3].x, xv[3].y);
+            }
+            pk_norm(h01, l01);
+            pk_norm(h23, l23);
+            const dfs hs[4] = {{h01.x, l01.x}, {h01.y, l01.y}, {h23.x, l23.x}, {h23.y, l23.y}};
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr) {
+                const size_t o = ((size_t)B * 4 + rr) * T + cl;
+                const dfs vi = df_mul(df_ld(wprev + o), inv);
+                dfs wi = df_mul(hs[rr], inv);
+                if (j > 0) wi = df_add(wi, df_mul(nbprev, df_ld(vprev + o)));
+                vcur[o] = make_float2(vi.hi, vi.lo);
+                wcur[o] = make_float2(wi.hi, wi.lo);
+                df_acc_prod(acc, vi, wi);
+            }
+        }
+        slot_partial<T>(df_to(df_norm(acc.hi, acc.lo)), s_w, a.part_a, G);
+        if (!grid_barrier(a.sync, epoch)) return;
+        slot_sums<T>(a.part_a, G, s_al);
+        const dfs nal = df_of(-s_al[cl]);
+        acc = dfs{0.f, 0.f};
+        for (int64_t B = bfirst; B < bend; B += bstep)
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr) {
+                const size_t o = ((size_t)B * 4 + rr) * T + cl;
+                const dfs wi = df_add(df_ld(wcur + o), df_mul(nal, df_ld(vcur + o)));
+                wcur[o] = make_float2(wi.hi, wi.lo);
+                df_acc_prod(acc, wi, wi);
+            }
+        slot_partial<T>(df_to(df_norm(acc.hi, acc.lo)), s_w, a.part_b, G);
+        if (!grid_barrier(a.sync, epoch)) return;
+        slot_sums<T>(a.part_b, G, s_b2);
+        if (threadIdx.x < T) {
+            const int t = threadIdx.x;
+            const double be = sqrt(s_b2[t]);
+            bool end = s_end[t] != 0;
+            if (!end) {
+                s_tn[t] = fmax(s_tn[t], fabs(s_al[t]) + be + (j > 0 ? s_bprev[t] : 0.0));
+                end = (j + 1 == a.nu) || !(be > 1e-12 * s_tn[t]);
+                if (cta == 0) {
+                    a.alpha[(size_t)t * a.nu + j] = s_al[t];
+                    a.beta[(size_t)t * a.nu + j] = be;
+                    if (end) a.kdim[t] = j + 1;
+                }
+            }
+            s_end[t] = end;
+            s_bprev[t] = be;
+            s_inv[t] = end ? 0.0 : 1.0 / be;
+        }
+        __syncthreads();
+        bool live = false;
+#pragma unroll
+        for (int t = 0; t < T; ++t) live = live || !s_end[t];
+        if (!live) break;
+        wprev = wcur;
+    }
+}
+
+// x [nslot][n] (FP64) -> y [n][T] as float pairs (hi, lo), zero past nslot
+__global__ void k_to_slots_df(int64_t n, int T, int nslot, const double* x, float2* y) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n * T) return;
+    const int64_t row = i / T;
+    const int t = (int)(i % T);
+    const double v = t < nslot ? x[(size_t)t * n + row] : 0.0;
+    const float hi = (float)v;
+    y[i] = make_float2(hi, (float)(v - (double)hi));
+}
+
 // x [nslot][n] -> y [n][T] (slot fastest), zero in the slots past nslot
 __global__ void k_to_slots(int64_t n, int T, int nslot, const double* x, double* y) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1287,12 +1470,17 @@ extern "C" int scocg_krylov_sd(scocg_handle h, const double* b, int nu, const sc
 #ifndef SCOCG_KRSD_CTAS_PER_SM
 #define SCOCG_KRSD_CTAS_PER_SM 2
 #endif
+#ifndef SCOCG_KRSD_DF_CTAS_PER_SM
+#define SCOCG_KRSD_DF_CTAS_PER_SM 2   // the compensated recursion measured the same with 2, 4 and 6
+#endif
 namespace scocg {
 namespace {
 template <int T>
-int krylov_block_grid(const scocg_ctx* h) {
+int krylov_block_grid(const scocg_ctx* h, bool df) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_krylov_block<T>, kVecBlock, 0) != cudaSuccess || nb < 1) {
+    const cudaError_t oe = df ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_krylov_block_df<T>, kVecBlock, 0)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_krylov_block<T>, kVecBlock, 0);
+    if (oe != cudaSuccess || nb < 1) {
         cudaGetLastError();
         return 0;
     }
@@ -1300,8 +1488,8 @@ int krylov_block_grid(const scocg_ctx* h) {
     // 16 recursions on the 32^3 x 4 matrix, against 45.0 with four and 48.2
     // with eight), at most one warp step of block rows per warp
     const int64_t steps = (h->nunits_bsr * 8 + (kVecBlock / 32) * (32 / T) - 1) / ((kVecBlock / 32) * (32 / T));
-    int g = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::min(nb, SCOCG_KRSD_CTAS_PER_SM) * h->num_sms,
-                                                          steps));
+    const int per_sm = df ? SCOCG_KRSD_DF_CTAS_PER_SM : SCOCG_KRSD_CTAS_PER_SM;
+    int g = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::min(nb, per_sm) * h->num_sms, steps));
     if (h->opts.grid > 0) g = std::min(g, h->opts.grid);
     return g;
 }
@@ -1310,6 +1498,11 @@ template <int T>
 cudaError_t launch_krylov_block(const KrylovBlockArgs& ka, int grid, cudaStream_t st) {
     void* args[] = {(void*)&ka};
     return cudaLaunchCooperativeKernel((const void*)k_krylov_block<T>, dim3(grid), dim3(kVecBlock), args, 0, st);
+}
+template <int T>
+cudaError_t launch_krylov_block_df(const KrylovBlockDfArgs& ka, int grid, cudaStream_t st) {
+    void* args[] = {(void*)&ka};
+    return cudaLaunchCooperativeKernel((const void*)k_krylov_block_df<T>, dim3(grid), dim3(kVecBlock), args, 0, st);
 }
 }  // namespace
 }  // namespace scocg
@@ -1342,7 +1535,10 @@ extern "C" int scocg_krylov_sd_multi(scocg_handle h, const double* B, int nrhs, 
         return SCOCG_OK;
     }
     const int T = nrhs <= 8 ? 8 : (nrhs <= 16 ? 16 : 32);
-    const int Gp = T == 8 ? krylov_block_grid<8>(h) : T == 16 ? krylov_block_grid<16>(h) : krylov_block_grid<32>(h);
+    // compensated FP32 recursion for SCOCG_MIXED_DF handles (H's FP32 blocks)
+    const bool df = h->opts.precision == SCOCG_MIXED_DF && h->d_bval32;
+    const int Gp = T == 8 ? krylov_block_grid<8>(h, df) : T == 16 ? krylov_block_grid<16>(h, df)
+                                                         : krylov_block_grid<32>(h, df);
     if (Gp < 1) return SCOCG_ERR_CUDA;
     Carver cv{nullptr, 0};
     double *X0 = nullptr, *vb[4] = {nullptr, nullptr, nullptr, nullptr}, *P = nullptr, *alpha = nullptr,
@@ -1392,7 +1588,11 @@ extern "C" int scocg_krylov_sd_multi(scocg_handle h, const double* B, int nrhs, 
             for (int m = 0; m < M; ++m) idx_tile[(size_t)t * M + m] = t < ns ? proj_idx[(size_t)(r0 + t) * M + m] : 0;
         e = cudaMemcpyAsync(d_idx, idx_tile.data(), sizeof(int64_t) * idx_tile.size(), cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) {
-            k_to_slots<<<(unsigned)((n * T + 255) / 256), 256, 0, st>>>(n, T, ns, B + (size_t)r0 * n, X0);
+            if (df)
+                k_to_slots_df<<<(unsigned)((n * T + 255) / 256), 256, 0, st>>>(n, T, ns, B + (size_t)r0 * n,
+                                                                               (float2*)X0);
+            else
+                k_to_slots<<<(unsigned)((n * T + 255) / 256), 256, 0, st>>>(n, T, ns, B + (size_t)r0 * n, X0);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaMemsetAsync(P, 0, sizeof(double) * (size_t)T * M * nu, st);
@@ -1410,8 +1610,22 @@ extern "C" int scocg_krylov_sd_multi(scocg_handle h, const double* B, int nrhs, 
         ka.sync.status = &h->d_ctrl->status;
         ka.sync.timeout_ns = (uint64_t)(h->opts.timeout_ms * 1e6);
         ka.sync.nctas = Gp;
-        e = T == 8 ? launch_krylov_block<8>(ka, Gp, st)
-            : T == 16 ? launch_krylov_block<16>(ka, Gp, st) : launch_krylov_block<32>(ka, Gp, st);
+        if (df) {
+            KrylovBlockDfArgs kd2;
+            kd2.n = n; kd2.nunits = h->nunits_bsr;
+            kd2.unit_off = h->d_unit_off; kd2.bcol = h->d_bcol; kd2.bval = h->d_bval32;
+            kd2.B = (const float2*)X0;
+            kd2.V[0] = (float2*)vb[0]; kd2.V[1] = (float2*)vb[1]; kd2.W[0] = (float2*)vb[2]; kd2.W[1] = (float2*)vb[3];
+            kd2.nu = nu; kd2.M = M; kd2.nslot = ns;
+            kd2.idx = d_idx; kd2.P = P; kd2.alpha = alpha; kd2.beta = beta; kd2.bnorm = bnorm; kd2.kdim = kdim;
+            kd2.part_a = pa; kd2.part_b = pb;
+            kd2.sync = ka.sync;
+            e = T == 8 ? launch_krylov_block_df<8>(kd2, Gp, st)
+                : T == 16 ? launch_krylov_block_df<16>(kd2, Gp, st) : launch_krylov_block_df<32>(kd2, Gp, st);
+        } else {
+            e = T == 8 ? launch_krylov_block<8>(ka, Gp, st)
+                : T == 16 ? launch_krylov_block<16>(ka, Gp, st) : launch_krylov_block<32>(ka, Gp, st);
+        }
         int bar = 0;
         if (e == cudaSuccess) e = cudaMemcpyAsync(kd.data(), kdim, sizeof(int) * T, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(bn.data(), bnorm, sizeof(double) * T, cudaMemcpyDeviceToHost, st);

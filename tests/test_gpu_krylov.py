@@ -227,7 +227,8 @@ def test_multi_slots_end_on_their_own(S):
     isolated 4 x 4 block (108 + 256 + 4 rows): a right-hand side inside the
     4 x 4 block spans 4 Krylov vectors, so its slot ends (beta vanishes)
     after at most 4 steps while the others run on (nu = 600); every
-    right-hand side's G then equals its dense Green's function."""
+    right-hand side's G then equals its dense Green's function, with FP64
+    and with compensated arithmetic."""
     import scipy.sparse as sp
     from oracle import dense
     a, b_ = inputs.anderson_csr(3, seed=4), inputs.anderson_csr(4, seed=6)
@@ -244,18 +245,20 @@ def test_multi_slots_end_on_their_own(S):
     B[5, 364:] = [0.5, -0.5, 0.5, 0.5]
     pidx = np.array([[5, 7], [150, 151], [0, 100], [365, 366], [3, 250], [364, 367]])
     z = np.linspace(-6, 6, 13) + 0.2j
-    h = S.scocg_create_csr(Hs.indptr.astype(np.int64), Hs.indices.astype(np.int64), Hs.data)
-    try:
-        Gm, used, info = S.scocg_krylov_sd_multi(h, dev(B), 600, z, pidx)
-    finally:
-        S.scocg_destroy(h)
-    Gm = Gm.cpu().numpy()
-    assert used[3] <= 4 and used[5] <= 4
-    assert all(used[r] > 100 for r in (0, 1, 2, 4))
     Hd = Hs.toarray()
-    for r in range(6):
-        ref = dense.green_dense(Hd, z, B[r].astype(np.complex128), np.eye(n)[pidx[r]].astype(np.complex128))
-        assert np.max(np.abs(Gm[r] - ref)) < 1e-9 * np.max(np.abs(ref)), r
+    for prec, bound in ((0, 1e-9), (2, 1e-8)):
+        h = S.scocg_create_csr(Hs.indptr.astype(np.int64), Hs.indices.astype(np.int64), Hs.data,
+                               opts=S.SolveOptions(precision=prec))
+        try:
+            Gm, used, info = S.scocg_krylov_sd_multi(h, dev(B), 600, z, pidx)
+        finally:
+            S.scocg_destroy(h)
+        Gm = Gm.cpu().numpy()
+        assert used[3] <= 4 and used[5] <= 4
+        assert all(used[r] > 100 for r in (0, 1, 2, 4))
+        for r in range(6):
+            ref = dense.green_dense(Hd, z, B[r].astype(np.complex128), np.eye(n)[pidx[r]].astype(np.complex128))
+            assert np.max(np.abs(Gm[r] - ref)) < bound * np.max(np.abs(ref)), (prec, r)
 
 
 def test_multi_on_other_layouts_and_refusals(S):
@@ -293,3 +296,34 @@ def test_multi_on_other_layouts_and_refusals(S):
         assert np.array_equal(Gm.cpu().numpy(), Gs)
     finally:
         S.scocg_destroy(hb)
+
+
+def test_multi_compensated_matches_fp64_and_oracle(S):
+    """The compensated recursion (SCOCG_MIXED_DF handle: FP32 blocks of H,
+    vectors as float pairs, FP64 step scalars) on the 8^3 x 4 matrix, 19
+    right-hand sides, nu = 30: G within 1e-9 of the FP64 recursion's and of
+    the oracle's (the values of H are FP32-exact)."""
+    from oracle import ground
+    h_csr = inputs.anderson_csr(8, seed=9)
+    n = h_csr.n
+    rng = np.random.default_rng(3)
+    sites = rng.choice(n, 19, replace=False)
+    B = np.stack([inputs.random_unit_real(n, 200 + r) for r in range(19)])
+    B[1::2] = 0.0
+    B[np.arange(1, 19, 2), sites[1::2]] = 1.0
+    pidx = np.stack([sites, rng.choice(n, 19)], axis=1)
+    z = np.linspace(-7, 7, 21) + 0.05j
+    out = {}
+    for prec in (0, 2):
+        h = S.scocg_create_csr(h_csr.rowptr, h_csr.col, h_csr.val, opts=S.SolveOptions(precision=prec))
+        try:
+            G, used, _ = S.scocg_krylov_sd_multi(h, dev(B), 30, z, pidx)
+        finally:
+            S.scocg_destroy(h)
+        assert np.all(used == 30)
+        out[prec] = G.cpu().numpy()
+    for r in range(19):
+        assert np.max(np.abs(out[2][r] - out[0][r])) < 1e-9 * np.max(np.abs(out[0][r])), r
+    for r in (0, 1, 18):
+        ref = ground.krylov_sd(h_csr.scipy(), B[r], 30, z, np.eye(n)[pidx[r]])
+        assert np.max(np.abs(out[2][r] - ref.G)) < 1e-9 * np.max(np.abs(ref.G)), r
