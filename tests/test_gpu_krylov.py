@@ -327,3 +327,27 @@ def test_multi_compensated_matches_fp64_and_oracle(S):
     for r in (0, 1, 18):
         ref = ground.krylov_sd(h_csr.scipy(), B[r], 30, z, np.eye(n)[pidx[r]])
         assert np.max(np.abs(out[2][r] - ref.G)) < 1e-9 * np.max(np.abs(ref.G)), r
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_multi_one_step_closed_form(S, prec):
+    """nu = 1 from b = e_j with projection e_j: T = [H_jj], so G = 1 / (z -
+    H_jj) exactly, for a single right-hand side (one slot of eight used) and
+    for 33 of them (a full tile of 32 and a tile with one)."""
+    h_csr = inputs.anderson_csr(6, seed=3)
+    n = h_csr.n
+    Hd = h_csr.dense()
+    z = np.linspace(-3, 3, 7) + 0.25j
+    h = S.scocg_create_csr(h_csr.rowptr, h_csr.col, h_csr.val, opts=S.SolveOptions(precision=prec))
+    try:
+        for sites in ([17], list(range(5, 5 + 33 * 7, 7))):
+            B = np.zeros((len(sites), n))
+            B[np.arange(len(sites)), sites] = 1.0
+            G, used, _ = S.scocg_krylov_sd_multi(h, dev(B), 1, z, np.array(sites)[:, None])
+            G = G.cpu().numpy()
+            assert np.all(used == 1)
+            for r, j in enumerate(sites):
+                ref = 1.0 / (z - Hd[j, j])
+                assert np.max(np.abs(G[r, 0] - ref)) < 1e-13 * np.max(np.abs(ref)), (prec, j)
+    finally:
+        S.scocg_destroy(h)
