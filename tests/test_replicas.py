@@ -61,3 +61,27 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     monkeypatch.setenv("RANK", "1")
     assert bench.run_reference(type("A", (), {"steps": 1, "warmup": 0, "gpus": 2})(), None) is None
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line(monkeypatch, capsys):
+    """The reference arm on one process: the oracle timed on a bounded sample
+    (here the 6^3 x 4 workload, 30 seed iterations) and one JSON line with the
+    keys the benchmark contract asks for, its e2e and cpu_baseline equal to
+    its own value."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_0802_0748_gb300 import inputs
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    monkeypatch.delenv("RANK", raising=False)
+    wl = inputs.workload("anderson", "small")
+    real = bench.oracle_sample
+    monkeypatch.setattr(bench, "oracle_sample", lambda w, n_shift=16, n_iter=800: real(w, n_shift, 30))
+    bench.run_reference(type("A", (), {"steps": 2, "warmup": 1, "gpus": 1})(), wl)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "higher_is_better", "scaling", "dtype",
+                "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["cpu_baseline"]["value"] == line["value"] == line["e2e"]["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
